@@ -1,0 +1,173 @@
+"""ctypes wrapper of the C oracle (trk_oracle.c) plus lattice marshalling.
+
+Oracle / test infrastructure only (see oracle/__init__.py).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "trk_oracle.c")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7}
+APERTURES = {None: 0, "rect": 1, "ellipse": 2}
+ED_N, EM_N = 16, 504
+
+
+def build(force=False):
+    """Compile the oracle (-O2 -ffp-contract=off: every operation rounds as written)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", tmp, SRC, "-lm"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        L.o_track.restype = ctypes.c_int64
+        L.o_track.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                              P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                              P, P, P, P, P, P]
+        L.o_moments.restype = None
+        L.o_moments.argtypes = [P, P, ctypes.c_int64, P]
+        L.o_wake_hist.restype = ctypes.c_int64
+        L.o_wake_hist.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, P, P, P]
+        L.o_wake_conv.restype = None
+        L.o_wake_conv.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, P]
+        L.o_wake_interp.restype = ctypes.c_double
+        L.o_wake_interp.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.o_wake.restype = None
+        L.o_wake.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lattice_arrays(lat):
+    els = lat["elements"]
+    ne = len(els)
+    ei = np.zeros((ne, 4), np.int32)
+    ed = np.zeros((ne, ED_N), np.float64)
+    em = np.zeros((ne, EM_N), np.float64)
+    for e, el in enumerate(els):
+        t = el["type"]
+        ei[e, 0] = TYPES[t]
+        if t == "MAP":
+            m = el["map"]
+            ei[e, 1] = m["order"]
+            em[e, 0:6] = m["C"]
+            em[e, 6:42] = np.asarray(m["R"]).ravel()
+            em[e, 42:168] = np.asarray(m["T"]).ravel()
+            em[e, 168:504] = np.asarray(m["U"]).ravel()
+        elif t == "EDRIFT":
+            ed[e, 0] = el["L"]
+        elif t in ("KQUAD", "KSEXT"):
+            ed[e, 0] = el["L"]
+            ed[e, 1] = el.get("K1", 0.0)
+            ed[e, 2] = el.get("K2", 0.0)
+            ei[e, 2] = el["n_kicks"]
+        elif t == "THINSEXT":
+            ed[e, 9] = el["K2L"]
+        elif t == "RFCA":
+            ed[e, 3], ed[e, 4], ed[e, 5] = el["volt"], el["phase_deg"], el["freq_hz"]
+        elif t == "WAKE":
+            ei[e, 3] = el["nbins"]
+            ed[e, 6], ed[e, 7], ed[e, 8] = el["W0"], el["sc"], el["charge"]
+        else:
+            raise ValueError(t)
+    return ei, ed, em
+
+
+def track(lat, z, n_turns, turn0=0, state=None, moments=True, p0c=None, n_total=None):
+    """Track a copy of z (n x 6).  `state` (from a previous call) continues a run.
+    Returns dict z, alive, loss_turn, loss_elem, margin, moments, p0c, n_alive."""
+    ei, ed, em = lattice_arrays(lat)
+    if state is None:
+        z = np.array(z, dtype=np.float64, order="C", copy=True)
+        n = z.shape[0]
+        state = {"z": z, "alive": np.ones(n, np.uint8), "loss_turn": np.full(n, -1, np.int32),
+                 "loss_elem": np.full(n, -1, np.int32), "margin": np.full(n, np.inf),
+                 "p0c": lat["p0c"] if p0c is None else p0c, "n_total": n if n_total is None else n_total}
+    else:
+        state = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in state.items()}
+    n = state["z"].shape[0]
+    mom = np.zeros((max(n_turns, 1), 28)) if moments else None
+    p0 = ctypes.c_double(state["p0c"])
+    ap = lat.get("aperture")
+    ap_t, ap_a, ap_b = (APERTURES[ap[0]], ap[1], ap[2]) if ap else (0, 0.0, 0.0)
+    na = lib().o_track(len(lat["elements"]), _p(ei), _p(ed), _p(em), ap_t, ap_a, ap_b,
+                       _p(state["z"]), n, state["n_total"], n_turns, turn0,
+                       _p(state["alive"]), _p(state["loss_turn"]), _p(state["loss_elem"]),
+                       _p(state["margin"]), _p(mom) if moments else None, ctypes.byref(p0))
+    state["p0c"] = p0.value
+    state["n_alive"] = int(na)
+    state["moments"] = mom[:n_turns] if moments else None
+    return state
+
+
+def moments(z, alive=None):
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    alive = np.ones(z.shape[0], np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    out = np.zeros(28)
+    lib().o_moments(_p(z), _p(alive), z.shape[0], _p(out))
+    return out
+
+
+def wake_hist(l, nbins, alive=None):
+    n = len(l)
+    z = np.zeros((n, 6))
+    z[:, 4] = l
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    lmin, dl = ctypes.c_double(), ctypes.c_double()
+    na = lib().o_wake_hist(_p(z), _p(alive), n, nbins, ctypes.byref(lmin), ctypes.byref(dl), _p(h))
+    return h, lmin.value, dl.value, int(na)
+
+
+def wake_conv(hist, dl, w0, sc, qm):
+    hist = np.ascontiguousarray(hist, np.int64)
+    V = np.zeros(len(hist))
+    lib().o_wake_conv(_p(hist), len(hist), dl, w0, sc, qm, _p(V))
+    return V
+
+
+def wake_interp(V, lmin, dl, l):
+    V = np.ascontiguousarray(V, np.float64)
+    return lib().o_wake_interp(_p(V), len(V), lmin, dl, l)
+
+
+def wake(z, nbins, w0, sc, charge, p0c, alive=None, n_total=None):
+    """One wake element on a copy of z; returns (z, hist, V)."""
+    z = np.array(z, dtype=np.float64, order="C", copy=True)
+    n = z.shape[0]
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    V = np.zeros(nbins)
+    lib().o_wake(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, w0, sc, charge, p0c,
+                 _p(h), _p(V))
+    return z, h, V
+
+
+def survival_turns(lat, z0, n_turns):
+    """DA survival turn per particle: the 1-based turn of the loss, n_turns + 1
+    if it survives."""
+    s = track(lat, z0, n_turns, moments=False)
+    return np.where(s["alive"] == 1, n_turns + 1, s["loss_turn"] + 1).astype(np.int32)

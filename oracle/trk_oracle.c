@@ -1,0 +1,390 @@
+/*
+ * trk_oracle.c -- plain, slow, single-threaded FP64 CPU tracker.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py load this library.  It shares
+ * no code, header or table with the product library and is compiled with
+ * -O2 -ffp-contract=off so every operation rounds exactly as written.
+ *
+ * What it computes (GPU acceleration of Elegant, arXiv:1710.07350):
+ *   - the element-by-element particle loop of the paper's CPU listings
+ *     (Sec. 2.1, exactDrift over double **part), kept array-of-structs;
+ *   - transport maps up to third order (Sec. 1; Table 1 track_particles M1-M3):
+ *       x_i <- C_i + sum_j R_ij x_j + sum_{j<=k} T_ijk x_j x_k
+ *                  + sum_{j<=k<=l} U_ijkl x_j x_k x_l     (simultaneous update);
+ *   - exact drift EDRIFT (Sec. 2.1 listings, path-length deviation stored);
+ *   - kick-drift thick quadrupole / sextupole (Table 1 multipole_tracking2,
+ *     Sec. 3 "canonical kick ... 4th order symplectic integration"):
+ *     n steps of the 4th-order Yoshida scheme D K D K D K D, exact-Hamiltonian
+ *     drifts, canonical momenta converted from / to slopes at entry / exit;
+ *   - thin sextupole kick, thin RF cavity (Table 1 simple_rf_cavity, beta = 1);
+ *   - global aperture after every element with particle loss (Sec. 2.5, Table 1
+ *     limit_amplitudes / RCOL / ECOL); lost particles keep their coordinates
+ *     at the loss point and the (turn, element) of the loss;
+ *   - per-turn beam moments (Sec. 2.4, accumulate_beam_sums; compensated sums as
+ *     the paper's USE_KAHAN option): n, 6 means, 21 central second moments;
+ *   - longitudinal wake (Sec. 2.2-2.3, Table 1 WAKE): min/max of l, histogram,
+ *     direct O(N^2) causal convolution with W(s) = W0/sqrt(max(s, s_c)),
+ *     linearly interpolated energy kick.
+ *
+ * Coordinates: (x, x', y, y', l, delta), l the path-length deviation [m].
+ * Lattice description: one row per element in three flat arrays
+ *   ei[4*e + 0..3]  = type, order (MAP), n_kicks (KQUAD/KSEXT), nbins (WAKE)
+ *   ed[16*e + ...]  = see ED_* below
+ *   em[504*e + ...] = C[6], R[36] (row-major), T[6*21], U[6*56] (MAP only)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7 };
+enum { O_AP_NONE = 0, O_AP_RECT = 1, O_AP_ELLIPSE = 2 };
+enum { ED_LENGTH = 0, ED_K1 = 1, ED_K2 = 2, ED_VOLT = 3, ED_PHASE = 4, ED_FREQ = 5,
+       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_N = 16 };
+#define EM_N 504
+#define C_LIGHT 299792458.0
+#define O_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------- maps ---- */
+
+/* Dense plain definition of a polynomial map of order 1..3.  Monomial order:
+ * (j,k) j<=k and (j,k,l) j<=k<=l, lexicographic. */
+static void apply_map(double *z, const double *m, int order)
+{
+    const double *C = m, *R = m + 6, *T = m + 42, *U = m + 168;
+    double in[6], out[6];
+    memcpy(in, z, sizeof in);
+    for (int i = 0; i < 6; ++i) {
+        double acc = C[i];
+        for (int j = 0; j < 6; ++j)
+            acc += R[6 * i + j] * in[j];
+        if (order >= 2) {
+            int q = 0;
+            for (int j = 0; j < 6; ++j)
+                for (int k = j; k < 6; ++k, ++q)
+                    acc += T[21 * i + q] * in[j] * in[k];
+        }
+        if (order >= 3) {
+            int q = 0;
+            for (int j = 0; j < 6; ++j)
+                for (int k = j; k < 6; ++k)
+                    for (int l = k; l < 6; ++l, ++q)
+                        acc += U[56 * i + q] * in[j] * in[k] * in[l];
+        }
+        out[i] = acc;
+    }
+    memcpy(z, out, sizeof out);
+}
+
+/* ------------------------------------------------------- exact drift ---- */
+
+static void exact_drift(double *z, double L)
+{
+    double xp = z[1], yp = z[3];
+    z[0] += L * xp;
+    z[2] += L * yp;
+    z[4] += L * (sqrt(1.0 + xp * xp + yp * yp) - 1.0);
+}
+
+/* ------------------------------------------------ kick-drift multipoles ---- */
+
+static void drift_canonical(double *c, double h)
+{
+    double P = 1.0 + c[5];
+    double pz = sqrt(P * P - c[1] * c[1] - c[3] * c[3]);
+    c[0] += h * c[1] / pz;
+    c[2] += h * c[3] / pz;
+    c[4] += h * (P / pz - 1.0);
+}
+
+static void kick_canonical(double *c, double h, double k1, double k2)
+{
+    double x = c[0], y = c[2];
+    if (k1 != 0.0) {
+        c[1] -= k1 * h * x;
+        c[3] += k1 * h * y;
+    }
+    if (k2 != 0.0) {
+        c[1] -= 0.5 * k2 * h * (x * x - y * y);
+        c[3] += k2 * h * x * y;
+    }
+}
+
+/* 4th-order Yoshida: w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1 (= -2^(1/3) w1);
+ * one step D(w1/2) K(w1) D((w0+w1)/2) K(w0) D((w0+w1)/2) K(w1) D(w1/2). */
+static void thick_multipole(double *z, double L, double k1, double k2, int n)
+{
+    double w1 = 1.0 / (2.0 - cbrt(2.0));
+    double w0 = 1.0 - 2.0 * w1;
+    double h = L / n;
+    double c[6];
+    double P = 1.0 + z[5];
+    double r = sqrt(1.0 + z[1] * z[1] + z[3] * z[3]);
+    c[0] = z[0]; c[1] = P * z[1] / r;
+    c[2] = z[2]; c[3] = P * z[3] / r;
+    c[4] = z[4]; c[5] = z[5];
+    for (int s = 0; s < n; ++s) {
+        drift_canonical(c, 0.5 * w1 * h);
+        kick_canonical(c, w1 * h, k1, k2);
+        drift_canonical(c, 0.5 * (w0 + w1) * h);
+        kick_canonical(c, w0 * h, k1, k2);
+        drift_canonical(c, 0.5 * (w0 + w1) * h);
+        kick_canonical(c, w1 * h, k1, k2);
+        drift_canonical(c, 0.5 * w1 * h);
+    }
+    double pz = sqrt(P * P - c[1] * c[1] - c[3] * c[3]);
+    z[0] = c[0]; z[1] = c[1] / pz;
+    z[2] = c[2]; z[3] = c[3] / pz;
+    z[4] = c[4];
+}
+
+static void thin_sext(double *z, double k2l)
+{
+    double x = z[0], y = z[2];
+    z[1] -= 0.5 * k2l * (x * x - y * y);
+    z[3] += k2l * x * y;
+}
+
+/* ------------------------------------------------------------------ RF ---- */
+
+static void rfca(double *z, double volt, double phi, double k, double p0c, double p0c1)
+{
+    double P = (1.0 + z[5]) * p0c;
+    double P1 = P + volt * cos(phi + k * z[4]);
+    double s = P / P1;
+    z[1] *= s;
+    z[3] *= s;
+    z[5] = P1 / p0c1 - 1.0;
+}
+
+/* ------------------------------------------------------------ aperture ---- */
+
+/* Returns 1 if the particle is inside (edge counts as inside; NaN is outside).
+ * *margin receives an estimate of the distance to the edge [m]. */
+static int aperture_ok(const double *z, int type, double a, double b, double *margin)
+{
+    double x = z[0], y = z[2];
+    if (type == O_AP_RECT) {
+        double mx = a - fabs(x), my = b - fabs(y);
+        *margin = mx < my ? mx : my;
+        return fabs(x) <= a && fabs(y) <= b;
+    }
+    /* ellipse */
+    double u = x / a, v = y / b;
+    double rho = u * u + v * v;
+    double gx = 2.0 * x / (a * a), gy = 2.0 * y / (b * b);
+    double g = sqrt(gx * gx + gy * gy);
+    *margin = g > 0.0 ? (1.0 - rho) / g : (a < b ? a : b);
+    return rho <= 1.0;
+}
+
+/* ------------------------------------------------------------- moments ---- */
+
+/* Neumaier's improved Kahan-Babuska summation. */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum *a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double nsum_get(const nsum *a) { return a->s + a->c; }
+
+/* out[28] = n, 6 means, 21 population central second moments (j<=k),
+ * two-pass over the alive particles.  No alive particle: all zero. */
+void o_moments(const double *x, const uint8_t *alive, int64_t n, double *out)
+{
+    memset(out, 0, 28 * sizeof(double));
+    int64_t na = 0;
+    nsum s1[6];
+    memset(s1, 0, sizeof s1);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        ++na;
+        for (int j = 0; j < 6; ++j) nsum_add(&s1[j], x[6 * i + j]);
+    }
+    out[0] = (double)na;
+    if (na == 0) return;
+    double m[6];
+    for (int j = 0; j < 6; ++j) m[j] = nsum_get(&s1[j]) / (double)na;
+    nsum s2[21];
+    memset(s2, 0, sizeof s2);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        double d[6];
+        for (int j = 0; j < 6; ++j) d[j] = x[6 * i + j] - m[j];
+        int q = 0;
+        for (int j = 0; j < 6; ++j)
+            for (int k = j; k < 6; ++k, ++q) nsum_add(&s2[q], d[j] * d[k]);
+    }
+    for (int j = 0; j < 6; ++j) out[1 + j] = m[j];
+    for (int q = 0; q < 21; ++q) out[7 + q] = nsum_get(&s2[q]) / (double)na;
+}
+
+/* ---------------------------------------------------------------- wake ---- */
+
+/* A10 + A11: window [min l, max l] over alive particles, nb equal bins,
+ * bin = clamp(floor((l - lmin)/dl), 0, nb-1).  If max == min, dl = 0 and every
+ * particle is in bin 0.  Returns the number of alive particles. */
+int64_t o_wake_hist(const double *x, const uint8_t *alive, int64_t n, int nb,
+                    double *lmin_out, double *dl_out, int64_t *hist)
+{
+    double lmin = INFINITY, lmax = -INFINITY;
+    int64_t na = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        double l = x[6 * i + 4];
+        if (l < lmin) lmin = l;
+        if (l > lmax) lmax = l;
+        ++na;
+    }
+    memset(hist, 0, (size_t)nb * sizeof(int64_t));
+    if (na == 0) { *lmin_out = 0.0; *dl_out = 0.0; return 0; }
+    double dl = (lmax - lmin) / nb;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        int64_t b = 0;
+        if (dl > 0.0) {
+            b = (int64_t)floor((x[6 * i + 4] - lmin) / dl);
+            if (b < 0) b = 0;
+            if (b > nb - 1) b = nb - 1;
+        }
+        ++hist[b];
+    }
+    *lmin_out = lmin;
+    *dl_out = dl;
+    return na;
+}
+
+/* A12: V_k = -q_m sum_{j<=k} h_j W((k-j) dl),  W(s) = W0/sqrt(max(s, s_c)).
+ * Direct O(nb^2), compensated sums. */
+void o_wake_conv(const int64_t *hist, int nb, double dl, double w0, double sc, double qm, double *V)
+{
+    for (int k = 0; k < nb; ++k) {
+        nsum acc = {0.0, 0.0};
+        for (int j = 0; j <= k; ++j) {
+            if (hist[j] == 0) continue;
+            double s = (double)(k - j) * dl;
+            double w = w0 / sqrt(s > sc ? s : sc);
+            nsum_add(&acc, (double)hist[j] * w);
+        }
+        V[k] = -qm * nsum_get(&acc);
+    }
+}
+
+/* Voltage seen at l: linear interpolation between bin centres, clamped to the
+ * end bins.  dl == 0: V[0]. */
+double o_wake_interp(const double *V, int nb, double lmin, double dl, double l)
+{
+    if (!(dl > 0.0)) return V[0];
+    double u = (l - lmin) / dl - 0.5;
+    double k0 = floor(u);
+    if (k0 < 0.0) return V[0];
+    if (k0 >= (double)(nb - 1)) return V[nb - 1];
+    int k = (int)k0;
+    double f = u - k0;
+    return (1.0 - f) * V[k] + f * V[k + 1];
+}
+
+/* A13: delta += V(l)/p0c for every alive particle. */
+void o_wake_kick(double *x, const uint8_t *alive, int64_t n, const double *V, int nb,
+                 double lmin, double dl, double p0c)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        x[6 * i + 5] += o_wake_interp(V, nb, lmin, dl, x[6 * i + 4]) / p0c;
+    }
+}
+
+/* Whole wake element; n_total sets the macro-particle charge q_m = Q/n_total.
+ * hist_out / V_out (nb entries each) may be NULL. */
+void o_wake(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb,
+            double w0, double sc, double charge, double p0c, int64_t *hist_out, double *V_out)
+{
+    int64_t *h = (int64_t *)malloc((size_t)nb * sizeof(int64_t));
+    double *V = (double *)malloc((size_t)nb * sizeof(double));
+    double lmin, dl;
+    int64_t na = o_wake_hist(x, alive, n, nb, &lmin, &dl, h);
+    if (na > 0) {
+        o_wake_conv(h, nb, dl, w0, sc, charge / (double)n_total, V);
+        o_wake_kick(x, alive, n, V, nb, lmin, dl, p0c);
+    } else {
+        memset(V, 0, (size_t)nb * sizeof(double));
+    }
+    if (hist_out) memcpy(hist_out, h, (size_t)nb * sizeof(int64_t));
+    if (V_out) memcpy(V_out, V, (size_t)nb * sizeof(double));
+    free(h);
+    free(V);
+}
+
+/* ------------------------------------------------------------ tracking ---- */
+
+/*
+ * Track n particles (x: n x 6, AoS) for n_turns turns through ne elements.
+ *   alive[i]      in/out, 1 = alive; lost particles are skipped.
+ *   loss_turn[i]  out, absolute turn (turn0 + t) of the loss, -1 if alive
+ *   loss_elem[i]  out, element index of the loss, -1 if alive
+ *   margin[i]     in/out, running minimum of |distance to the aperture edge|
+ *                 over all element exits checked so far (pass +inf initially)
+ *   moments       out [n_turns][28] after each turn, or NULL
+ *   p0c           in/out reference momentum [eV]
+ *   n_total       particle count that sets the wake macro-charge
+ * Returns the number of alive particles at the end.
+ */
+int64_t o_track(int ne, const int32_t *ei, const double *ed, const double *em,
+                int ap_type, double ap_a, double ap_b,
+                double *x, int64_t n, int64_t n_total, int n_turns, int turn0,
+                uint8_t *alive, int32_t *loss_turn, int32_t *loss_elem, double *margin,
+                double *moments, double *p0c)
+{
+    for (int t = 0; t < n_turns; ++t) {
+        for (int e = 0; e < ne; ++e) {
+            const int32_t *iv = ei + 4 * e;
+            const double *dv = ed + ED_N * e;
+            int type = iv[0];
+            if (type == O_WAKE) {
+                o_wake(x, alive, n, n_total, iv[3], dv[ED_W0], dv[ED_SC], dv[ED_CHARGE], *p0c, NULL, NULL);
+            } else if (type == O_RFCA) {
+                double phi = dv[ED_PHASE] * O_PI / 180.0;
+                double k = 2.0 * O_PI * dv[ED_FREQ] / C_LIGHT;
+                double p1 = *p0c + dv[ED_VOLT] * cos(phi);
+                for (int64_t i = 0; i < n; ++i)
+                    if (alive[i]) rfca(x + 6 * i, dv[ED_VOLT], phi, k, *p0c, p1);
+                *p0c = p1;
+            } else {
+                for (int64_t i = 0; i < n; ++i) {
+                    if (!alive[i]) continue;
+                    double *z = x + 6 * i;
+                    switch (type) {
+                    case O_MAP: apply_map(z, em + (size_t)EM_N * e, iv[1]); break;
+                    case O_EDRIFT: exact_drift(z, dv[ED_LENGTH]); break;
+                    case O_KQUAD:
+                    case O_KSEXT: thick_multipole(z, dv[ED_LENGTH], dv[ED_K1], dv[ED_K2], iv[2]); break;
+                    case O_THINSEXT: thin_sext(z, dv[ED_K2L]); break;
+                    default: break;
+                    }
+                }
+            }
+            if (ap_type != O_AP_NONE) {
+                for (int64_t i = 0; i < n; ++i) {
+                    if (!alive[i]) continue;
+                    double m;
+                    int ok = aperture_ok(x + 6 * i, ap_type, ap_a, ap_b, &m);
+                    double am = fabs(m);
+                    if (!(am >= margin[i])) margin[i] = am; /* NaN margin also recorded */
+                    if (!ok) {
+                        alive[i] = 0;
+                        loss_turn[i] = turn0 + t;
+                        loss_elem[i] = e;
+                    }
+                }
+            }
+        }
+        if (moments) o_moments(x, alive, n, moments + 28 * (size_t)t);
+    }
+    int64_t na = 0;
+    for (int64_t i = 0; i < n; ++i) na += alive[i] ? 1 : 0;
+    return na;
+}
