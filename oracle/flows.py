@@ -81,10 +81,12 @@ def canonical_to_slopes(z):
 
 
 def drift_canonical(z, h):
+    """l += h (P/pz - 1), evaluated as h (px^2 + py^2) / (pz (P + pz))."""
     x, px, y, py, l, d = z
     P = 1.0 + d
-    pz = sqrt(P * P - px * px - py * py)
-    return [x + h * px / pz, px, y + h * py / pz, py, l + h * (P / pz - 1.0), d]
+    p2 = px * px + py * py
+    pz = sqrt(P * P - p2)
+    return [x + h * px / pz, px, y + h * py / pz, py, l + h * (p2 / (pz * (P + pz))), d]
 
 
 def kick_canonical(z, h, k1, k2):
@@ -115,10 +117,11 @@ def thick_multipole(z, length, k1, k2, n_steps, scheme=YOSHIDA4):
 
 
 def exact_drift(z, length):
-    """EDRIFT (Sec. 2.1 listings), storing the path-length deviation."""
+    """EDRIFT (Sec. 2.1 listings), storing the path-length deviation
+    L (sqrt(1 + v) - 1), evaluated as L v / (sqrt(1 + v) + 1)."""
     x, xp, y, yp, l, d = z
-    return [x + length * xp, xp, y + length * yp, yp,
-            l + length * (sqrt(1.0 + xp * xp + yp * yp) - 1.0), d]
+    v = xp * xp + yp * yp
+    return [x + length * xp, xp, y + length * yp, yp, l + length * (v / (sqrt(1.0 + v) + 1.0)), d]
 
 
 def thin_quad(z, k1l):

@@ -79,23 +79,31 @@ static void apply_map(double *z, const double *m, int order)
 
 /* ------------------------------------------------------- exact drift ---- */
 
+/* The path-length deviation L (sqrt(1 + v) - 1), v = x'^2 + y'^2, is evaluated
+ * as L v / (sqrt(1 + v) + 1): the same quantity without the cancellation that
+ * would quantise an increment of ~1e-10 m to the 2.2e-16 spacing of doubles
+ * near 1. */
 static void exact_drift(double *z, double L)
 {
     double xp = z[1], yp = z[3];
+    double v = xp * xp + yp * yp;
     z[0] += L * xp;
     z[2] += L * yp;
-    z[4] += L * (sqrt(1.0 + xp * xp + yp * yp) - 1.0);
+    z[4] += L * (v / (sqrt(1.0 + v) + 1.0));
 }
 
 /* ------------------------------------------------ kick-drift multipoles ---- */
 
+/* l += h (P/pz - 1), written as h (px^2 + py^2) / (pz (P + pz)) (since
+ * P^2 - pz^2 = px^2 + py^2) to keep the small increment free of cancellation. */
 static void drift_canonical(double *c, double h)
 {
     double P = 1.0 + c[5];
-    double pz = sqrt(P * P - c[1] * c[1] - c[3] * c[3]);
+    double p2 = c[1] * c[1] + c[3] * c[3];
+    double pz = sqrt(P * P - p2);
     c[0] += h * c[1] / pz;
     c[2] += h * c[3] / pz;
-    c[4] += h * (P / pz - 1.0);
+    c[4] += h * (p2 / (pz * (P + pz)));
 }
 
 static void kick_canonical(double *c, double h, double k1, double k2)

@@ -42,6 +42,9 @@ C3_NBINS, C3_W0, C3_CHARGE = 4096, 4.0e11, 250e-12
 C3_SIGMA_L = 100e-6
 C3_SC = 0.1 * C3_SIGMA_L
 K2L_THIN = K2_SEXT * L_SEXT
+# c5 names no sextupole strength; 10x the c4 value makes the DA sextupole-limited
+# inside the +-20 mm aperture (with K2L_THIN it is the aperture rectangle).
+K2L_C5 = 10.0 * K2L_THIN
 EMIT, SIGMA_D, SIGMA_L = 1e-8, 1e-3, 1e-3
 DA_HALF_WIDTH, DA_N = 0.025, 512
 
@@ -144,8 +147,8 @@ def c5_params(n_var=64, seed=5):
 
 def c5_strengths(p):
     return (K1_QUAD * (1 + 0.02 * p[0]), -K1_QUAD * (1 + 0.02 * p[1]),
-            K2L_THIN * (1 + 0.1 * p[2]), K2L_THIN * (1 + 0.1 * p[3]),
-            -K2L_THIN * (1 + 0.1 * p[4]), -K2L_THIN * (1 + 0.1 * p[5]))
+            K2L_C5 * (1 + 0.1 * p[2]), K2L_C5 * (1 + 0.1 * p[3]),
+            -K2L_C5 * (1 + 0.1 * p[4]), -K2L_C5 * (1 + 0.1 * p[5]))
 
 
 def lattice_c5(v):
@@ -199,6 +202,9 @@ def bunch(name, n=None, seed=None):
     if name == "c3":
         return gaussian_bunch(n or 10_000_000, 3 if seed is None else seed, twiss("c3"),
                               sigma_l=C3_SIGMA_L, tail_frac=0.05, tail_half_width=6 * C3_SIGMA_L)
-    if name == "c4":
-        return gaussian_bunch(n, 4 if seed is None else seed, twiss("c1"))
     raise KeyError(name)
+
+
+def c4_bunch(v, n):
+    """Bunch of c4 variant v (its own Philox key, disjoint from the variant draw)."""
+    return gaussian_bunch(n, (4 << 16) + v, twiss("c1"))
