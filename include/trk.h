@@ -1,0 +1,203 @@
+/*
+ * trk.h -- C ABI of the GB300 (sm_103a) FP64 particle tracker.
+ *
+ * The library implements the data-parallel hot path of GPU-accelerated Elegant
+ * (King et al., "GPU acceleration and performance of the particle-beam-dynamics
+ * code Elegant", arXiv:1710.07350): the per-turn 6D tracking loop through
+ * lumped elements (Sec. 1; Table 1), particle loss at apertures (Sec. 2.5),
+ * per-turn beam moments by reduction (Sec. 2.4), and the longitudinal wakefield
+ * path of histogram (Sec. 2.2), convolution (Sec. 2.3) and energy kick
+ * (Table 1, WAKE / RFCW).
+ *
+ * Conventions shared by every call
+ *   Coordinates  per particle (x [m], x' [rad], y [m], y' [rad], l [m], delta):
+ *                slopes as in the paper's exactDrift listings (Sec. 2.1); l is
+ *                the path-length DEVIATION from the reference particle; delta
+ *                is the relative momentum deviation from the reference p0.
+ *                Particles are ultra-relativistic (beta = 1).
+ *   Layout       structure of arrays (Sec. 2, barrier 1): coordinate c of
+ *                particle i is coords[c * pitch + i], FP64, device memory.
+ *                pitch >= n; coords must be 16-byte aligned.
+ *   Ownership    particle arrays and outputs passed as device pointers are
+ *                owned by the CALLER (e.g. PyTorch tensors) and only borrowed.
+ *                Lattices and all scratch are owned by the library and freed by
+ *                trk_destroy_lattice / trk_bunch_free.
+ *   Streams      device work is enqueued on the bunch's CUDA stream; calls that
+ *                enqueue work return before it completes.  Calls that return
+ *                host data (trk_moments, trk_lost, trk_n_alive, trk_bunch_p0c)
+ *                synchronise that stream first.
+ *   Errors       every call returns a trk_status; nothing aborts, exits or
+ *                traps.  trk_last_error() gives the calling thread's text for
+ *                the last non-OK status.  Device-side failures surface as
+ *                TRK_ECUDA at the next call that synchronises.
+ *   Ordering     after trk_track the alive particles occupy slots [0, n_alive)
+ *                in their previous relative order (stable compaction); lost
+ *                particles follow in order of loss.  Identify particles by id.
+ */
+#ifndef TRK_H
+#define TRK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRK_OK = 0,
+    TRK_EINVAL = 1,       /* invalid argument or descriptor */
+    TRK_ENOMEM = 2,       /* device or host allocation failed */
+    TRK_ECUDA = 3,        /* a CUDA runtime call failed */
+    TRK_EKERNEL = 4,      /* a kernel reported an internal error */
+    TRK_ETIMEOUT = 5,     /* a bounded device wait ran out */
+    TRK_EUNSUPPORTED = 6  /* valid request the library does not implement */
+} trk_status;
+
+/* Element types (Table 1 of the paper). */
+typedef enum {
+    TRK_MAP = 1,       /* polynomial transport map of order 1..3 (R, T, U):
+                          "transport matrices (up to third order)", Sec. 1;
+                          track_particles M1/M2/M3 rows of Table 1.
+                          x_i <- C_i + sum_j R_ij x_j + sum_{j<=k} T_i(jk) x_j x_k
+                                     + sum_{j<=k<=l} U_i(jkl) x_j x_k x_l
+                          evaluated from the input vector (simultaneous update) */
+    TRK_EDRIFT = 2,    /* exact drift (Sec. 2.1 listings): x += L x', y += L y',
+                          l += L (sqrt(1 + x'^2 + y'^2) - 1) */
+    TRK_KQUAD = 3,     /* thick quadrupole by canonical kick-drift integration,
+                          4th-order Yoshida, n_kicks steps (Table 1,
+                          multipole_tracking2; Sec. 3) */
+    TRK_KSEXT = 4,     /* thick sextupole, same integrator (k1 may be nonzero) */
+    TRK_THINSEXT = 5,  /* thin sextupole: x' -= (k2l/2)(x^2 - y^2), y' += k2l x y */
+    TRK_RFCA = 6,      /* thin RF cavity with exact phase dependence (Table 1,
+                          simple_rf_cavity): dE = V cos(phi + 2 pi f l / c),
+                          P' = P + dE, p0' = p0 + V cos(phi),
+                          delta' = P'/p0' - 1, x' and y' scaled by P/P' */
+    TRK_WAKE = 7       /* longitudinal wake (Table 1 WAKE; Sec. 2.2-2.3): l-window
+                          [min, max] over alive particles, nbins equal bins,
+                          counts h_j, V_k = -q_m sum_{j<=k} h_j W((k-j) dl) with
+                          W(s) = w0 / sqrt(max(s, s_c)), q_m = charge / n,
+                          delta += V(l) / p0c, V linearly interpolated between
+                          bin centres and clamped at the end bins */
+} trk_elem_type;
+
+typedef enum { TRK_APERTURE_NONE = 0, TRK_APERTURE_RECT = 1, TRK_APERTURE_ELLIPSE = 2 } trk_aperture;
+
+/* One element.  Map coefficient arrays are HOST pointers read (copied) by
+ * trk_create_lattice; unused fields are ignored. */
+typedef struct {
+    int32_t type;       /* trk_elem_type */
+    int32_t order;      /* TRK_MAP: 1, 2 or 3 (U ignored below 3, T below 2) */
+    int32_t n_kicks;    /* TRK_KQUAD / TRK_KSEXT: Yoshida-4 steps (>= 1) */
+    int32_t nbins;      /* TRK_WAKE: histogram bins (1 .. 65536) */
+    double length;      /* m (TRK_EDRIFT, TRK_KQUAD, TRK_KSEXT) */
+    double k1;          /* m^-2 (TRK_KQUAD, TRK_KSEXT) */
+    double k2;          /* m^-3 (TRK_KSEXT) */
+    double k2l;         /* m^-2 (TRK_THINSEXT) */
+    double volt;        /* V (TRK_RFCA) */
+    double phase_deg;   /* degrees (TRK_RFCA) */
+    double freq_hz;     /* Hz (TRK_RFCA) */
+    double wake_w0;     /* V m^1/2 / C (TRK_WAKE) */
+    double wake_sc;     /* m, saturation length s_c (TRK_WAKE) */
+    double charge;      /* C, bunch charge (TRK_WAKE) */
+    const double *C;    /* TRK_MAP: [6] or NULL (zero) */
+    const double *R;    /* TRK_MAP: [6*6] row-major */
+    const double *T;    /* TRK_MAP: [6*21], (j,k) j<=k lexicographic, or NULL */
+    const double *U;    /* TRK_MAP: [6*56], (j,k,l) j<=k<=l lexicographic, or NULL */
+} trk_element_desc;
+
+typedef struct {
+    int32_t aperture;   /* trk_aperture, checked at the exit of every element
+                           (Table 1 limit_amplitudes / RCOL / ECOL): RECT keeps
+                           |x| <= a and |y| <= b, ELLIPSE keeps
+                           (x/a)^2 + (y/b)^2 <= 1; NaN is lost */
+    int32_t moments;    /* 1: compute per-turn moments (Sec. 2.4), 0: skip */
+    double a, b;        /* aperture half-widths [m] */
+    double p0c_ev;      /* reference momentum at the lattice entrance [eV] */
+} trk_lattice_opts;
+
+typedef struct trk_lattice trk_lattice;   /* opaque, library-owned */
+typedef struct trk_bunch trk_bunch;       /* opaque view over caller arrays */
+
+/* Compile n element descriptors into a device-resident lattice.  Returns
+ * TRK_EINVAL for an unknown type, a MAP without R, order outside 1..3,
+ * n_kicks < 1, nbins outside 1..65536, or a non-positive aperture. */
+trk_status trk_create_lattice(const trk_element_desc *elems, int32_t n,
+                              const trk_lattice_opts *opts, trk_lattice **out);
+trk_status trk_destroy_lattice(trk_lattice *lat);
+
+/* Wrap caller-owned device arrays as a bunch of n alive particles.
+ *   d_coords  [6 * pitch] FP64, SoA as above, pitch >= n
+ *   d_id      [n] int32 particle ids (permuted with the coordinates)
+ *   stream    cudaStream_t (NULL = legacy default stream)
+ * Allocates library scratch (loss records, compaction buffers, partial sums)
+ * of about 80 bytes per particle.  The arrays must outlive the bunch. */
+trk_status trk_bunch_wrap(double *d_coords, int64_t pitch, int32_t *d_id, int64_t n,
+                          void *stream, trk_bunch **out);
+/* Frees the wrapper and the library scratch only (never the caller arrays). */
+trk_status trk_bunch_free(trk_bunch *b);
+
+/* Reference momentum carried by the bunch [eV]; set from the lattice at the
+ * first trk_track unless set explicitly.  trk_bunch_p0c synchronises. */
+trk_status trk_bunch_set_p0c(trk_bunch *b, double p0c_ev);
+trk_status trk_bunch_p0c(trk_bunch *b, double *p0c_ev);
+
+/* Launch schedule: threads per block (64..512, multiple of 32), particles per
+ * thread (1 or 2), turns per fused launch between compactions (>= 1).  Zero
+ * fields keep the current value. */
+typedef struct {
+    int32_t block;
+    int32_t per_thread;
+    int32_t chunk_turns;
+    int32_t pad;
+} trk_schedule;
+trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s);
+
+/* Track the alive particles n_turns turns through the lattice (Sec. 2-3):
+ * every element in order, the aperture at every element exit, moments after
+ * every turn, stable compaction of survivors after each chunk of turns.
+ * Asynchronous on the bunch's stream.  Loss records carry the absolute turn
+ * (counted over all trk_track calls of this bunch) and the element index. */
+trk_status trk_track(trk_bunch *b, const trk_lattice *lat, int32_t n_turns);
+
+/* Per-turn moments of the last trk_track call, host_out[t*28 + q]:
+ *   q = 0      number of alive particles after turn t
+ *   q = 1..6   means of the 6 coordinates
+ *   q = 7..27  population central second moments <d_j d_k>, j <= k
+ *              lexicographic (0,0) (0,1) .. (0,5) (1,1) .. (5,5)
+ * (all zero when no particle is alive).  cap_turns bounds the rows written;
+ * *n_turns receives the number of rows available.  Synchronises. */
+trk_status trk_moments(trk_bunch *b, double *host_out, int32_t cap_turns, int32_t *n_turns);
+
+/* Lost particles so far (slots [n_alive, n)): ids, absolute loss turn and
+ * element index, host arrays of capacity cap.  Synchronises. */
+trk_status trk_lost(trk_bunch *b, int32_t *ids, int32_t *turn, int32_t *elem,
+                    int64_t cap, int64_t *n_lost);
+trk_status trk_n_alive(trk_bunch *b, int64_t *n_alive);
+
+/* Standalone longitudinal wake (one TRK_WAKE element) on the alive particles
+ * of the bunch, at reference momentum p0c_ev; q_m = charge / n (n = particles
+ * wrapped).  d_hist [nbins] uint32 counts and d_volt [nbins] FP64 voltages are
+ * optional caller device outputs (NULL to skip).  Asynchronous. */
+trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc, double charge,
+                    double p0c_ev, uint32_t *d_hist, double *d_volt);
+
+/* Launch statistics of a bunch.  With timing enabled the library records CUDA
+ * events on the bunch's stream around every fused tracking launch; the summed
+ * device time of those launches is track_kernel_ms.  trk_bunch_stats
+ * synchronises; reset != 0 zeroes the counters afterwards. */
+typedef struct {
+    double track_kernel_ms;   /* device time of the fused tracking launches [ms] */
+    int64_t track_launches;   /* fused tracking launches */
+    int64_t launches;         /* all kernel launches issued for this bunch */
+} trk_stats;
+trk_status trk_bunch_enable_timing(trk_bunch *b, int32_t on);
+trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t reset);
+
+/* Text for the calling thread's last non-OK status ("" if none). */
+const char *trk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRK_H */

@@ -1,0 +1,656 @@
+// C ABI: lattice compilation, bunch scratch, and the launch schedule of
+// trk_track (fused launches per turn chunk, wake steps, moment finalisation,
+// loss compaction).  See include/trk.h for the contract of every call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "trk_internal.cuh"
+
+using namespace trk;
+
+namespace {
+
+thread_local std::string g_err;
+
+trk_status fail(trk_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define TRK_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(TRK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kClight = 299792458.0;
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+// Monomial code of (j[,k[,l]]) for a map term.
+int32_t mono_code(int deg, int j, int k, int l) { return deg | (j << 2) | (k << 5) | (l << 8); }
+
+}  // namespace
+
+struct trk_lattice {
+    std::vector<DevElem> elems;
+    std::vector<DevTerm> terms;
+    DevElem *d_elems = nullptr;
+    DevTerm *d_terms = nullptr;
+    LatticeView view{};
+    int moments = 1;
+    double p0c = 0.0;
+    std::vector<int> wakes;  // element indices of TRK_WAKE
+    int max_bins = 0;
+};
+
+struct trk_bunch {
+    double *coords = nullptr;
+    int64_t pitch = 0;
+    int32_t *ids = nullptr;
+    int64_t n = 0;
+    cudaStream_t stream = nullptr;
+    int32_t *lt = nullptr, *le = nullptr;
+    double *cb = nullptr;
+    int32_t *ib = nullptr, *ltb = nullptr, *leb = nullptr;
+    BunchState *st = nullptr;
+    int block = 128, per_thread = 1, chunk = 100;
+    int32_t *tile_alive = nullptr;
+    int64_t *tile_off = nullptr;
+    int64_t tiles_cap = 0;
+    double *partials = nullptr;
+    size_t partials_rows = 0;
+    double *moments = nullptr;
+    int moments_cap = 0, moments_turns = 0;
+    uint32_t *hist = nullptr;
+    double *wfun = nullptr, *V = nullptr;
+    int wake_cap = 0;
+    int64_t turn = 0;
+    double p0c = 0.0;
+    bool p0c_set = false;
+    // statistics
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // recorded pairs
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    int64_t track_launches = 0, launches = 0;
+    double track_ms = 0.0;
+};
+
+// Fused tracking launch with optional event timing and launch counting.
+static cudaError_t track_launch(trk_bunch *b, const TrackArgs &a, int n_tiles) {
+    std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
+    if (b->timing) {
+        if (!b->ev_free.empty()) {
+            pr = b->ev_free.back();
+            b->ev_free.pop_back();
+        } else {
+            cudaError_t e = cudaEventCreate(&pr.first);
+            if (e == cudaSuccess) e = cudaEventCreate(&pr.second);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(pr.first, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_track(a, b->block, b->per_thread, n_tiles, b->stream);
+    if (e != cudaSuccess) return e;
+    ++b->track_launches;
+    ++b->launches;
+    if (b->timing) {
+        e = cudaEventRecord(pr.second, b->stream);
+        if (e != cudaSuccess) return e;
+        b->ev.push_back(pr);
+    }
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------- lattice ----
+
+static trk_status compile_map(const trk_element_desc &d, int idx, DevElem &E, std::vector<DevTerm> &terms) {
+    if (!d.R) return fail(TRK_EINVAL, "element " + std::to_string(idx) + ": TRK_MAP needs R");
+    if (d.order < 1 || d.order > 3) return fail(TRK_EINVAL, "element " + std::to_string(idx) + ": order must be 1..3");
+    if (d.order >= 2 && !d.T) return fail(TRK_EINVAL, "element " + std::to_string(idx) + ": order >= 2 needs T");
+    if (d.order >= 3 && !d.U) return fail(TRK_EINVAL, "element " + std::to_string(idx) + ": order 3 needs U");
+    E.term0 = (int32_t)terms.size();
+    E.n = d.order;
+    E.flags = 0;
+    int pos = 0;
+    bool delta_changes = false;
+    for (int r = 0; r < 6; ++r) {
+        E.rb[r] = (int16_t)pos;
+        auto add = [&](double c, int32_t code) {
+            if (c == 0.0) return;
+            DevTerm t;
+            t.c = c;
+            t.code = code;
+            t.pad = 0;
+            terms.push_back(t);
+            ++pos;
+        };
+        if (d.R[6 * r + r] == 1.0) E.flags |= 1u << r;
+        if (d.C) add(d.C[r], mono_code(0, 0, 0, 0));
+        for (int j = 0; j < 6; ++j) {
+            if (j == r && d.R[6 * r + r] == 1.0) continue;
+            add(d.R[6 * r + j], mono_code(1, j, 0, 0));
+        }
+        if (d.order >= 2) {
+            int q = 0;
+            for (int j = 0; j < 6; ++j)
+                for (int k = j; k < 6; ++k, ++q) add(d.T[21 * r + q], mono_code(2, j, k, 0));
+        }
+        if (d.order >= 3) {
+            int q = 0;
+            for (int j = 0; j < 6; ++j)
+                for (int k = j; k < 6; ++k)
+                    for (int l = k; l < 6; ++l, ++q) add(d.U[56 * r + q], mono_code(3, j, k, l));
+        }
+        if (r == 5 && (pos > E.rb[5] || !(E.flags & 32u))) delta_changes = true;
+        if (pos > 32000) return fail(TRK_EINVAL, "element " + std::to_string(idx) + ": too many map terms");
+    }
+    E.rb[6] = (int16_t)pos;
+    E.rb[7] = (int16_t)pos;
+    if (delta_changes) E.flags |= 64u;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t n, const trk_lattice_opts *opts,
+                                         trk_lattice **out) {
+    if (!out) return fail(TRK_EINVAL, "trk_create_lattice: out is NULL");
+    *out = nullptr;
+    if (!opts) return fail(TRK_EINVAL, "trk_create_lattice: opts is NULL");
+    if (n < 0 || (n > 0 && !elems)) return fail(TRK_EINVAL, "trk_create_lattice: bad element array");
+    if (!(opts->p0c_ev > 0.0)) return fail(TRK_EINVAL, "trk_create_lattice: p0c_ev must be > 0");
+    if (opts->aperture != TRK_APERTURE_NONE && opts->aperture != TRK_APERTURE_RECT &&
+        opts->aperture != TRK_APERTURE_ELLIPSE)
+        return fail(TRK_EINVAL, "trk_create_lattice: unknown aperture type");
+    if (opts->aperture != TRK_APERTURE_NONE && !(opts->a > 0.0 && opts->b > 0.0))
+        return fail(TRK_EINVAL, "trk_create_lattice: aperture half-widths must be > 0");
+    auto *L = new trk_lattice();
+    L->moments = opts->moments ? 1 : 0;
+    L->p0c = opts->p0c_ev;
+    const double w1 = 1.0 / (2.0 - std::cbrt(2.0));
+    const double w0 = 1.0 - 2.0 * w1;
+    for (int i = 0; i < n; ++i) {
+        const trk_element_desc &d = elems[i];
+        DevElem E;
+        std::memset(&E, 0, sizeof E);
+        E.type = d.type;
+        trk_status s = TRK_OK;
+        switch (d.type) {
+        case TRK_MAP: s = compile_map(d, i, E, L->terms); break;
+        case TRK_EDRIFT:
+            if (!std::isfinite(d.length)) s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": bad length");
+            E.p[0] = d.length;
+            break;
+        case TRK_KQUAD:
+        case TRK_KSEXT: {
+            if (d.n_kicks < 1) {
+                s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": n_kicks must be >= 1");
+                break;
+            }
+            const double k2 = d.type == TRK_KSEXT ? d.k2 : 0.0;
+            const double h = d.length / d.n_kicks;
+            E.n = d.n_kicks;
+            E.p[0] = 0.5 * w1 * h;
+            E.p[1] = 0.5 * (w0 + w1) * h;
+            E.p[2] = w1 * h;
+            E.p[3] = d.k1 * (w1 * h);
+            E.p[4] = d.k1 * (w0 * h);
+            E.p[5] = (0.5 * k2) * (w1 * h);
+            E.p[6] = (0.5 * k2) * (w0 * h);
+            E.p[7] = k2 * (w1 * h);
+            E.p[8] = k2 * (w0 * h);
+            E.flags = (d.k1 != 0.0 ? 1u : 0u) | (k2 != 0.0 ? 2u : 0u);
+            break;
+        }
+        case TRK_THINSEXT:
+            E.p[0] = d.k2l;
+            E.p[1] = 0.5 * d.k2l;
+            break;
+        case TRK_RFCA: {
+            const double phi = d.phase_deg * kPi / 180.0;
+            E.p[0] = d.volt;
+            E.p[1] = phi;
+            E.p[2] = 2.0 * kPi * d.freq_hz / kClight;
+            E.p[3] = d.volt * std::cos(phi);
+            break;
+        }
+        case TRK_WAKE:
+            if (d.nbins < 1 || d.nbins > kMaxBins) {
+                s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": nbins must be 1..65536");
+                break;
+            }
+            E.n = d.nbins;
+            E.term0 = (int32_t)L->wakes.size();
+            E.p[0] = d.wake_w0;
+            E.p[1] = d.wake_sc;
+            E.p[2] = d.charge;
+            L->wakes.push_back(i);
+            if (d.nbins > L->max_bins) L->max_bins = d.nbins;
+            break;
+        default: s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": unknown type " + std::to_string(d.type));
+        }
+        if (s != TRK_OK) {
+            delete L;
+            return s;
+        }
+        L->elems.push_back(E);
+    }
+    cudaError_t e1 = dalloc(&L->d_elems, L->elems.size());
+    cudaError_t e2 = dalloc(&L->d_terms, L->terms.size());
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaFree(L->d_elems);
+        cudaFree(L->d_terms);
+        delete L;
+        return fail(TRK_ENOMEM, "trk_create_lattice: device allocation failed");
+    }
+    cudaError_t e3 = cudaMemcpy(L->d_elems, L->elems.data(), L->elems.size() * sizeof(DevElem), cudaMemcpyHostToDevice);
+    cudaError_t e4 = L->terms.empty() ? cudaSuccess
+                                      : cudaMemcpy(L->d_terms, L->terms.data(), L->terms.size() * sizeof(DevTerm),
+                                                   cudaMemcpyHostToDevice);
+    if (e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaFree(L->d_elems);
+        cudaFree(L->d_terms);
+        delete L;
+        return fail(TRK_ECUDA, "trk_create_lattice: copy to device failed");
+    }
+    LatticeView &v = L->view;
+    v.elems = L->d_elems;
+    v.terms = L->d_terms;
+    v.n_elem = n;
+    v.ap_type = opts->aperture;
+    v.ap_a = opts->a;
+    v.ap_b = opts->b;
+    std::memcpy(&v.ap_a_bits, &opts->a, 8);
+    std::memcpy(&v.ap_b_bits, &opts->b, 8);
+    v.ap_ia2f = opts->aperture == TRK_APERTURE_ELLIPSE ? (float)(1.0 / (opts->a * opts->a)) : 0.0f;
+    v.ap_ib2f = opts->aperture == TRK_APERTURE_ELLIPSE ? (float)(1.0 / (opts->b * opts->b)) : 0.0f;
+    *out = L;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_destroy_lattice(trk_lattice *L) {
+    if (!L) return TRK_OK;
+    cudaFree(L->d_elems);
+    cudaFree(L->d_terms);
+    delete L;
+    return TRK_OK;
+}
+
+// --------------------------------------------------------------- bunch ----
+
+static void free_bunch_scratch(trk_bunch *b) {
+    for (auto &pr : b->ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto &pr : b->ev_free) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    b->ev.clear();
+    b->ev_free.clear();
+    cudaFree(b->lt);
+    cudaFree(b->le);
+    cudaFree(b->cb);
+    cudaFree(b->ib);
+    cudaFree(b->ltb);
+    cudaFree(b->leb);
+    cudaFree(b->st);
+    cudaFree(b->tile_alive);
+    cudaFree(b->tile_off);
+    cudaFree(b->partials);
+    cudaFree(b->moments);
+    cudaFree(b->hist);
+    cudaFree(b->wfun);
+    cudaFree(b->V);
+}
+
+extern "C" trk_status trk_bunch_wrap(double *d_coords, int64_t pitch, int32_t *d_id, int64_t n, void *stream,
+                                     trk_bunch **out) {
+    if (!out) return fail(TRK_EINVAL, "trk_bunch_wrap: out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > 0x7fffffffll) return fail(TRK_EINVAL, "trk_bunch_wrap: n must be 0 .. 2^31-1");
+    if (pitch < n) return fail(TRK_EINVAL, "trk_bunch_wrap: pitch < n");
+    if (n > 0 && (!d_coords || !d_id)) return fail(TRK_EINVAL, "trk_bunch_wrap: NULL array");
+    if (((uintptr_t)d_coords & 15u) != 0) return fail(TRK_EINVAL, "trk_bunch_wrap: coords not 16-byte aligned");
+    auto *b = new trk_bunch();
+    b->coords = d_coords;
+    b->pitch = pitch;
+    b->ids = d_id;
+    b->n = n;
+    b->stream = (cudaStream_t)stream;
+    const int64_t tiles = (n + 63) / 64 + 1;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&b->lt, n);
+    if (e == cudaSuccess) e = dalloc(&b->le, n);
+    if (e == cudaSuccess) e = dalloc(&b->cb, 6 * (size_t)pitch);
+    if (e == cudaSuccess) e = dalloc(&b->ib, n);
+    if (e == cudaSuccess) e = dalloc(&b->ltb, n);
+    if (e == cudaSuccess) e = dalloc(&b->leb, n);
+    if (e == cudaSuccess) e = dalloc(&b->st, 1);
+    if (e == cudaSuccess) e = dalloc(&b->tile_alive, tiles);
+    if (e == cudaSuccess) e = dalloc(&b->tile_off, tiles);
+    if (e != cudaSuccess) {
+        free_bunch_scratch(b);
+        delete b;
+        return fail(TRK_ENOMEM, std::string("trk_bunch_wrap: device allocation failed: ") + cudaGetErrorString(e));
+    }
+    b->tiles_cap = tiles;
+    e = launch_init_bunch(b->st, b->lt, b->le, n, b->stream);
+    if (e != cudaSuccess) {
+        free_bunch_scratch(b);
+        delete b;
+        return fail(TRK_ECUDA, std::string("trk_bunch_wrap: init failed: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_free(trk_bunch *b) {
+    if (!b) return TRK_OK;
+    cudaStreamSynchronize(b->stream);
+    free_bunch_scratch(b);
+    delete b;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_set_p0c(trk_bunch *b, double p0c) {
+    if (!b || !(p0c > 0.0)) return fail(TRK_EINVAL, "trk_bunch_set_p0c: bad argument");
+    b->p0c = p0c;
+    b->p0c_set = true;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_p0c(trk_bunch *b, double *p0c) {
+    if (!b || !p0c) return fail(TRK_EINVAL, "trk_bunch_p0c: bad argument");
+    TRK_CUDA(cudaStreamSynchronize(b->stream));
+    *p0c = b->p0c_set ? b->p0c : 0.0;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s) {
+    if (!b || !s) return fail(TRK_EINVAL, "trk_bunch_set_schedule: NULL argument");
+    if (s->block && (s->block < 64 || s->block > 256 || s->block % 32))
+        return fail(TRK_EINVAL, "trk_bunch_set_schedule: block must be 64..256, a multiple of 32");
+    if (s->per_thread && s->per_thread != 1 && s->per_thread != 2)
+        return fail(TRK_EINVAL, "trk_bunch_set_schedule: per_thread must be 1 or 2");
+    if (s->chunk_turns < 0) return fail(TRK_EINVAL, "trk_bunch_set_schedule: chunk_turns must be >= 0");
+    if (s->block) b->block = s->block;
+    if (s->per_thread) b->per_thread = s->per_thread;
+    if (s->chunk_turns) b->chunk = s->chunk_turns;
+    return TRK_OK;
+}
+
+// ------------------------------------------------------------ tracking ----
+
+static trk_status ensure_moments(trk_bunch *b, int n_turns, int n_tiles, int chunk) {
+    if (n_turns > b->moments_cap) {
+        cudaFree(b->moments);
+        b->moments = nullptr;
+        b->moments_cap = 0;
+        if (dalloc(&b->moments, (size_t)n_turns * kMomentsN) != cudaSuccess)
+            return fail(TRK_ENOMEM, "trk_track: moments allocation failed");
+        b->moments_cap = n_turns;
+    }
+    const size_t rows = (size_t)chunk * n_tiles;
+    if (rows > b->partials_rows) {
+        cudaFree(b->partials);
+        b->partials = nullptr;
+        b->partials_rows = 0;
+        if (dalloc(&b->partials, rows * kMomentsN) != cudaSuccess)
+            return fail(TRK_ENOMEM, "trk_track: partial-sum allocation failed");
+        b->partials_rows = rows;
+    }
+    return TRK_OK;
+}
+
+static trk_status ensure_wake(trk_bunch *b, int nbins) {
+    if (nbins <= b->wake_cap) return TRK_OK;
+    cudaFree(b->hist);
+    cudaFree(b->wfun);
+    cudaFree(b->V);
+    b->hist = nullptr;
+    b->wfun = b->V = nullptr;
+    b->wake_cap = 0;
+    if (dalloc(&b->hist, nbins) != cudaSuccess || dalloc(&b->wfun, nbins) != cudaSuccess ||
+        dalloc(&b->V, nbins) != cudaSuccess)
+        return fail(TRK_ENOMEM, "wake scratch allocation failed");
+    b->wake_cap = nbins;
+    return TRK_OK;
+}
+
+// p0 after elements [e0, e1) starting from p0 (same additions as the kernel).
+static double advance_p0(const trk_lattice *L, int e0, int e1, double p0) {
+    for (int e = e0; e < e1; ++e)
+        if (L->elems[e].type == TRK_RFCA) p0 = p0 + L->elems[e].p[3];
+    return p0;
+}
+
+static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
+    TrackArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.coords = b->coords;
+    a.pitch = b->pitch;
+    a.loss_turn = b->lt;
+    a.loss_elem = b->le;
+    a.st = b->st;
+    a.lat = L->view;
+    a.n_tiles = n_tiles;
+    a.partials = b->partials;
+    a.tile_alive = b->tile_alive;
+    a.kick_wake = -1;
+    a.minmax_slot = -1;
+    a.wake_V = b->V;
+    return a;
+}
+
+extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_turns) {
+    if (!b || !L) return fail(TRK_EINVAL, "trk_track: NULL bunch or lattice");
+    if (n_turns < 0) return fail(TRK_EINVAL, "trk_track: n_turns < 0");
+    if (b->turn + n_turns > 0x7fffffffll) return fail(TRK_EINVAL, "trk_track: turn counter overflow");
+    if (!b->p0c_set) {
+        b->p0c = L->p0c;
+        b->p0c_set = true;
+    }
+    b->moments_turns = 0;
+    if (n_turns == 0 || b->n == 0) {
+        b->turn += n_turns;
+        return TRK_OK;
+    }
+    const int tile = b->block * b->per_thread;
+    const int n_tiles = (int)((b->n + tile - 1) / tile);
+    const bool wakes = !L->wakes.empty();
+    const int chunk = b->chunk < n_turns ? b->chunk : n_turns;
+    if (L->moments) {
+        trk_status s = ensure_moments(b, n_turns, n_tiles, chunk);
+        if (s != TRK_OK) return s;
+    }
+    if (wakes) {
+        trk_status s = ensure_wake(b, L->max_bins);
+        if (s != TRK_OK) return s;
+    }
+    const int ne = L->view.n_elem;
+    const double qm_base = 1.0 / (double)b->n;
+    for (int t0 = 0; t0 < n_turns; t0 += chunk) {
+        const int nt = chunk < n_turns - t0 ? chunk : n_turns - t0;
+        TrackArgs a = base_args(b, L, n_tiles);
+        if (!wakes) {
+            a.e0 = 0;
+            a.e1 = ne;
+            a.n_turns = nt;
+            a.turn_abs0 = (int32_t)(b->turn + t0);
+            a.local_turn0 = 0;
+            a.do_moments = L->moments;
+            a.p0c = b->p0c;
+            TRK_CUDA(track_launch(b, a, n_tiles));
+            for (int t = 0; t < nt; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
+        } else {
+            const int nw = (int)L->wakes.size();
+            for (int t = 0; t < nt; ++t) {
+                int e_start = 0, prev_wake = -1, prev_slot = 0;
+                double p0 = b->p0c;
+                for (int s = 0; s <= nw; ++s) {
+                    const int e_end = s < nw ? L->wakes[s] : ne;
+                    const int slot = s & 1;
+                    TrackArgs g = a;
+                    g.e0 = e_start;
+                    g.e1 = e_end;
+                    g.n_turns = 1;
+                    g.turn_abs0 = (int32_t)(b->turn + t0 + t);
+                    g.local_turn0 = t;
+                    g.kick_wake = prev_wake;
+                    g.kick_slot = prev_slot;
+                    g.wake_nbins = prev_wake >= 0 ? L->elems[prev_wake].n : 0;
+                    g.minmax_slot = s < nw ? slot : -1;
+                    g.do_moments = L->moments && s == nw;
+                    g.p0c = p0;
+                    if (s < nw) {
+                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist, L->elems[e_end].n, b->stream));
+                        ++b->launches;
+                    }
+                    TRK_CUDA(track_launch(b, g, n_tiles));
+                    p0 = advance_p0(L, e_start, e_end, p0);
+                    if (s < nw) {
+                        const DevElem &W = L->elems[e_end];
+                        TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, W.p[0], W.p[1],
+                                                  b->hist, b->wfun, b->n, b->stream));
+                        TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, b->V, b->stream));
+                        b->launches += 2;
+                    }
+                    prev_wake = e_end;
+                    prev_slot = slot;
+                    e_start = e_end + 1;
+                }
+                b->p0c = p0;
+            }
+        }
+        if (L->moments) {
+            TRK_CUDA(launch_moments_finalize(b->partials, n_tiles, nt, b->st, tile,
+                                             b->moments + (size_t)t0 * kMomentsN, b->stream));
+            ++b->launches;
+        }
+        TRK_CUDA(launch_compact(b->coords, b->pitch, b->ids, b->lt, b->le, b->cb, b->ib, b->ltb, b->leb,
+                                b->tile_alive, b->tile_off, n_tiles, tile, b->st, b->stream));
+        b->launches += 4;
+    }
+    b->turn += n_turns;
+    b->moments_turns = L->moments ? n_turns : 0;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_moments(trk_bunch *b, double *host_out, int32_t cap_turns, int32_t *n_turns) {
+    if (!b) return fail(TRK_EINVAL, "trk_moments: NULL bunch");
+    TRK_CUDA(cudaStreamSynchronize(b->stream));
+    if (n_turns) *n_turns = b->moments_turns;
+    const int rows = cap_turns < b->moments_turns ? cap_turns : b->moments_turns;
+    if (rows > 0) {
+        if (!host_out) return fail(TRK_EINVAL, "trk_moments: NULL output");
+        TRK_CUDA(cudaMemcpy(host_out, b->moments, (size_t)rows * kMomentsN * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_n_alive(trk_bunch *b, int64_t *n_alive) {
+    if (!b || !n_alive) return fail(TRK_EINVAL, "trk_n_alive: NULL argument");
+    TRK_CUDA(cudaStreamSynchronize(b->stream));
+    BunchState st;
+    TRK_CUDA(cudaMemcpy(&st, b->st, sizeof st, cudaMemcpyDeviceToHost));
+    *n_alive = st.n_alive;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_lost(trk_bunch *b, int32_t *ids, int32_t *turn, int32_t *elem, int64_t cap,
+                               int64_t *n_lost) {
+    if (!b || !n_lost) return fail(TRK_EINVAL, "trk_lost: NULL argument");
+    int64_t na = 0;
+    trk_status s = trk_n_alive(b, &na);
+    if (s != TRK_OK) return s;
+    *n_lost = b->n - na;
+    const int64_t m = cap < *n_lost ? cap : *n_lost;
+    if (m > 0) {
+        if (!ids || !turn || !elem) return fail(TRK_EINVAL, "trk_lost: NULL output");
+        TRK_CUDA(cudaMemcpy(ids, b->ids + na, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        TRK_CUDA(cudaMemcpy(turn, b->lt + na, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        TRK_CUDA(cudaMemcpy(elem, b->le + na, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc, double charge, double p0c_ev,
+                               uint32_t *d_hist, double *d_volt) {
+    if (!b) return fail(TRK_EINVAL, "trk_wake: NULL bunch");
+    if (nbins < 1 || nbins > kMaxBins) return fail(TRK_EINVAL, "trk_wake: nbins must be 1..65536");
+    if (!(p0c_ev > 0.0)) return fail(TRK_EINVAL, "trk_wake: p0c_ev must be > 0");
+    if (b->n == 0) return TRK_OK;
+    trk_status s = ensure_wake(b, nbins);
+    if (s != TRK_OK) return s;
+    TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nbins, b->stream));
+    TRK_CUDA(launch_wake_minmax(b->coords, b->pitch, b->lt, b->st, 0, b->n, b->stream));
+    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, 0, nbins, w0, sc, b->hist, b->wfun, b->n,
+                              b->stream));
+    TRK_CUDA(launch_wake_conv(b->hist, b->wfun, nbins, charge / (double)b->n, b->V, b->stream));
+    const int tile = b->block * b->per_thread;
+    const int n_tiles = (int)((b->n + tile - 1) / tile);
+    TrackArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.coords = b->coords;
+    a.pitch = b->pitch;
+    a.loss_turn = b->lt;
+    a.loss_elem = b->le;
+    a.st = b->st;
+    a.lat.ap_type = TRK_APERTURE_NONE;
+    a.e0 = a.e1 = 0;
+    a.n_turns = 1;
+    a.turn_abs0 = (int32_t)b->turn;
+    a.kick_wake = 0;
+    a.kick_slot = 0;
+    a.minmax_slot = -1;
+    a.p0c = p0c_ev;
+    a.wake_V = b->V;
+    a.wake_nbins = nbins;
+    TRK_CUDA(track_launch(b, a, n_tiles));
+    b->launches += 4;
+    if (d_hist)
+        TRK_CUDA(cudaMemcpyAsync(d_hist, b->hist, nbins * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b->stream));
+    if (d_volt)
+        TRK_CUDA(cudaMemcpyAsync(d_volt, b->V, nbins * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_enable_timing(trk_bunch *b, int32_t on) {
+    if (!b) return fail(TRK_EINVAL, "trk_bunch_enable_timing: NULL bunch");
+    b->timing = on != 0;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t reset) {
+    if (!b || !out) return fail(TRK_EINVAL, "trk_bunch_stats: NULL argument");
+    TRK_CUDA(cudaStreamSynchronize(b->stream));
+    for (auto &pr : b->ev) {
+        float ms = 0.0f;
+        TRK_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        b->track_ms += ms;
+        b->ev_free.push_back(pr);
+    }
+    b->ev.clear();
+    out->track_kernel_ms = b->track_ms;
+    out->track_launches = b->track_launches;
+    out->launches = b->launches;
+    if (reset) {
+        b->track_ms = 0.0;
+        b->track_launches = 0;
+        b->launches = 0;
+    }
+    return TRK_OK;
+}
+
+extern "C" const char *trk_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,125 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trk.h"
+
+namespace trk {
+
+constexpr int kMaxBins = 65536;
+constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
+
+// Device element record (128 bytes, read warp-uniformly).
+//   KQUAD/KSEXT  p[0] d1 = w1 h / 2     p[1] d2 = (w0 + w1) h / 2   p[2] dm = w1 h
+//                p[3] a1 = K1 w1 h       p[4] a0 = K1 w0 h
+//                p[5] hb1 = K2 w1 h / 2  p[6] hb0 = K2 w0 h / 2
+//                p[7] b1 = K2 w1 h       p[8] b0 = K2 w0 h
+//                n = steps; flags bit0 = has K1, bit1 = has K2
+//   EDRIFT       p[0] L
+//   THINSEXT     p[0] K2L, p[1] K2L / 2
+//   RFCA         p[0] V, p[1] phi [rad], p[2] k_rf = 2 pi f / c, p[3] G = V cos(phi)
+//   WAKE         p[0] W0, p[1] s_c, p[2] charge; n = nbins; term0 = wake ordinal
+//   MAP          term0 = first term; rb[r]..rb[r+1] = terms of output row r;
+//                flags bit r (r < 6) = row r starts from x_r (R_rr == 1 folded);
+//                flags bit 6 = row 5 (delta) changes
+struct alignas(16) DevElem {
+    int32_t type;
+    int32_t n;
+    int32_t term0;
+    uint32_t flags;
+    int16_t rb[8];
+    double p[12];
+};
+static_assert(sizeof(DevElem) == 128, "DevElem layout");
+
+// One map term: coefficient and monomial code deg | j << 2 | k << 5 | l << 8.
+struct alignas(16) DevTerm {
+    double c;
+    int32_t code;
+    int32_t pad;
+};
+
+struct LatticeView {
+    const DevElem *elems;
+    const DevTerm *terms;
+    int32_t n_elem;
+    int32_t ap_type;
+    double ap_a, ap_b;
+    long long ap_a_bits, ap_b_bits;   // bit patterns of a, b (> 0): |x| <= a as integers
+    float ap_ia2f, ap_ib2f;           // 1/a^2, 1/b^2 for the FP32 ellipse pre-filter
+};
+
+// Device-resident bunch state.
+struct BunchState {
+    int64_t n_alive;        // alive particles occupy [0, n_alive)
+    int64_t n_alive_next;   // result of the pending compaction
+    uint64_t lkey[4];       // l min/max order keys, two wake slots: [2s] min, [2s+1] max
+    int32_t error;
+    int32_t pad;
+};
+
+// Arguments of one fused tracking launch over elements [e0, e1).
+struct TrackArgs {
+    double *coords;
+    int64_t pitch;
+    int32_t *loss_turn;     // -1 = alive
+    int32_t *loss_elem;
+    BunchState *st;
+    LatticeView lat;
+    int32_t e0, e1;
+    int32_t n_turns;        // > 1 only when [e0, e1) is the whole lattice
+    int32_t turn_abs0;      // absolute turn number of the first turn
+    int32_t local_turn0;    // row of the first turn in the partial-sum buffer
+    int32_t kick_wake;      // element index of a wake to kick with first, or -1
+    int32_t kick_slot;      // its key slot
+    int32_t minmax_slot;    // key slot to fill with l min/max at the end, or -1
+    int32_t do_moments;     // per-turn moments at the end of each turn
+    int32_t n_tiles;        // stride of the partial-sum rows
+    double p0c;             // reference momentum at element e0 [eV]
+    double *partials;       // [turn][tile][28]
+    int32_t *tile_alive;    // alive count per tile at the end (may be null)
+    const double *wake_V;   // voltages of the kicking wake
+    int32_t wake_nbins;
+};
+
+// Launchers (trk_track.cu / trk_wake.cu); all asynchronous on `s`.
+cudaError_t launch_track(const TrackArgs &a, int block, int per_thread, int n_tiles, cudaStream_t s);
+cudaError_t launch_moments_finalize(const double *partials, int n_tiles, int n_turns, const BunchState *st,
+                                    int tile, double *out, cudaStream_t s);
+cudaError_t launch_compact(double *coords, int64_t pitch, int32_t *ids, int32_t *lt, int32_t *le,
+                           double *coords_b, int32_t *ids_b, int32_t *lt_b, int32_t *le_b,
+                           const int32_t *tile_alive, int64_t *tile_off, int n_tiles, int tile,
+                           BunchState *st, cudaStream_t s);
+cudaError_t launch_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n, cudaStream_t s);
+cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, int nbins, cudaStream_t s);
+cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
+                               int slot, int64_t n_max, cudaStream_t s);
+cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot, int nbins,
+                             double w0, double sc, uint32_t *hist, double *wfun, int64_t n_max, cudaStream_t s);
+cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
+                             cudaStream_t s);
+
+// Order-preserving 64-bit key of a double (non-NaN) and its inverse.
+__host__ __device__ inline uint64_t dkey(double v) {
+#ifdef __CUDA_ARCH__
+    uint64_t b = (uint64_t)__double_as_longlong(v);
+#else
+    uint64_t b;
+    __builtin_memcpy(&b, &v, 8);
+#endif
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double dkey_inv(uint64_t k) {
+    uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double v;
+    __builtin_memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
+}  // namespace trk

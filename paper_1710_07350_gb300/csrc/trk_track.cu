@@ -1,0 +1,691 @@
+// Fused FP64 tracking kernel, per-turn moment partials, moment finalisation and
+// stable loss compaction.
+//
+// Design (GB300, FP64-pipe bound): one launch pushes a tile of particles
+// through many consecutive elements and turns with the 6 coordinates held in
+// registers (the paper's particle accessor keeps one read/write per coordinate
+// per element kernel, Sec. 2.1; here it is one per launch).  Element records
+// are read warp-uniformly.  Square roots and divisions of the exact drift and
+// the slope/canonical conversions are replaced, for the small arguments that
+// occur in practice, by truncated binomial series that agree with the exact
+// expressions to FP64 rounding (the exact path runs otherwise); aperture tests
+// run on integer bit patterns or an FP32 pre-filter with an FP64 fallback near
+// the edge, so they cost no FP64 instructions.
+#include <cmath>
+
+#include "trk_internal.cuh"
+
+namespace trk {
+namespace {
+
+// Series are used below this argument: the first dropped binomial term is
+// then below 4e-18 relative.
+constexpr float kSeriesMax = 6.103515625e-05f;  // 2^-14
+
+__device__ __forceinline__ bool series_ok(double v) { return __double2float_rz(v) < kSeriesMax; }
+
+struct Part {
+    double x, xp, y, yp, l, d;
+};
+
+__device__ __forceinline__ double pget(const Part &q, int j) {
+    double r = q.x;
+    r = (j == 1) ? q.xp : r;
+    r = (j == 2) ? q.y : r;
+    r = (j == 3) ? q.yp : r;
+    r = (j == 4) ? q.l : r;
+    r = (j == 5) ? q.d : r;
+    return r;
+}
+
+__device__ __forceinline__ DevElem load_elem(const DevElem *p) {
+    DevElem e;
+    const int4 *src = reinterpret_cast<const int4 *>(p);
+    int4 *dst = reinterpret_cast<int4 *>(&e);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i] = __ldg(src + i);
+    return e;
+}
+
+// ---------------------------------------------------------------- map ----
+// x_i <- C_i + R x + T x x + U x x x from the input vector (simultaneous).
+__device__ __forceinline__ void apply_map(Part &q, const DevElem &E, const DevTerm *__restrict__ terms,
+                                          bool &dirty) {
+    const Part in = q;
+    const double2 *t = reinterpret_cast<const double2 *>(terms + E.term0);
+    double out[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        double acc = ((E.flags >> r) & 1u) ? pget(in, r) : 0.0;
+        const int kb = E.rb[r], ke = E.rb[r + 1];
+        for (int k = kb; k < ke; ++k) {
+            const double2 tv = __ldg(t + k);
+            const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
+            const int deg = code & 3;
+            double m = 1.0;
+            if (deg >= 1) m = pget(in, (code >> 2) & 7);
+            if (deg >= 2) m *= pget(in, (code >> 5) & 7);
+            if (deg >= 3) m *= pget(in, (code >> 8) & 7);
+            acc = fma(tv.x, m, acc);
+        }
+        out[r] = acc;
+    }
+    q.x = out[0]; q.xp = out[1]; q.y = out[2]; q.yp = out[3]; q.l = out[4]; q.d = out[5];
+    if (E.flags & 64u) dirty = true;
+}
+
+// -------------------------------------------------------- exact drift ----
+// x += L x', y += L y', l += L (sqrt(1 + v) - 1), v = x'^2 + y'^2.
+__device__ __forceinline__ void edrift(Part &q, double L) {
+    q.x = fma(L, q.xp, q.x);
+    q.y = fma(L, q.yp, q.y);
+    const double v = fma(q.xp, q.xp, q.yp * q.yp);
+    double g;
+    if (series_ok(v)) {
+        // sqrt(1+v) - 1 = v/2 - v^2/8 + v^3/16 - 5 v^4/128 + ...
+        g = v * fma(v, fma(v, fma(v, -0.0390625, 0.0625), -0.125), 0.5);
+    } else {
+        g = v / (sqrt(1.0 + v) + 1.0);
+    }
+    q.l = fma(L, g, q.l);
+}
+
+// ------------------------------------------------ kick-drift multipole ----
+// Exact-Hamiltonian drift in canonical momenta: pz = P sqrt(1 - u),
+// u = (px^2 + py^2)/P^2, so h/pz = (h/P)(1 + g) and h (P/pz - 1) = h g with
+// g = (1 - u)^(-1/2) - 1 = u/2 + 3u^2/8 + 5u^3/16 + ...
+__device__ __forceinline__ void drift_c(double &x, double &y, double &l, double px, double py, double P,
+                                        double iP2, double h, double hiP) {
+    const double u = fma(px, px, py * py) * iP2;
+    double t;
+    if (series_ok(u)) {
+        const double g = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
+        l = fma(h, g, l);
+        t = fma(hiP, g, hiP);
+    } else {
+        const double r = rsqrt(fma(-px, px, fma(-py, py, P * P)));
+        t = h * r;
+        l = fma(t, P, l - h);
+    }
+    x = fma(t, px, x);
+    y = fma(t, py, y);
+}
+
+__device__ __forceinline__ void kick_c(double x, double y, double &px, double &py, uint32_t fl, double a,
+                                       double hb, double b) {
+    if (fl & 1u) {
+        px = fma(-a, x, px);
+        py = fma(a, y, py);
+    }
+    if (fl & 2u) {
+        const double t = (x - y) * (x + y);
+        px = fma(-hb, t, px);
+        py = fma(b, x * y, py);
+    }
+}
+
+// n steps of the 4th-order Yoshida scheme D K D K D K D with adjacent drifts of
+// consecutive steps merged; slopes converted to canonical momenta at entry and
+// back at exit.
+__device__ __forceinline__ void kick_drift(Part &q, double &iP, bool &dirty, const DevElem &E) {
+    const double P = 1.0 + q.d;
+    if (dirty) {
+        iP = 1.0 / P;
+        dirty = false;
+    }
+    const double iP2 = iP * iP;
+    const double v = fma(q.xp, q.xp, q.yp * q.yp);
+    // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
+    const double c = series_ok(v) ? fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0) : rsqrt(1.0 + v);
+    const double pc = P * c;
+    double px = pc * q.xp, py = pc * q.yp;
+    double x = q.x, y = q.y, l = q.l;
+    const double d1 = E.p[0], d2 = E.p[1], dm = E.p[2];
+    const double hd1 = d1 * iP, hd2 = d2 * iP, hdm = dm * iP;
+    const uint32_t fl = E.flags;
+    drift_c(x, y, l, px, py, P, iP2, d1, hd1);
+    for (int s = 0; s < E.n; ++s) {
+        kick_c(x, y, px, py, fl, E.p[3], E.p[5], E.p[7]);
+        drift_c(x, y, l, px, py, P, iP2, d2, hd2);
+        kick_c(x, y, px, py, fl, E.p[4], E.p[6], E.p[8]);
+        drift_c(x, y, l, px, py, P, iP2, d2, hd2);
+        kick_c(x, y, px, py, fl, E.p[3], E.p[5], E.p[7]);
+        if (s + 1 < E.n)
+            drift_c(x, y, l, px, py, P, iP2, dm, hdm);
+        else
+            drift_c(x, y, l, px, py, P, iP2, d1, hd1);
+    }
+    const double u = fma(px, px, py * py) * iP2;
+    const double ipz = series_ok(u) ? fma(iP, u * fma(u, fma(u, 0.3125, 0.375), 0.5), iP)
+                                    : rsqrt(fma(-px, px, fma(-py, py, P * P)));
+    q.x = x; q.y = y; q.l = l;
+    q.xp = px * ipz;
+    q.yp = py * ipz;
+}
+
+__device__ __forceinline__ void thin_sext(Part &q, const DevElem &E) {
+    const double t = (q.x - q.y) * (q.x + q.y);
+    q.xp = fma(-E.p[1], t, q.xp);
+    q.yp = fma(E.p[0], q.x * q.y, q.yp);
+}
+
+// Thin RF: P = (1+delta) p0, P' = P + V cos(phi + k l), delta' = P'/p0' - 1,
+// slopes scaled by P/P'.
+__device__ __forceinline__ void rfca(Part &q, const DevElem &E, double p0, double ip01, bool &dirty) {
+    const double P = (1.0 + q.d) * p0;
+    const double P1 = fma(E.p[0], cos(fma(E.p[2], q.l, E.p[1])), P);
+    const double s = P / P1;
+    q.xp *= s;
+    q.yp *= s;
+    q.d = fma(P1, ip01, -1.0);
+    dirty = true;
+}
+
+// Wake voltage at l: linear interpolation between bin centres, clamped.
+__device__ __forceinline__ double wake_volt(double l, double lmin, double idl, bool flat,
+                                            const double *__restrict__ V, int nb) {
+    if (flat) return __ldg(V);
+    const double u = fma(l - lmin, idl, -0.5);
+    const double k0 = floor(u);
+    if (!(k0 >= 0.0)) return __ldg(V);
+    if (k0 >= (double)(nb - 1)) return __ldg(V + nb - 1);
+    const int k = (int)k0;
+    const double f = u - k0;
+    const double v0 = __ldg(V + k), v1 = __ldg(V + k + 1);
+    return fma(f, v1 - v0, v0);
+}
+
+// Aperture: edge counts as inside, NaN as outside.
+__device__ __forceinline__ bool inside(const Part &q, const LatticeView &L) {
+    if (L.ap_type == TRK_APERTURE_RECT) {
+        const long long ax = __double_as_longlong(q.x) & 0x7fffffffffffffffll;
+        const long long ay = __double_as_longlong(q.y) & 0x7fffffffffffffffll;
+        return (ax <= L.ap_a_bits) & (ay <= L.ap_b_bits);
+    }
+    if (L.ap_type == TRK_APERTURE_ELLIPSE) {
+        const float xf = __double2float_rn(q.x), yf = __double2float_rn(q.y);
+        const float r = xf * xf * L.ap_ia2f + yf * yf * L.ap_ib2f;
+        if (r < 0.9999f) return true;
+        if (r > 1.0001f) return false;
+        const double u = __ddiv_rn(q.x, L.ap_a), v = __ddiv_rn(q.y, L.ap_b);
+        return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
+    }
+    return true;
+}
+
+// -------------------------------------------------------- block sums ----
+// Sum 28 per-thread values over the block; the totals land in tot[0..27].
+__device__ __forceinline__ void block_sum28(double (&v)[kMomentsN], double *sh, double *tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kMomentsN; ++q) {
+        double s = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        v[q] = s;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kMomentsN; ++q) sh[w * kMomentsN + q] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kMomentsN) {
+        double s = 0.0;
+        for (int j = 0; j < nw; ++j) s += sh[j * kMomentsN + threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+template <int P>
+__device__ __forceinline__ void tile_moments(const Part (&q)[P], const bool (&alive)[P], double *sh, double *tot,
+                                             double *K, double *out) {
+    double v[kMomentsN];
+#pragma unroll
+    for (int i = 0; i < kMomentsN; ++i) v[i] = 0.0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!alive[p]) continue;
+        const double d[6] = {q[p].x - K[0], q[p].xp - K[1], q[p].y - K[2],
+                             q[p].yp - K[3], q[p].l - K[4], q[p].d - K[5]};
+        v[0] += 1.0;
+        int m = 7;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            v[1 + j] += d[j];
+#pragma unroll
+            for (int k = j; k < 6; ++k) {
+                v[m] = fma(d[j], d[k], v[m]);
+                ++m;
+            }
+        }
+    }
+    block_sum28(v, sh, tot);
+    if (threadIdx.x == 0) {
+        const double n = tot[0];
+        out[0] = n;
+        if (n > 0.0) {
+            const double in = 1.0 / n;
+            double s1[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                s1[j] = tot[1 + j];
+                out[1 + j] = K[j] + s1[j] * in;
+            }
+            int m = 7;
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+#pragma unroll
+                for (int k = j; k < 6; ++k, ++m) out[m] = tot[m] - s1[j] * s1[k] * in;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) K[j] = out[1 + j];
+        } else {
+#pragma unroll
+            for (int j = 1; j < kMomentsN; ++j) out[j] = 0.0;
+        }
+    }
+    __syncthreads();
+}
+
+// Initial moment shift: the tile's mean (keeps the shifted sums well conditioned).
+template <int P>
+__device__ __forceinline__ void tile_mean(const Part (&q)[P], const bool (&alive)[P], double *sh, double *tot,
+                                          double *K) {
+    double v[kMomentsN];
+#pragma unroll
+    for (int i = 0; i < kMomentsN; ++i) v[i] = 0.0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!alive[p]) continue;
+        v[0] += 1.0;
+        v[1] += q[p].x; v[2] += q[p].xp; v[3] += q[p].y;
+        v[4] += q[p].yp; v[5] += q[p].l; v[6] += q[p].d;
+    }
+    block_sum28(v, sh, tot);
+    if (threadIdx.x < 6) K[threadIdx.x] = tot[0] > 0.0 ? tot[1 + threadIdx.x] / tot[0] : 0.0;
+    __syncthreads();
+}
+
+constexpr int kMaxBlock = 512;
+
+template <int P>
+__global__ void __launch_bounds__(256) k_track(TrackArgs a) {
+    __shared__ double sh[(kMaxBlock / 32) * kMomentsN];
+    __shared__ double tot[kMomentsN];
+    __shared__ double K[6];
+    __shared__ unsigned long long mm[2];
+    __shared__ int cnt;
+
+    const int64_t n_alive = a.st->n_alive;
+    const int T = blockDim.x * P;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    if (base >= n_alive) return;  // whole block beyond the alive range
+
+    Part q[P];
+    bool alive[P];
+    int lt[P], le[P];
+    double iP[P];
+    bool dirty[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
+        alive[p] = false;
+        lt[p] = -1;
+        le[p] = -1;
+        iP[p] = 1.0;
+        dirty[p] = true;
+        q[p] = Part{0, 0, 0, 0, 0, 0};
+        if (i < n_alive) {
+            const int32_t l0 = a.loss_turn[i];
+            alive[p] = l0 < 0;
+            q[p].x = a.coords[i];
+            q[p].xp = a.coords[a.pitch + i];
+            q[p].y = a.coords[2 * a.pitch + i];
+            q[p].yp = a.coords[3 * a.pitch + i];
+            q[p].l = a.coords[4 * a.pitch + i];
+            q[p].d = a.coords[5 * a.pitch + i];
+        }
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    if (a.do_moments) tile_mean<P>(q, alive, sh, tot, K);
+
+    const LatticeView &L = a.lat;
+    const DevElem *__restrict__ elems = L.elems;
+    double p0 = a.p0c;  // reference momentum, identical in every thread
+    for (int t = 0; t < a.n_turns; ++t) {
+        const int turn = a.turn_abs0 + t;
+        if (a.kick_wake >= 0) {
+            // Kick of the wake element that precedes this segment.
+            const uint64_t kmin = a.st->lkey[2 * a.kick_slot], kmax = a.st->lkey[2 * a.kick_slot + 1];
+            const double lmin = dkey_inv(kmin), lmax = dkey_inv(kmax);
+            const double dl = (lmax - lmin) / a.wake_nbins;
+            const bool flat = !(dl > 0.0);
+            const double idl = flat ? 0.0 : 1.0 / dl;
+            const double ip0 = 1.0 / p0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (!alive[p]) continue;
+                q[p].d = fma(wake_volt(q[p].l, lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q[p].d);
+                dirty[p] = true;
+                if (!inside(q[p], L)) {
+                    alive[p] = false;
+                    lt[p] = turn;
+                    le[p] = a.kick_wake;
+                }
+            }
+        }
+        for (int e = a.e0; e < a.e1; ++e) {
+            const DevElem E = load_elem(elems + e);
+            double p01 = p0, ip01 = 0.0;
+            if (E.type == TRK_RFCA) {
+                p01 = p0 + E.p[3];
+                ip01 = 1.0 / p01;
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (!alive[p]) continue;
+                switch (E.type) {
+                case TRK_MAP: apply_map(q[p], E, L.terms, dirty[p]); break;
+                case TRK_EDRIFT: edrift(q[p], E.p[0]); break;
+                case TRK_KQUAD:
+                case TRK_KSEXT: kick_drift(q[p], iP[p], dirty[p], E); break;
+                case TRK_THINSEXT: thin_sext(q[p], E); break;
+                case TRK_RFCA: rfca(q[p], E, p0, ip01, dirty[p]); break;
+                default: break;
+                }
+                if (!inside(q[p], L)) {
+                    alive[p] = false;
+                    lt[p] = turn;
+                    le[p] = e;
+                }
+            }
+            p0 = p01;
+        }
+        if (a.do_moments)
+            tile_moments<P>(q, alive, sh, tot, K,
+                            a.partials + ((size_t)(a.local_turn0 + t) * a.n_tiles + blockIdx.x) * kMomentsN);
+    }
+
+    if (a.minmax_slot >= 0) {
+        // l window of the next wake over the alive particles.
+        unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!alive[p]) continue;
+            const unsigned long long k = dkey(q[p].l);
+            kmin = k < kmin ? k : kmin;
+            kmax = k > kmax ? k : kmax;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a1 = __shfl_xor_sync(0xffffffffu, kmin, o);
+            const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmin = a1 < kmin ? a1 : kmin;
+            kmax = b1 > kmax ? b1 : kmax;
+        }
+        if (threadIdx.x == 0) {
+            mm[0] = ~0ull;
+            mm[1] = 0ull;
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[0], kmin);
+            atomicMax(&mm[1], kmax);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicMin((unsigned long long *)&a.st->lkey[2 * a.minmax_slot], mm[0]);
+            atomicMax((unsigned long long *)&a.st->lkey[2 * a.minmax_slot + 1], mm[1]);
+        }
+    }
+
+    int na = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
+        if (i >= n_alive) continue;
+        a.coords[i] = q[p].x;
+        a.coords[a.pitch + i] = q[p].xp;
+        a.coords[2 * a.pitch + i] = q[p].y;
+        a.coords[3 * a.pitch + i] = q[p].yp;
+        a.coords[4 * a.pitch + i] = q[p].l;
+        a.coords[5 * a.pitch + i] = q[p].d;
+        if (lt[p] >= 0) {
+            a.loss_turn[i] = lt[p];
+            a.loss_elem[i] = le[p];
+        }
+        na += alive[p] ? 1 : 0;
+    }
+    if (a.tile_alive) {
+        na = __reduce_add_sync(0xffffffffu, na);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicAdd(&cnt, na);
+        __syncthreads();
+        if (threadIdx.x == 0) a.tile_alive[blockIdx.x] = cnt;
+    }
+}
+
+// ---------------------------------------------------- moments finalise ----
+// Chan et al. pairwise merge of (n, mean, M2) partials in a fixed order.
+struct Acc {
+    double n, m[6], M[21];
+};
+
+__device__ __forceinline__ void acc_merge(Acc &a, const Acc &b) {
+    if (b.n == 0.0) return;
+    if (a.n == 0.0) {
+        a = b;
+        return;
+    }
+    const double n = a.n + b.n;
+    const double fb = b.n / n, fab = a.n * b.n / n;
+    double d[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        d[j] = b.m[j] - a.m[j];
+        a.m[j] = fma(d[j], fb, a.m[j]);
+    }
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int k = j; k < 6; ++k, ++q) a.M[q] = a.M[q] + b.M[q] + d[j] * d[k] * fab;
+    a.n = n;
+}
+
+constexpr int kFinThreads = 128;
+
+__global__ void __launch_bounds__(kFinThreads) k_moments_finalize(const double *__restrict__ partials, int n_tiles,
+                                                                   const BunchState *st, int tile,
+                                                                   double *__restrict__ out) {
+    __shared__ Acc sh[kFinThreads];
+    const int t = blockIdx.x;
+    const int64_t n_alive = st->n_alive;
+    const int n_act = (int)((n_alive + tile - 1) / tile);
+    Acc a;
+    a.n = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a.m[j] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 21; ++q) a.M[q] = 0.0;
+    for (int j = threadIdx.x; j < n_act; j += kFinThreads) {
+        const double *p = partials + ((size_t)t * n_tiles + j) * kMomentsN;
+        Acc b;
+        b.n = p[0];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b.m[k] = p[1 + k];
+#pragma unroll
+        for (int q = 0; q < 21; ++q) b.M[q] = p[7 + q];
+        acc_merge(a, b);
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = kFinThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            Acc x = sh[threadIdx.x];
+            acc_merge(x, sh[threadIdx.x + s]);
+            sh[threadIdx.x] = x;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const Acc &r = sh[0];
+        double *o = out + (size_t)t * kMomentsN;
+        o[0] = r.n;
+        const double in = r.n > 0.0 ? 1.0 / r.n : 0.0;
+        for (int j = 0; j < 6; ++j) o[1 + j] = r.n > 0.0 ? r.m[j] : 0.0;
+        for (int q = 0; q < 21; ++q) o[7 + q] = r.M[q] * in;
+    }
+}
+
+// ------------------------------------------------------------ compaction ----
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ tile_alive,
+                                                              int64_t *__restrict__ tile_off, int tile,
+                                                              BunchState *st) {
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int64_t n_alive = st->n_alive;
+    const int n_act = (int)((n_alive + tile - 1) / tile);
+    const int per = (n_act + kScanThreads - 1) / kScanThreads;
+    const int b = threadIdx.x * per, e = min(b + per, n_act);
+    int64_t s = 0;
+    for (int j = b; j < e; ++j) s += tile_alive[j];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t v = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int64_t off = inc - s + (w > 0 ? wsum[w - 1] : 0);
+    for (int j = b; j < e; ++j) {
+        tile_off[j] = off;
+        off += tile_alive[j];
+    }
+    if (threadIdx.x == kScanThreads - 1) st->n_alive_next = off;
+}
+
+// Stable partition of each tile into the compaction buffers: alive particles to
+// [tile_off, ...), lost ones after all survivors, in slot order.
+__global__ void k_scatter(const double *__restrict__ coords, int64_t pitch, const int32_t *__restrict__ ids,
+                          const int32_t *__restrict__ lt, const int32_t *__restrict__ le, double *__restrict__ cb,
+                          int32_t *__restrict__ ib, int32_t *__restrict__ ltb, int32_t *__restrict__ leb,
+                          const int64_t *__restrict__ tile_off, const BunchState *st) {
+    __shared__ int wcnt[32];
+    const int64_t n_alive = st->n_alive, n_next = st->n_alive_next;
+    if (n_next == n_alive) return;  // nothing lost in this chunk
+    const int T = blockDim.x;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    if (base >= n_alive) return;
+    const int64_t i = base + threadIdx.x;
+    const bool valid = i < n_alive;
+    const bool al = valid && lt[i] < 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, al);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int j = 0; j < w; ++j) before += wcnt[j];
+    const int rank = before + __popc(bal & ((1u << lane) - 1u));
+    if (!valid) return;
+    const int64_t toff = tile_off[blockIdx.x];
+    int64_t dst;
+    if (al)
+        dst = toff + rank;
+    else
+        dst = n_next + (base - toff) + (threadIdx.x - rank);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cb[c * pitch + dst] = coords[c * pitch + i];
+    ib[dst] = ids[i];
+    ltb[dst] = lt[i];
+    leb[dst] = le[i];
+}
+
+__global__ void k_copyback(double *__restrict__ coords, int64_t pitch, int32_t *__restrict__ ids,
+                           int32_t *__restrict__ lt, int32_t *__restrict__ le, const double *__restrict__ cb,
+                           const int32_t *__restrict__ ib, const int32_t *__restrict__ ltb,
+                           const int32_t *__restrict__ leb, const BunchState *st) {
+    const int64_t n_alive = st->n_alive;
+    if (st->n_alive_next == n_alive) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_alive;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) coords[c * pitch + i] = cb[c * pitch + i];
+        ids[i] = ib[i];
+        lt[i] = ltb[i];
+        le[i] = leb[i];
+    }
+}
+
+__global__ void k_commit(BunchState *st) { st->n_alive = st->n_alive_next; }
+
+__global__ void k_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        lt[i] = -1;
+        le[i] = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->n_alive = n;
+        st->n_alive_next = n;
+        st->error = 0;
+        for (int s = 0; s < 2; ++s) {
+            st->lkey[2 * s] = ~0ull;
+            st->lkey[2 * s + 1] = 0ull;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_track(const TrackArgs &a, int block, int per_thread, int n_tiles, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (per_thread == 2)
+        k_track<2><<<n_tiles, block, 0, s>>>(a);
+    else
+        k_track<1><<<n_tiles, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_finalize(const double *partials, int n_tiles, int n_turns, const BunchState *st, int tile,
+                                    double *out, cudaStream_t s) {
+    if (n_turns <= 0) return cudaSuccess;
+    k_moments_finalize<<<n_turns, kFinThreads, 0, s>>>(partials, n_tiles, st, tile, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(double *coords, int64_t pitch, int32_t *ids, int32_t *lt, int32_t *le, double *coords_b,
+                           int32_t *ids_b, int32_t *lt_b, int32_t *le_b, const int32_t *tile_alive,
+                           int64_t *tile_off, int n_tiles, int tile, BunchState *st, cudaStream_t s) {
+    k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_alive, tile_off, tile, st);
+    k_scatter<<<n_tiles, tile, 0, s>>>(coords, pitch, ids, lt, le, coords_b, ids_b, lt_b, le_b, tile_off, st);
+    const int64_t n = (int64_t)n_tiles * tile;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_copyback<<<grid, 256, 0, s>>>(coords, pitch, ids, lt, le, coords_b, ids_b, lt_b, le_b, st);
+    k_commit<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n, cudaStream_t s) {
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    k_init_bunch<<<grid, 256, 0, s>>>(st, lt, le, n);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

@@ -1,0 +1,192 @@
+// Longitudinal wake path (Sec. 2.2 histogram, Sec. 2.3 convolution; Table 1
+// WAKE): l-window by min/max over alive particles, privatised shared-memory
+// histogram with an exact bin index, causal convolution with the wake function,
+// and (in the tracking kernel) the interpolated energy kick.
+#include <cmath>
+
+#include "trk_internal.cuh"
+
+namespace trk {
+namespace {
+
+constexpr int kHistThreads = 512;
+constexpr int kSmemBins = 8192;      // sub-histograms in shared memory up to this many bins
+constexpr int kSubHists = 2;         // per block (one per half of the warps)
+constexpr int kConvOut = 16;         // outputs per convolution block
+constexpr int kConvThreads = 256;
+
+__global__ void k_wake_reset(BunchState *st, int slot, uint32_t *hist, int nbins) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) hist[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->lkey[2 * slot] = ~0ull;
+        st->lkey[2 * slot + 1] = 0ull;
+    }
+}
+
+__global__ void k_wake_minmax(const double *__restrict__ coords, int64_t pitch, const int32_t *__restrict__ lt,
+                              BunchState *st, int slot) {
+    __shared__ unsigned long long mm[2];
+    const int64_t n = st->n_alive;
+    unsigned long long kmin = ~0ull, kmax = 0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (lt[i] >= 0) continue;
+        const unsigned long long k = dkey(coords[4 * pitch + i]);
+        kmin = k < kmin ? k : kmin;
+        kmax = k > kmax ? k : kmax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
+    }
+    if (threadIdx.x == 0) {
+        mm[0] = ~0ull;
+        mm[1] = 0ull;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], kmin);
+        atomicMax(&mm[1], kmax);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMin((unsigned long long *)&st->lkey[2 * slot], mm[0]);
+        atomicMax((unsigned long long *)&st->lkey[2 * slot + 1], mm[1]);
+    }
+}
+
+// Bin index exactly as floor((l - lmin) / dl) in IEEE double, clamped.
+__device__ __forceinline__ int bin_of(double l, double lmin, double dl, int nbins) {
+    if (!(dl > 0.0)) return 0;
+    const double u = floor(__ddiv_rn(__dsub_rn(l, lmin), dl));
+    if (!(u >= 0.0)) return 0;
+    if (u > (double)(nbins - 1)) return nbins - 1;
+    return (int)u;
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__restrict__ coords, int64_t pitch,
+                                                             const int32_t *__restrict__ lt, const BunchState *st,
+                                                             int slot, int nbins, double w0, double sc,
+                                                             uint32_t *__restrict__ hist, double *__restrict__ wfun) {
+    extern __shared__ uint32_t sh[];
+    const int64_t n = st->n_alive;
+    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const bool any = kmin <= kmax;
+    const double lmin = any ? dkey_inv(kmin) : 0.0;
+    const double lmax = any ? dkey_inv(kmax) : 0.0;
+    const double dl = (lmax - lmin) / nbins;
+    // wake function samples W(m dl) = w0 / sqrt(max(m dl, s_c))
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nbins; m += gridDim.x * blockDim.x) {
+        const double s = (double)m * dl;
+        wfun[m] = w0 / sqrt(s > sc ? s : sc);
+    }
+    if (!any) return;
+    const bool smem = nbins <= kSmemBins;
+    if (smem) {
+        for (int i = threadIdx.x; i < kSubHists * nbins; i += blockDim.x) sh[i] = 0u;
+        __syncthreads();
+    }
+    uint32_t *mine = sh + ((threadIdx.x >> 5) % kSubHists) * nbins;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (lt[i] >= 0) continue;
+        const int b = bin_of(coords[4 * pitch + i], lmin, dl, nbins);
+        if (smem)
+            atomicAdd(mine + b, 1u);
+        else
+            atomicAdd(hist + b, 1u);
+    }
+    if (smem) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int s = 0; s < kSubHists; ++s) c += sh[s * nbins + b];
+            if (c) atomicAdd(hist + b, c);
+        }
+    }
+}
+
+// V_k = -q_m sum_{j <= k} h_j W((k - j) dl); a block owns kConvOut outputs and
+// its threads split the source bins.
+__global__ void __launch_bounds__(kConvThreads) k_wake_conv(const uint32_t *__restrict__ hist,
+                                                             const double *__restrict__ wfun, int nbins, double qm,
+                                                             double *__restrict__ V) {
+    __shared__ double sh[(kConvThreads / 32) * kConvOut];
+    const int k0 = blockIdx.x * kConvOut;
+    const int kend = min(k0 + kConvOut, nbins);
+    double acc[kConvOut];
+#pragma unroll
+    for (int i = 0; i < kConvOut; ++i) acc[i] = 0.0;
+    for (int j = threadIdx.x; j < kend; j += blockDim.x) {
+        const uint32_t hj = __ldg(hist + j);
+        if (hj == 0u) continue;
+        const double h = (double)hj;
+#pragma unroll
+        for (int i = 0; i < kConvOut; ++i) {
+            const int k = k0 + i;
+            if (k >= j && k < kend) acc[i] = fma(h, __ldg(wfun + (k - j)), acc[i]);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kConvOut; ++i) {
+        double s = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[w * kConvOut + i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < kConvOut && k0 + threadIdx.x < kend) {
+        double s = 0.0;
+        for (int j = 0; j < kConvThreads / 32; ++j) s += sh[j * kConvOut + threadIdx.x];
+        V[k0 + threadIdx.x] = -qm * s;
+    }
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, int nbins, cudaStream_t s) {
+    k_wake_reset<<<grid_for(nbins, 256, 64), 256, 0, s>>>(st, slot, hist, nbins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot,
+                               int64_t n_max, cudaStream_t s) {
+    k_wake_minmax<<<grid_for(n_max, 256, 152 * 8), 256, 0, s>>>(coords, pitch, lt, st, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot,
+                             int nbins, double w0, double sc, uint32_t *hist, double *wfun, int64_t n_max,
+                             cudaStream_t s) {
+    const size_t smem = nbins <= kSmemBins ? (size_t)kSubHists * nbins * sizeof(uint32_t) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wake_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSubHists * kSmemBins * (int)sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int g = grid_for(n_max, kHistThreads, 152 * 2);
+    const int gw = (nbins + kHistThreads - 1) / kHistThreads;
+    if (g < gw) g = gw;
+    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, slot, nbins, w0, sc, hist, wfun);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
+                             cudaStream_t s) {
+    k_wake_conv<<<(nbins + kConvOut - 1) / kConvOut, kConvThreads, 0, s>>>(hist, wfun, nbins, qm, V);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

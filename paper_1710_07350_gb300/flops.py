@@ -1,0 +1,84 @@
+"""Algorithmic work of the tracking path, for the roofline.
+
+Convention: one flop per +, -, *, /, sqrt or cos of the element model as the
+paper and the oracle state it (an FMA is two flops); per-element constants
+(K1 h, 0.5 K2 h, ...) are not counted.  This is the work the method needs,
+whatever instructions the kernel spends on it.
+
+Per particle and pass (alive particle entering the element):
+  EDRIFT        x += L x', y += L y' (4); l += L (sqrt(1 + x'^2 + y'^2) - 1) (8)  -> 12
+  kick-drift    entry P = 1 + delta, r = sqrt(1 + x'^2 + y'^2), px, py          -> 10
+                per merged drift (n_steps * 3 + 1 of them): pz = sqrt(P^2 - px^2 - py^2) (6),
+                x += h px/pz (3), y (3), l += h (P/pz - 1) (4)                     -> 16
+                per quad kick (3 per step): px -= a x, py += a y                   -> 4
+                per sextupole kick (3 per step): (x^2 - y^2) (3), *c, -= (2); x y * c += (3) -> 8
+                exit: pz (6), x' = px/pz, y' = py/pz (2)                           -> 8
+  THINSEXT      x' -= (K2L/2)(x^2 - y^2) (5), y' += K2L x y (3)                      -> 8
+  RFCA          P (2), phi + k l (2), cos (1), V * (1), + (1), P/P' (1), 2 *, delta (2) -> 12
+  MAP           per nonzero term of degree d (the R_rr = 1 diagonal is free): d * (products) + 1 add
+                i.e. deg 0: 1, deg 1: 2, deg 2: 3, deg 3: 4
+  aperture      RECT |x| <= a, |y| <= b: 4;  ELLIPSE (x/a)^2 + (y/b)^2 <= 1: 6
+  moments       per alive particle and turn: 6 means + 21 centred products: 54
+"""
+import numpy as np
+
+MOMENTS_FLOPS = 54
+APERTURE_FLOPS = {None: 0, "rect": 4, "ellipse": 6}
+
+
+def map_flops(m):
+    order = int(m["order"])
+    f = 0
+    R = np.asarray(m["R"]).reshape(6, 6)
+    C = np.asarray(m["C"]).ravel()
+    for r in range(6):
+        f += int(C[r] != 0.0)
+        for j in range(6):
+            if R[r, j] != 0.0 and not (j == r and R[r, j] == 1.0):
+                f += 2
+        if order >= 2:
+            f += 3 * int(np.count_nonzero(np.asarray(m["T"]).reshape(6, 21)[r]))
+        if order >= 3:
+            f += 4 * int(np.count_nonzero(np.asarray(m["U"]).reshape(6, 56)[r]))
+    return f
+
+
+def element_flops(el):
+    t = el["type"]
+    if t == "EDRIFT":
+        return 12
+    if t in ("KQUAD", "KSEXT"):
+        n = el["n_kicks"]
+        kick = (4 if el.get("K1", 0.0) != 0.0 else 0) + (8 if el.get("K2", 0.0) != 0.0 and t == "KSEXT" else 0)
+        return 10 + (3 * n + 1) * 16 + 3 * n * kick + 8
+    if t == "THINSEXT":
+        return 8
+    if t == "RFCA":
+        return 12
+    if t == "MAP":
+        return map_flops(el["map"])
+    if t == "WAKE":
+        return 0  # counted separately (histogram, convolution, kick)
+    raise ValueError(t)
+
+
+def lattice_pass_flops(lat):
+    """Per element: flops of one particle pass including the aperture test."""
+    ap = lat.get("aperture")
+    fa = APERTURE_FLOPS[ap[0] if ap else None]
+    return np.array([element_flops(el) + fa for el in lat["elements"]], dtype=np.float64)
+
+
+def step_work(lat, n_start, n_turns, lost_turn_local=(), lost_elem=(), moments=True):
+    """(passes, flops) of n_turns turns for n_start alive particles of which the
+    listed ones are lost at (local turn, element)."""
+    f = lattice_pass_flops(lat)
+    ne = len(f)
+    cum = np.cumsum(f)
+    turn_f = cum[-1] + (MOMENTS_FLOPS if moments else 0)
+    lt = np.asarray(lost_turn_local, dtype=np.int64)
+    le = np.asarray(lost_elem, dtype=np.int64)
+    n_surv = n_start - lt.size
+    passes = n_surv * n_turns * ne + float(np.sum(lt * ne + le + 1))
+    flops = n_surv * n_turns * turn_f + float(np.sum(lt * turn_f + cum[le])) if lt.size else n_surv * n_turns * turn_f
+    return float(passes), float(flops)

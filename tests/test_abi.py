@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/trk.h; the ctypes structures match the C layouts."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1710_07350_gb300 import build, trk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(trk_[A-Za-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_core_calls():
+    names = declared_functions()
+    for must in ("trk_create_lattice", "trk_track", "trk_moments", "trk_wake", "trk_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build.build())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "trk.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(trk_element_desc), offsetof(trk_element_desc, C),
+         offsetof(trk_element_desc, charge), sizeof(trk_lattice_opts), offsetof(trk_lattice_opts, p0c_ev),
+         sizeof(trk_schedule));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(trk.trk_element_desc), trk.trk_element_desc.C.offset, trk.trk_element_desc.charge.offset,
+            ctypes.sizeof(trk.trk_lattice_opts), trk.trk_lattice_opts.p0c_ev.offset, ctypes.sizeof(trk.trk_schedule)]
+    assert got == want
+
+
+def test_invalid_descriptors_rejected_without_gpu():
+    """Argument validation happens on the host before any device call."""
+    lib = trk.lib()
+    h = ctypes.c_void_p()
+    o = trk.trk_lattice_opts()
+    o.p0c_ev = 1e9
+    d = (trk.trk_element_desc * 1)()
+    d[0].type = 99
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert b"unknown type" in lib.trk_last_error()
+    d[0].type = trk.TYPES["MAP"]
+    d[0].order = 2
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert b"needs R" in lib.trk_last_error()
+    d[0].type = trk.TYPES["KQUAD"]
+    d[0].n_kicks = 0
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    o.p0c_ev = -1.0
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    o.p0c_ev = 1e9
+    o.aperture = 1
+    o.a = 0.0
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert lib.trk_bunch_wrap(None, 0, None, -1, None, ctypes.byref(h)) == 1
+    assert lib.trk_bunch_wrap(None, 5, None, 10, None, ctypes.byref(h)) == 1
+    assert lib.trk_track(None, None, 1) == 1
+
+
+def test_step_work_accounting():
+    """Passes and flops of a step from loss records (used by the bench)."""
+    import numpy as np
+    import synthetic as syn
+    from paper_1710_07350_gb300 import flops
+    lat = syn.lattice_c2(cells=1)
+    ne = len(lat["elements"])
+    p, f = flops.step_work(lat, 10, 3)
+    assert p == 10 * 3 * ne
+    per = flops.lattice_pass_flops(lat)
+    assert f == 10 * 3 * (per.sum() + flops.MOMENTS_FLOPS)
+    p2, f2 = flops.step_work(lat, 10, 3, [1], [2])
+    assert p2 == 9 * 3 * ne + (1 * ne + 3)
+    assert f2 == 9 * 3 * (per.sum() + 54) + (per.sum() + 54) + per[:3].sum()
+    # kick-drift quad with 4 steps: entry 10 + 13 drifts x 16 + 12 kicks x 4 + exit 8
+    assert flops.element_flops({"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}) == 274
+    assert flops.element_flops({"type": "KSEXT", "L": 0.1, "K2": 20.0, "n_kicks": 4}) == 322

@@ -1,0 +1,167 @@
+"""GPU parity of the fused tracking path (through the C ABI) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import oracle as orc
+
+from gpu_util import (MARGIN, TOL_100, TOL_PASS, by_id, compare_moments, compare_tracking, gpu_track)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def rand_particles(n, seed, scale=(1e-3, 1e-4, 1e-3, 1e-4, 1e-3, 1e-3), big=0.1):
+    """Mostly beam-like particles plus a fraction with large angles that take
+    the exact (non-series) branches."""
+    rng = np.random.default_rng(seed)
+    z = rng.normal(size=(n, 6)) * np.array(scale)
+    k = int(big * n)
+    z[:k, 1] = rng.uniform(-2e-2, 2e-2, k)
+    z[:k, 3] = rng.uniform(-2e-2, 2e-2, k)
+    return z
+
+
+ONE_ELEMENT = [
+    ("MAP.o2", lambda: {"type": "MAP", "map": syn.stored_map("QF.o2")}),
+    ("MAP.o3", lambda: {"type": "MAP", "map": syn.stored_map("QD.o3")}),
+    ("MAP.drift", lambda: {"type": "MAP", "map": syn.stored_map("D1.0.o2")}),
+    ("EDRIFT", lambda: {"type": "EDRIFT", "L": 0.9}),
+    ("KQUAD", lambda: {"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}),
+    ("KQUAD-", lambda: {"type": "KQUAD", "L": 0.2, "K1": -1.2, "n_kicks": 1}),
+    ("KSEXT", lambda: {"type": "KSEXT", "L": 0.1, "K2": 20.0, "n_kicks": 4}),
+    ("KSEXT+K1", lambda: {"type": "KSEXT", "L": 0.3, "K1": 0.5, "K2": -20.0, "n_kicks": 3}),
+    ("THINSEXT", lambda: {"type": "THINSEXT", "K2L": 20.0}),
+    ("RFCA", lambda: {"type": "RFCA", "volt": 20e6, "phase_deg": -10.0, "freq_hz": 2.856e9}),
+]
+
+
+@pytest.mark.parametrize("name,mk", ONE_ELEMENT, ids=[n for n, _ in ONE_ELEMENT])
+def test_single_element_one_pass(name, mk):
+    lat = {"elements": [mk()], "aperture": None, "p0c": syn.P0C_1GEV}
+    z = rand_particles(1000, 7)
+    g = gpu_track(lat, z, 1)
+    o = orc.track(lat, z, 1)
+    compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"])
+    assert g["p0c"] == o["p0c"]
+
+
+@pytest.mark.parametrize("block,per_thread", [(128, 1), (64, 2), (256, 1), (96, 2)])
+def test_c1_100_turns(block, per_thread):
+    """Config 1 at full size (10k particles, 100 turns) in several schedules."""
+    lat = syn.lattice_c1()
+    z = syn.bunch("c1")
+    g = gpu_track(lat, z, 100, schedule={"block": block, "per_thread": per_thread, "chunk_turns": 37})
+    o = orc.track(lat, z, 100)
+    assert g["n_alive"] == o["n_alive"] == 10000
+    compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"])
+
+
+def test_c1_losses_ragged_tiles():
+    """Small aperture: many losses at many elements and turns; n not a multiple
+    of the tile; lost ids, turns and elements exact outside the margin."""
+    lat = syn.lattice_c1()
+    lat["aperture"] = ("rect", 7e-4, 4e-4)
+    z = syn.bunch("c1", n=3001, seed=21)
+    g = gpu_track(lat, z, 30, schedule={"block": 64, "per_thread": 1, "chunk_turns": 7})
+    o = orc.track(lat, z, 30)
+    assert 0 < o["n_alive"] < 3001
+    compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"])
+    # compaction: alive slots hold exactly the survivors, in id order (stable)
+    alive_ids = g["ids"][:g["n_alive"]]
+    assert np.all(np.diff(alive_ids) > 0)
+
+
+def test_c2_one_pass_and_100_turns():
+    lat = syn.lattice_c2()
+    z = syn.bunch("c2", n=600)
+    g1 = gpu_track(lat, z, 1)
+    o1 = orc.track(lat, z, 1)
+    compare_tracking(g1, o1, TOL_PASS)
+    compare_moments(g1["moments"], o1["moments"])
+    g = gpu_track(lat, z, 100, schedule={"chunk_turns": 30})
+    o = orc.track(lat, z, 100)
+    compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"])
+    assert g["p0c"] == o["p0c"]
+
+
+def test_c2_ellipse_losses():
+    lat = syn.lattice_c2(cells=5)
+    lat["aperture"] = ("ellipse", 1.2e-3, 6e-4)
+    z = syn.bunch("c2", n=2000, seed=9)
+    g = gpu_track(lat, z, 12, schedule={"block": 128, "per_thread": 2, "chunk_turns": 5})
+    o = orc.track(lat, z, 12)
+    assert 0 < o["n_alive"] < 2000
+    compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"])
+
+
+def test_resume_bit_identical():
+    lat = syn.lattice_c2(cells=3)
+    lat["aperture"] = ("ellipse", 1.5e-3, 8e-4)
+    z = syn.bunch("c2", n=1500, seed=4)
+    a = gpu_track(lat, z, 9)
+    b = gpu_track(lat, z, 9, calls=[2, 3, 4])
+    assert np.array_equal(a["z"], b["z"]) and np.array_equal(a["ids"], b["ids"])
+    for x, y in zip(a["lost"], b["lost"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a["moments"], b["moments"])
+
+
+def test_schedule_invariance_of_coordinates():
+    """The per-particle arithmetic does not depend on the launch shape."""
+    lat = syn.lattice_c2(cells=2)
+    z = syn.bunch("c2", n=999, seed=5)
+    a = gpu_track(lat, z, 5, schedule={"block": 64, "per_thread": 1, "chunk_turns": 1})
+    b = gpu_track(lat, z, 5, schedule={"block": 256, "per_thread": 2, "chunk_turns": 5})
+    za, _, _, _ = by_id(a, 999)
+    zb, _, _, _ = by_id(b, 999)
+    assert np.array_equal(za, zb)
+
+
+def test_edge_cases_empty_single_nan():
+    lat = syn.lattice_c1()
+    g = gpu_track(lat, np.zeros((0, 6)), 5)
+    assert g["n_alive"] == 0 and g["moments"].shape == (0, 28)
+    z = np.zeros((3, 6))
+    z[0, 0] = np.nan
+    z[1, 0] = 0.02
+    z[2, 2] = 1e-4
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    compare_tracking(g, o, TOL_PASS * 100)
+    k = list(g["lost"][0]).index(0)      # the NaN particle is lost at element 0 of turn 0
+    assert g["lost"][1][k] == 0 and g["lost"][2][k] == 0
+    one = syn.bunch("c1", n=1)
+    g = gpu_track(lat, one, 3)
+    o = orc.track(lat, one, 3)
+    compare_tracking(g, o, TOL_PASS * 10)
+    compare_moments(g["moments"], o["moments"])
+
+
+def test_all_lost():
+    lat = syn.lattice_c1()
+    lat["aperture"] = ("rect", 1e-7, 1e-7)
+    z = syn.bunch("c1", n=500)
+    g = gpu_track(lat, z, 3)
+    o = orc.track(lat, z, 3)
+    assert g["n_alive"] == 0 == o["n_alive"]
+    compare_tracking(g, o, TOL_PASS)
+    assert np.all(g["moments"] == 0.0)
+
+
+def test_order3_maps_ring():
+    lat = syn.lattice_c1(order=3)
+    z = syn.bunch("c1", n=2000, seed=3)
+    g = gpu_track(lat, z, 20)
+    o = orc.track(lat, z, 20)
+    compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"])

@@ -1,0 +1,83 @@
+"""GPU parity of the longitudinal wake path (histogram, convolution, kick)."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import oracle as orc
+from paper_1710_07350_gb300 import trk
+
+from gpu_util import TOL_PASS, compare_moments, compare_tracking, gpu_track
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def gpu_wake(z, nbins, w0, sc, charge, p0c, schedule=None):
+    coords, ids = trk.upload(z)
+    b = trk.trk_bunch_wrap(coords, ids)
+    if schedule:
+        trk.trk_bunch_set_schedule(b, **schedule)
+    hist = torch.zeros(nbins, dtype=torch.int32, device="cuda")
+    volt = torch.zeros(nbins, dtype=torch.float64, device="cuda")
+    trk.trk_wake(b, nbins, w0, sc, charge, p0c, hist=hist, volt=volt)
+    zz, ii = trk.download(b)
+    out = np.empty_like(zz)
+    out[ii] = zz
+    return out, hist.cpu().numpy().astype(np.int64), volt.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,nbins", [(20_000, 4096), (12_345, 1000), (5000, 16384), (3000, 1)])
+def test_wake_standalone(n, nbins):
+    z = syn.bunch("c3", n=n)
+    W0, sc, Q, p0 = syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 2.0e9
+    g, gh, gV = gpu_wake(z, nbins, W0, sc, Q, p0)
+    o, oh, oV = orc.wake(z, nbins, W0, sc, Q, p0)
+    assert np.array_equal(gh, oh), "histogram must be bit-exact on identical l"
+    assert np.allclose(gV, oV, rtol=1e-13, atol=0)
+    assert np.array_equal(g[:, :5], z[:, :5])
+    assert np.max(np.abs(g[:, 5] - o[:, 5])) <= 1e-15
+
+
+def test_wake_degenerate():
+    p0 = 1e9
+    z = np.zeros((7, 6))
+    z[:, 4] = 3e-5                       # all equal: dl = 0, everything in bin 0
+    g, gh, gV = gpu_wake(z, 64, 4e11, 1e-5, 1e-12, p0)
+    o, oh, oV = orc.wake(z, 64, 4e11, 1e-5, 1e-12, p0)
+    assert np.array_equal(gh, oh) and gh[0] == 7
+    assert np.allclose(gV, oV, rtol=1e-14, atol=0)
+    assert np.allclose(g, o, rtol=0, atol=1e-18)
+    g, gh, gV = gpu_wake(z[:1], 8, 4e11, 1e-5, 1e-12, p0)
+    o, oh, oV = orc.wake(z[:1], 8, 4e11, 1e-5, 1e-12, p0)
+    assert np.array_equal(gh, oh) and np.allclose(g, o, rtol=0, atol=1e-18)
+
+
+def test_wake_zero_strength_identity():
+    z = syn.bunch("c3", n=4000)
+    g, gh, gV = gpu_wake(z, 512, 0.0, 1e-5, 250e-12, 1e9)
+    assert np.array_equal(g, z) and np.all(gV == 0.0) and gh.sum() == 4000
+
+
+def test_c3_linac_reduced():
+    """Config-3 structure (RF, WAKE, drift, quad per period) at reduced size."""
+    lat = syn.lattice_c3(periods=6, nbins=512)
+    z = syn.bunch("c3", n=20_000)
+    g = gpu_track(lat, z, 1, schedule={"block": 128, "per_thread": 2})
+    o = orc.track(lat, z, 1)
+    compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], tol=1e-11)
+    assert g["p0c"] == o["p0c"]
+
+
+def test_wake_last_and_first_element():
+    """A lattice that starts and ends with a wake (segments of zero length)."""
+    wk = {"type": "WAKE", "nbins": 128, "W0": syn.C3_W0, "sc": syn.C3_SC, "charge": syn.C3_CHARGE}
+    rf = {"type": "RFCA", "volt": 20e6, "phase_deg": -10.0, "freq_hz": 2.856e9}
+    lat = {"elements": [wk, rf, wk, wk, {"type": "EDRIFT", "L": 1.0}, wk], "aperture": None, "p0c": syn.P0C_1GEV}
+    z = syn.bunch("c3", n=3000)
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    compare_tracking(g, o, TOL_PASS * 10)
+    compare_moments(g["moments"], o["moments"], tol=1e-11)
