@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--block", type=int, default=128)
     p.add_argument("--per-thread", type=int, default=1)
+    # smaller cases for profiling runs only (the bench line uses the defaults)
+    p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
+    p.add_argument("--particles", type=int, default=N_PARTICLES)
     return p.parse_args()
 
 
@@ -194,9 +197,10 @@ def run_ours(args):
 
     lat = syn.lattice_c2()
     L = trk.trk_create_lattice(lat)
-    z0 = syn.bunch("c2", n=N_PARTICLES, seed=2 + 1000 * rank)
+    tps, npart = args.turns_per_step, args.particles
+    z0 = syn.bunch("c2", n=npart, seed=2 + 1000 * rank)
     coords0, ids0 = trk.upload(z0)
-    sched = {"block": args.block, "per_thread": args.per_thread, "chunk_turns": TURNS_PER_STEP}
+    sched = {"block": args.block, "per_thread": args.per_thread, "chunk_turns": tps}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -205,7 +209,7 @@ def run_ours(args):
     b = trk.trk_bunch_wrap(coords, ids)
     trk.trk_bunch_set_schedule(b, **sched)
     for _ in range(args.warmup):
-        trk.trk_track(b, L, TURNS_PER_STEP)
+        trk.trk_track(b, L, tps)
     torch.cuda.synchronize()
     del b
 
@@ -219,19 +223,19 @@ def run_ours(args):
     barrier()
     clocks.start()
     step_ms, passes, flop = [], 0.0, 0.0
-    n_alive = N_PARTICLES
+    n_alive = npart
     n_lost_seen = 0
     for k in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        trk.trk_track(b, L, TURNS_PER_STEP)
+        trk.trk_track(b, L, tps)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         lid, lturn, lel = trk.trk_lost(b)
         new = slice(n_lost_seen, len(lid))
-        p, f = flops.step_work(lat, n_alive, TURNS_PER_STEP, lturn[new] - k * TURNS_PER_STEP, lel[new])
+        p, f = flops.step_work(lat, n_alive, tps, lturn[new] - k * tps, lel[new])
         passes += p
         flop += f
         n_alive -= len(lid) - n_lost_seen
@@ -261,31 +265,31 @@ def run_ours(args):
         di = torch.empty_like(ids0)
         b2 = trk.trk_bunch_wrap(dz, di)
         trk.trk_bunch_set_schedule(b2, **sched)
-        mom_host = torch.empty((TURNS_PER_STEP, 28), dtype=torch.float64).pin_memory()
+        mom_host = torch.empty((tps, 28), dtype=torch.float64).pin_memory()
         n_e2e = max(1, min(args.steps, 3))
         barrier()
         t0 = time.perf_counter()
         p_e2e = 0.0
-        na2 = N_PARTICLES
+        na2 = npart
         seen2 = 0
         for k in range(n_e2e):
             dz.copy_(hz, non_blocking=True)
             di.copy_(hi, non_blocking=True)
-            trk.trk_track(b2, L, TURNS_PER_STEP)
+            trk.trk_track(b2, L, tps)
             hz.copy_(dz, non_blocking=True)
             hi.copy_(di, non_blocking=True)
             mom = trk.trk_moments(b2)          # synchronises; result read on the host
             mom_host.copy_(torch.from_numpy(mom))
             lid, lturn, lel = trk.trk_lost(b2)
             new = slice(seen2, len(lid))
-            p, _ = flops.step_work(lat, na2, TURNS_PER_STEP, lturn[new] - k * TURNS_PER_STEP, lel[new])
+            p, _ = flops.step_work(lat, na2, tps, lturn[new] - k * tps, lel[new])
             p_e2e += p
             na2 -= len(lid) - seen2
             seen2 = len(lid)
         barrier()
         dt = time.perf_counter() - t0
         bi = coords0.numel() * 8 + ids0.numel() * 4
-        bo = bi + TURNS_PER_STEP * 28 * 8
+        bo = bi + tps * 28 * 8
         e2e = {"value": p_e2e * world / dt, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "steps": n_e2e}
 
@@ -294,13 +298,13 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
     cpu = None if args.no_cpu_baseline else cpu_baseline()
-    traffic = profiled_traffic_per_launch()
+    traffic = profiled_traffic_per_launch(npart, tps)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles_per_gpu": N_PARTICLES, "elements": len(lat["elements"]),
-                   "turns_per_step": TURNS_PER_STEP, "turns_timed": TURNS_PER_STEP * args.steps,
+        "config": {"workload": WORKLOAD, "particles_per_gpu": npart, "elements": len(lat["elements"]),
+                   "turns_per_step": tps, "turns_timed": tps * args.steps,
                    "l2": "flushed between steps (256 MiB write)", "block": args.block,
                    "per_thread": args.per_thread, "parallelism": "replica bunches, no collective" if world > 1
                    else "1 GPU"},
@@ -324,7 +328,7 @@ def run_ours(args):
     return 0
 
 
-def profiled_traffic_per_launch():
+def profiled_traffic_per_launch(npart, tps):
     """DRAM bytes per k_track launch scaled from the committed ncu summary
     (profiles/k_track_c2.txt, line 'dram_bytes_per_particle_turn: X'), or None."""
     path = os.path.join(ROOT, "profiles", "k_track_c2.txt")
@@ -333,7 +337,7 @@ def profiled_traffic_per_launch():
     for line in open(path):
         if line.startswith("dram_bytes_per_particle_turn:"):
             try:
-                return float(line.split(":")[1]) * N_PARTICLES * TURNS_PER_STEP
+                return float(line.split(":")[1]) * npart * tps
             except ValueError:
                 return None
     return None

@@ -271,8 +271,9 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.ap_b = opts->b;
     std::memcpy(&v.ap_a_bits, &opts->a, 8);
     std::memcpy(&v.ap_b_bits, &opts->b, 8);
-    v.ap_ia2f = opts->aperture == TRK_APERTURE_ELLIPSE ? (float)(1.0 / (opts->a * opts->a)) : 0.0f;
-    v.ap_ib2f = opts->aperture == TRK_APERTURE_ELLIPSE ? (float)(1.0 / (opts->b * opts->b)) : 0.0f;
+    const double ia = 0.7 * opts->a, ib = 0.7 * opts->b;
+    std::memcpy(&v.ap_ia_bits, &ia, 8);
+    std::memcpy(&v.ap_ib_bits, &ib, 8);
     *out = L;
     return TRK_OK;
 }

@@ -48,7 +48,7 @@ struct LatticeView {
     int32_t ap_type;
     double ap_a, ap_b;
     long long ap_a_bits, ap_b_bits;   // bit patterns of a, b (> 0): |x| <= a as integers
-    float ap_ia2f, ap_ib2f;           // 1/a^2, 1/b^2 for the FP32 ellipse pre-filter
+    long long ap_ia_bits, ap_ib_bits; // bit patterns of 0.7 a, 0.7 b: inner box of the ellipse
 };
 
 // Device-resident bunch state.

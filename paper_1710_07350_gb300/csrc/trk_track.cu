@@ -18,11 +18,12 @@
 namespace trk {
 namespace {
 
-// Series are used below this argument: the first dropped binomial term is
-// then below 4e-18 relative.
-constexpr float kSeriesMax = 6.103515625e-05f;  // 2^-14
+// Series are used below 2^-14: the first dropped binomial term is then below
+// 4e-18 relative.  v >= 0 (a sum of squares) or NaN, so the test is an integer
+// compare of the high word (NaN fails it and takes the exact branch).
+constexpr int kSeriesMaxHi = 0x3F100000;  // high word of 2^-14
 
-__device__ __forceinline__ bool series_ok(double v) { return __double2float_rz(v) < kSeriesMax; }
+__device__ __forceinline__ bool series_ok(double v) { return __double2hiint(v) < kSeriesMaxHi; }
 
 struct Part {
     double x, xp, y, yp, l, d;
@@ -203,10 +204,12 @@ __device__ __forceinline__ bool inside(const Part &q, const LatticeView &L) {
         return (ax <= L.ap_a_bits) & (ay <= L.ap_b_bits);
     }
     if (L.ap_type == TRK_APERTURE_ELLIPSE) {
-        const float xf = __double2float_rn(q.x), yf = __double2float_rn(q.y);
-        const float r = xf * xf * L.ap_ia2f + yf * yf * L.ap_ib2f;
-        if (r < 0.9999f) return true;
-        if (r > 1.0001f) return false;
+        // |x| <= 0.7 a and |y| <= 0.7 b is inside ((0.7)^2 + (0.7)^2 < 1): integer
+        // compares of the bit patterns; otherwise the exact test, rounded as
+        // (x/a)^2 + (y/b)^2 <= 1 in IEEE double.
+        const long long ax = __double_as_longlong(q.x) & 0x7fffffffffffffffll;
+        const long long ay = __double_as_longlong(q.y) & 0x7fffffffffffffffll;
+        if ((ax <= L.ap_ia_bits) & (ay <= L.ap_ib_bits)) return true;
         const double u = __ddiv_rn(q.x, L.ap_a), v = __ddiv_rn(q.y, L.ap_b);
         return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
     }
@@ -278,7 +281,8 @@ __device__ __forceinline__ void tile_moments(const Part (&q)[P], const bool (&al
 #pragma unroll
                 for (int k = j; k < 6; ++k, ++m) out[m] = tot[m] - s1[j] * s1[k] * in;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) K[j] = out[1 + j];
+            for (int j = 0; j < 6; ++j)
+                if (isfinite(out[1 + j])) K[j] = out[1 + j];
         } else {
 #pragma unroll
             for (int j = 1; j < kMomentsN; ++j) out[j] = 0.0;
@@ -302,7 +306,11 @@ __device__ __forceinline__ void tile_mean(const Part (&q)[P], const bool (&alive
         v[4] += q[p].yp; v[5] += q[p].l; v[6] += q[p].d;
     }
     block_sum28(v, sh, tot);
-    if (threadIdx.x < 6) K[threadIdx.x] = tot[0] > 0.0 ? tot[1 + threadIdx.x] / tot[0] : 0.0;
+    if (threadIdx.x < 6) {
+        // A particle that is about to be lost may be non-finite: fall back to 0.
+        const double m = tot[0] > 0.0 ? tot[1 + threadIdx.x] / tot[0] : 0.0;
+        K[threadIdx.x] = isfinite(m) ? m : 0.0;
+    }
     __syncthreads();
 }
 

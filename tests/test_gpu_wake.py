@@ -66,8 +66,8 @@ def test_c3_linac_reduced():
     z = syn.bunch("c3", n=20_000)
     g = gpu_track(lat, z, 1, schedule={"block": 128, "per_thread": 2})
     o = orc.track(lat, z, 1)
-    compare_tracking(g, o, TOL_PASS)
-    compare_moments(g["moments"], o["moments"], tol=1e-11)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
     assert g["p0c"] == o["p0c"]
 
 
@@ -79,5 +79,5 @@ def test_wake_last_and_first_element():
     z = syn.bunch("c3", n=3000)
     g = gpu_track(lat, z, 2)
     o = orc.track(lat, z, 2)
-    compare_tracking(g, o, TOL_PASS * 10)
-    compare_moments(g["moments"], o["moments"], tol=1e-11)
+    err = compare_tracking(g, o, TOL_PASS * 10)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
