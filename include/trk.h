@@ -141,8 +141,9 @@ trk_status trk_bunch_free(trk_bunch *b);
 trk_status trk_bunch_set_p0c(trk_bunch *b, double p0c_ev);
 trk_status trk_bunch_p0c(trk_bunch *b, double *p0c_ev);
 
-/* Launch schedule: threads per block (64..512, multiple of 32), particles per
- * thread (1 or 2), turns per fused launch between compactions (>= 1).  Zero
+/* Launch schedule: threads per block (64..256, multiple of 32), particles per
+ * thread (1, 2 or 4, advanced in lock-step), turns per fused launch between
+ * compactions (>= 1).  Zero
  * fields keep the current value. */
 typedef struct {
     int32_t block;

@@ -382,8 +382,8 @@ extern "C" trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s
     if (!b || !s) return fail(TRK_EINVAL, "trk_bunch_set_schedule: NULL argument");
     if (s->block && (s->block < 64 || s->block > 256 || s->block % 32))
         return fail(TRK_EINVAL, "trk_bunch_set_schedule: block must be 64..256, a multiple of 32");
-    if (s->per_thread && s->per_thread != 1 && s->per_thread != 2)
-        return fail(TRK_EINVAL, "trk_bunch_set_schedule: per_thread must be 1 or 2");
+    if (s->per_thread && s->per_thread != 1 && s->per_thread != 2 && s->per_thread != 4)
+        return fail(TRK_EINVAL, "trk_bunch_set_schedule: per_thread must be 1, 2 or 4");
     if (s->chunk_turns < 0) return fail(TRK_EINVAL, "trk_bunch_set_schedule: chunk_turns must be >= 0");
     if (s->block) b->block = s->block;
     if (s->per_thread) b->per_thread = s->per_thread;

@@ -25,160 +25,273 @@ constexpr int kSeriesMaxHi = 0x3F100000;  // high word of 2^-14
 
 __device__ __forceinline__ bool series_ok(double v) { return __double2hiint(v) < kSeriesMaxHi; }
 
-struct Part {
-    double x, xp, y, yp, l, d;
+// The P particles a thread owns, advanced in lock-step through every element so
+// that their independent FP64 chains interleave (the pipe's latency is long
+// compared with one particle's dependent drift-kick chain).
+template <int P>
+struct Tile {
+    double x[P], xp[P], y[P], yp[P], l[P], d[P];
 };
 
-__device__ __forceinline__ double pget(const Part &q, int j) {
-    double r = q.x;
-    r = (j == 1) ? q.xp : r;
-    r = (j == 2) ? q.y : r;
-    r = (j == 3) ? q.yp : r;
-    r = (j == 4) ? q.l : r;
-    r = (j == 5) ? q.d : r;
+template <int P>
+__device__ __forceinline__ double tget(const Tile<P> &q, int p, int j) {
+    double r = q.x[p];
+    r = (j == 1) ? q.xp[p] : r;
+    r = (j == 2) ? q.y[p] : r;
+    r = (j == 3) ? q.yp[p] : r;
+    r = (j == 4) ? q.l[p] : r;
+    r = (j == 5) ? q.d[p] : r;
     return r;
 }
 
-__device__ __forceinline__ DevElem load_elem(const DevElem *p) {
-    DevElem e;
-    const int4 *src = reinterpret_cast<const int4 *>(p);
-    int4 *dst = reinterpret_cast<int4 *>(&e);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) dst[i] = __ldg(src + i);
-    return e;
+// Exact fallbacks for arguments outside the series range.  They are kept out of
+// line so that the compiler cannot if-convert them into the hot path (where they
+// would execute for every particle); they run only when a particle needs them.
+__device__ __noinline__ double rsqrt_exact(double s) { return rsqrt(s); }
+
+__device__ __noinline__ double edrift_exact_g(double v) { return v / (sqrt(1.0 + v) + 1.0); }
+
+__device__ __noinline__ double2 drift_exact(double px, double py, double d, double h, double l) {
+    const double Pm = 1.0 + d;
+    const double t = h * rsqrt(fma(-px, px, fma(-py, py, Pm * Pm)));
+    return make_double2(t, fma(t, Pm, l - h));
+}
+
+__device__ __noinline__ bool ellipse_exact(double x, double y, double a, double b) {
+    const double u = __ddiv_rn(x, a), v = __ddiv_rn(y, b);
+    return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
 }
 
 // ---------------------------------------------------------------- map ----
 // x_i <- C_i + R x + T x x + U x x x from the input vector (simultaneous).
-__device__ __forceinline__ void apply_map(Part &q, const DevElem &E, const DevTerm *__restrict__ terms,
-                                          bool &dirty) {
-    const Part in = q;
-    const double2 *t = reinterpret_cast<const double2 *>(terms + E.term0);
-    double out[6];
+template <int P>
+__device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E, const DevTerm *__restrict__ terms,
+                                      bool &dirty) {
+    const Tile<P> in = q;
+    const uint32_t flags = __ldg(&E->flags);
+    const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
+    const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
+    const double2 *t = reinterpret_cast<const double2 *>(terms + __ldg(&E->term0));
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-        double acc = ((E.flags >> r) & 1u) ? pget(in, r) : 0.0;
-        const int kb = E.rb[r], ke = E.rb[r + 1];
+        double acc[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p] = ((flags >> r) & 1u) ? tget(in, p, r) : 0.0;
+        const int kb = rb[r], ke = rb[r + 1];
         for (int k = kb; k < ke; ++k) {
             const double2 tv = __ldg(t + k);
             const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
-            const int deg = code & 3;
-            double m = 1.0;
-            if (deg >= 1) m = pget(in, (code >> 2) & 7);
-            if (deg >= 2) m *= pget(in, (code >> 5) & 7);
-            if (deg >= 3) m *= pget(in, (code >> 8) & 7);
-            acc = fma(tv.x, m, acc);
+            const int deg = code & 3, j = (code >> 2) & 7, jk = (code >> 5) & 7, jl = (code >> 8) & 7;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                double m = 1.0;
+                if (deg >= 1) m = tget(in, p, j);
+                if (deg >= 2) m *= tget(in, p, jk);
+                if (deg >= 3) m *= tget(in, p, jl);
+                acc[p] = fma(tv.x, m, acc[p]);
+            }
         }
-        out[r] = acc;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (r == 0) q.x[p] = acc[p];
+            if (r == 1) q.xp[p] = acc[p];
+            if (r == 2) q.y[p] = acc[p];
+            if (r == 3) q.yp[p] = acc[p];
+            if (r == 4) q.l[p] = acc[p];
+            if (r == 5) q.d[p] = acc[p];
+        }
     }
-    q.x = out[0]; q.xp = out[1]; q.y = out[2]; q.yp = out[3]; q.l = out[4]; q.d = out[5];
-    if (E.flags & 64u) dirty = true;
+    if (flags & 64u) dirty = true;
 }
 
 // -------------------------------------------------------- exact drift ----
-// x += L x', y += L y', l += L (sqrt(1 + v) - 1), v = x'^2 + y'^2.
-__device__ __forceinline__ void edrift(Part &q, double L) {
-    q.x = fma(L, q.xp, q.x);
-    q.y = fma(L, q.yp, q.y);
-    const double v = fma(q.xp, q.xp, q.yp * q.yp);
-    double g;
-    if (series_ok(v)) {
-        // sqrt(1+v) - 1 = v/2 - v^2/8 + v^3/16 - 5 v^4/128 + ...
-        g = v * fma(v, fma(v, fma(v, -0.0390625, 0.0625), -0.125), 0.5);
-    } else {
-        g = v / (sqrt(1.0 + v) + 1.0);
+// x += L x', y += L y', l += L (sqrt(1 + v) - 1), v = x'^2 + y'^2; for v < 2^-14
+// sqrt(1+v) - 1 = v/2 - v^2/8 + v^3/16 - 5 v^4/128 to FP64 rounding.
+template <int P>
+__device__ __forceinline__ void v_edrift(Tile<P> &q, double L) {
+    double g[P];
+    bool need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+        g[p] = v * fma(v, fma(v, fma(v, -0.0390625, 0.0625), -0.125), 0.5);
+        need |= !series_ok(v);
+        q.x[p] = fma(L, q.xp[p], q.x[p]);
+        q.y[p] = fma(L, q.yp[p], q.y[p]);
     }
-    q.l = fma(L, g, q.l);
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+            if (!series_ok(v)) g[p] = edrift_exact_g(v);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) q.l[p] = fma(L, g[p], q.l[p]);
 }
 
 // ------------------------------------------------ kick-drift multipole ----
 // Exact-Hamiltonian drift in canonical momenta: pz = P sqrt(1 - u),
 // u = (px^2 + py^2)/P^2, so h/pz = (h/P)(1 + g) and h (P/pz - 1) = h g with
-// g = (1 - u)^(-1/2) - 1 = u/2 + 3u^2/8 + 5u^3/16 + ...
-__device__ __forceinline__ void drift_c(double &x, double &y, double &l, double px, double py, double P,
-                                        double iP2, double h, double hiP) {
-    const double u = fma(px, px, py * py) * iP2;
-    double t;
-    if (series_ok(u)) {
-        const double g = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
-        l = fma(h, g, l);
-        t = fma(hiP, g, hiP);
-    } else {
-        const double r = rsqrt(fma(-px, px, fma(-py, py, P * P)));
-        t = h * r;
-        l = fma(t, P, l - h);
+// g = (1 - u)^(-1/2) - 1 = u/2 + 3u^2/8 + 5u^3/16 + ... (exact form for u >= 2^-14).
+template <int P>
+__device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (&l)[P], const double (&px)[P],
+                                        const double (&py)[P], const double (&d)[P], const double (&iP2)[P],
+                                        const double (&hiP)[P], double h) {
+    double t[P], ln[P];
+    bool need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
+        const double u2 = u * u;
+        const double g = fma(u2, fma(u, 0.3125, 0.375), 0.5 * u);
+        t[p] = fma(hiP[p], g, hiP[p]);
+        ln[p] = fma(h, g, l[p]);
+        need |= !series_ok(u);
     }
-    x = fma(t, px, x);
-    y = fma(t, py, y);
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
+            if (!series_ok(u)) {
+                const double2 r = drift_exact(px[p], py[p], d[p], h, l[p]);
+                t[p] = r.x;
+                ln[p] = r.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        x[p] = fma(t[p], px[p], x[p]);
+        y[p] = fma(t[p], py[p], y[p]);
+        l[p] = ln[p];
+    }
 }
 
-__device__ __forceinline__ void kick_c(double x, double y, double &px, double &py, uint32_t fl, double a,
-                                       double hb, double b) {
+template <int P>
+__device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&px)[P], double (&py)[P],
+                                       uint32_t fl, const double *kp) {
+    const double a = __ldg(kp), hb = __ldg(kp + 2), b = __ldg(kp + 4);
     if (fl & 1u) {
-        px = fma(-a, x, px);
-        py = fma(a, y, py);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            px[p] = fma(-a, x[p], px[p]);
+            py[p] = fma(a, y[p], py[p]);
+        }
     }
     if (fl & 2u) {
-        const double t = (x - y) * (x + y);
-        px = fma(-hb, t, px);
-        py = fma(b, x * y, py);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double t = (x[p] - y[p]) * (x[p] + y[p]);
+            px[p] = fma(-hb, t, px[p]);
+            py[p] = fma(b, x[p] * y[p], py[p]);
+        }
     }
 }
 
 // n steps of the 4th-order Yoshida scheme D K D K D K D with adjacent drifts of
 // consecutive steps merged; slopes converted to canonical momenta at entry and
 // back at exit.
-__device__ __forceinline__ void kick_drift(Part &q, double &iP, bool &dirty, const DevElem &E) {
-    const double P = 1.0 + q.d;
+template <int P>
+__device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &dirty,
+                                             const DevElem *__restrict__ E) {
     if (dirty) {
-        iP = 1.0 / P;
+#pragma unroll
+        for (int p = 0; p < P; ++p) iP[p] = 1.0 / (1.0 + q.d[p]);
         dirty = false;
     }
-    const double iP2 = iP * iP;
-    const double v = fma(q.xp, q.xp, q.yp * q.yp);
+    const int n = __ldg(&E->n);
+    const uint32_t fl = __ldg(&E->flags);
+    const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
+    const double *k1p = &E->p[3], *k0p = &E->p[4];  // a, hb, b at stride 2
+    double px[P], py[P], iP2[P], h1[P], h2[P], hm[P];
+    bool need = false;
     // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
-    const double c = series_ok(v) ? fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0) : rsqrt(1.0 + v);
-    const double pc = P * c;
-    double px = pc * q.xp, py = pc * q.yp;
-    double x = q.x, y = q.y, l = q.l;
-    const double d1 = E.p[0], d2 = E.p[1], dm = E.p[2];
-    const double hd1 = d1 * iP, hd2 = d2 * iP, hdm = dm * iP;
-    const uint32_t fl = E.flags;
-    drift_c(x, y, l, px, py, P, iP2, d1, hd1);
-    for (int s = 0; s < E.n; ++s) {
-        kick_c(x, y, px, py, fl, E.p[3], E.p[5], E.p[7]);
-        drift_c(x, y, l, px, py, P, iP2, d2, hd2);
-        kick_c(x, y, px, py, fl, E.p[4], E.p[6], E.p[8]);
-        drift_c(x, y, l, px, py, P, iP2, d2, hd2);
-        kick_c(x, y, px, py, fl, E.p[3], E.p[5], E.p[7]);
-        if (s + 1 < E.n)
-            drift_c(x, y, l, px, py, P, iP2, dm, hdm);
-        else
-            drift_c(x, y, l, px, py, P, iP2, d1, hd1);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        iP2[p] = iP[p] * iP[p];
+        h1[p] = d1 * iP[p];
+        h2[p] = d2 * iP[p];
+        hm[p] = dm * iP[p];
+        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+        const double c = fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0);
+        const double pc = (1.0 + q.d[p]) * c;
+        px[p] = pc * q.xp[p];
+        py[p] = pc * q.yp[p];
+        need |= !series_ok(v);
     }
-    const double u = fma(px, px, py * py) * iP2;
-    const double ipz = series_ok(u) ? fma(iP, u * fma(u, fma(u, 0.3125, 0.375), 0.5), iP)
-                                    : rsqrt(fma(-px, px, fma(-py, py, P * P)));
-    q.x = x; q.y = y; q.l = l;
-    q.xp = px * ipz;
-    q.yp = py * ipz;
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+            if (!series_ok(v)) {
+                const double pc = (1.0 + q.d[p]) * rsqrt_exact(1.0 + v);
+                px[p] = pc * q.xp[p];
+                py[p] = pc * q.yp[p];
+            }
+        }
+    }
+    v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h1, d1);
+    for (int s = 0; s < n; ++s) {
+        v_kick<P>(q.x, q.y, px, py, fl, k1p);
+        v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h2, d2);
+        v_kick<P>(q.x, q.y, px, py, fl, k0p);
+        v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h2, d2);
+        v_kick<P>(q.x, q.y, px, py, fl, k1p);
+        if (s + 1 < n)
+            v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, hm, dm);
+        else
+            v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h1, d1);
+    }
+    need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
+        const double ipz = fma(iP[p], u * fma(u, fma(u, 0.3125, 0.375), 0.5), iP[p]);
+        need |= !series_ok(u);
+        q.xp[p] = px[p] * ipz;
+        q.yp[p] = py[p] * ipz;
+    }
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
+            if (!series_ok(u)) {
+                const double Pm = 1.0 + q.d[p];
+                const double ipz = rsqrt_exact(fma(-px[p], px[p], fma(-py[p], py[p], Pm * Pm)));
+                q.xp[p] = px[p] * ipz;
+                q.yp[p] = py[p] * ipz;
+            }
+        }
+    }
 }
 
-__device__ __forceinline__ void thin_sext(Part &q, const DevElem &E) {
-    const double t = (q.x - q.y) * (q.x + q.y);
-    q.xp = fma(-E.p[1], t, q.xp);
-    q.yp = fma(E.p[0], q.x * q.y, q.yp);
+template <int P>
+__device__ __forceinline__ void v_thin_sext(Tile<P> &q, const DevElem *__restrict__ E) {
+    const double k = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double t = (q.x[p] - q.y[p]) * (q.x[p] + q.y[p]);
+        q.xp[p] = fma(-hk, t, q.xp[p]);
+        q.yp[p] = fma(k, q.x[p] * q.y[p], q.yp[p]);
+    }
 }
 
 // Thin RF: P = (1+delta) p0, P' = P + V cos(phi + k l), delta' = P'/p0' - 1,
 // slopes scaled by P/P'.
-__device__ __forceinline__ void rfca(Part &q, const DevElem &E, double p0, double ip01, bool &dirty) {
-    const double P = (1.0 + q.d) * p0;
-    const double P1 = fma(E.p[0], cos(fma(E.p[2], q.l, E.p[1])), P);
-    const double s = P / P1;
-    q.xp *= s;
-    q.yp *= s;
-    q.d = fma(P1, ip01, -1.0);
+template <int P>
+__device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E, double p0, double ip01,
+                                       bool &dirty) {
+    const double V = __ldg(&E->p[0]), phi = __ldg(&E->p[1]), k = __ldg(&E->p[2]);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double Pp = (1.0 + q.d[p]) * p0;
+        const double P1 = fma(V, cos(fma(k, q.l[p], phi)), Pp);
+        const double s = Pp / P1;
+        q.xp[p] *= s;
+        q.yp[p] *= s;
+        q.d[p] = fma(P1, ip01, -1.0);
+    }
     dirty = true;
 }
 
@@ -197,21 +310,20 @@ __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, b
 }
 
 // Aperture: edge counts as inside, NaN as outside.
-__device__ __forceinline__ bool inside(const Part &q, const LatticeView &L) {
+__device__ __forceinline__ bool inside(double x, double y, const LatticeView &L) {
     if (L.ap_type == TRK_APERTURE_RECT) {
-        const long long ax = __double_as_longlong(q.x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(q.y) & 0x7fffffffffffffffll;
+        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
+        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
         return (ax <= L.ap_a_bits) & (ay <= L.ap_b_bits);
     }
     if (L.ap_type == TRK_APERTURE_ELLIPSE) {
         // |x| <= 0.7 a and |y| <= 0.7 b is inside ((0.7)^2 + (0.7)^2 < 1): integer
         // compares of the bit patterns; otherwise the exact test, rounded as
         // (x/a)^2 + (y/b)^2 <= 1 in IEEE double.
-        const long long ax = __double_as_longlong(q.x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(q.y) & 0x7fffffffffffffffll;
+        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
+        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
         if ((ax <= L.ap_ia_bits) & (ay <= L.ap_ib_bits)) return true;
-        const double u = __ddiv_rn(q.x, L.ap_a), v = __ddiv_rn(q.y, L.ap_b);
-        return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
+        return ellipse_exact(x, y, L.ap_a, L.ap_b);
     }
     return true;
 }
@@ -241,7 +353,7 @@ __device__ __forceinline__ void block_sum28(double (&v)[kMomentsN], double *sh, 
 }
 
 template <int P>
-__device__ __forceinline__ void tile_moments(const Part (&q)[P], const bool (&alive)[P], double *sh, double *tot,
+__device__ __forceinline__ void tile_moments(const Tile<P> &q, const bool (&alive)[P], double *sh, double *tot,
                                              double *K, double *out) {
     double v[kMomentsN];
 #pragma unroll
@@ -249,8 +361,8 @@ __device__ __forceinline__ void tile_moments(const Part (&q)[P], const bool (&al
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (!alive[p]) continue;
-        const double d[6] = {q[p].x - K[0], q[p].xp - K[1], q[p].y - K[2],
-                             q[p].yp - K[3], q[p].l - K[4], q[p].d - K[5]};
+        const double d[6] = {q.x[p] - K[0], q.xp[p] - K[1], q.y[p] - K[2],
+                             q.yp[p] - K[3], q.l[p] - K[4], q.d[p] - K[5]};
         v[0] += 1.0;
         int m = 7;
 #pragma unroll
@@ -293,7 +405,7 @@ __device__ __forceinline__ void tile_moments(const Part (&q)[P], const bool (&al
 
 // Initial moment shift: the tile's mean (keeps the shifted sums well conditioned).
 template <int P>
-__device__ __forceinline__ void tile_mean(const Part (&q)[P], const bool (&alive)[P], double *sh, double *tot,
+__device__ __forceinline__ void tile_mean(const Tile<P> &q, const bool (&alive)[P], double *sh, double *tot,
                                           double *K) {
     double v[kMomentsN];
 #pragma unroll
@@ -302,8 +414,8 @@ __device__ __forceinline__ void tile_mean(const Part (&q)[P], const bool (&alive
     for (int p = 0; p < P; ++p) {
         if (!alive[p]) continue;
         v[0] += 1.0;
-        v[1] += q[p].x; v[2] += q[p].xp; v[3] += q[p].y;
-        v[4] += q[p].yp; v[5] += q[p].l; v[6] += q[p].d;
+        v[1] += q.x[p]; v[2] += q.xp[p]; v[3] += q.y[p];
+        v[4] += q.yp[p]; v[5] += q.l[p]; v[6] += q.d[p];
     }
     block_sum28(v, sh, tot);
     if (threadIdx.x < 6) {
@@ -315,6 +427,37 @@ __device__ __forceinline__ void tile_mean(const Part (&q)[P], const bool (&alive
 }
 
 constexpr int kMaxBlock = 512;
+
+template <int P>
+__device__ __forceinline__ void store_particle(const TrackArgs &a, int64_t i, const Tile<P> &q, int p) {
+    a.coords[i] = q.x[p];
+    a.coords[a.pitch + i] = q.xp[p];
+    a.coords[2 * a.pitch + i] = q.y[p];
+    a.coords[3 * a.pitch + i] = q.yp[p];
+    a.coords[4 * a.pitch + i] = q.l[p];
+    a.coords[5 * a.pitch + i] = q.d[p];
+}
+
+// Check the aperture of every alive particle after element e; a particle that
+// is lost is written out at once (coordinates at the loss point and the loss
+// record) and its registers are zeroed so that it keeps taking the fast paths.
+template <int P>
+__device__ __forceinline__ void apply_aperture(const TrackArgs &a, const LatticeView &L, Tile<P> &q,
+                                               bool (&alive)[P], int64_t base, int turn, int e, int &lost_here) {
+    if (L.ap_type == TRK_APERTURE_NONE) return;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (alive[p] && !inside(q.x[p], q.y[p], L)) {
+            const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
+            store_particle<P>(a, i, q, p);
+            a.loss_turn[i] = turn;
+            a.loss_elem[i] = e;
+            alive[p] = false;
+            q.x[p] = q.xp[p] = q.y[p] = q.yp[p] = q.l[p] = q.d[p] = 0.0;
+            ++lost_here;
+        }
+    }
+}
 
 template <int P>
 __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
@@ -329,29 +472,24 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
     const int64_t base = (int64_t)blockIdx.x * T;
     if (base >= n_alive) return;  // whole block beyond the alive range
 
-    Part q[P];
+    Tile<P> q;
     bool alive[P];
-    int lt[P], le[P];
     double iP[P];
-    bool dirty[P];
+    bool dirty = true;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
         alive[p] = false;
-        lt[p] = -1;
-        le[p] = -1;
         iP[p] = 1.0;
-        dirty[p] = true;
-        q[p] = Part{0, 0, 0, 0, 0, 0};
-        if (i < n_alive) {
-            const int32_t l0 = a.loss_turn[i];
-            alive[p] = l0 < 0;
-            q[p].x = a.coords[i];
-            q[p].xp = a.coords[a.pitch + i];
-            q[p].y = a.coords[2 * a.pitch + i];
-            q[p].yp = a.coords[3 * a.pitch + i];
-            q[p].l = a.coords[4 * a.pitch + i];
-            q[p].d = a.coords[5 * a.pitch + i];
+        q.x[p] = q.xp[p] = q.y[p] = q.yp[p] = q.l[p] = q.d[p] = 0.0;
+        if (i < n_alive && a.loss_turn[i] < 0) {
+            alive[p] = true;
+            q.x[p] = a.coords[i];
+            q.xp[p] = a.coords[a.pitch + i];
+            q.y[p] = a.coords[2 * a.pitch + i];
+            q.yp[p] = a.coords[3 * a.pitch + i];
+            q.l[p] = a.coords[4 * a.pitch + i];
+            q.d[p] = a.coords[5 * a.pitch + i];
         }
     }
     if (threadIdx.x == 0) cnt = 0;
@@ -359,6 +497,7 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
 
     const LatticeView &L = a.lat;
     const DevElem *__restrict__ elems = L.elems;
+    int lost_here = 0;
     double p0 = a.p0c;  // reference momentum, identical in every thread
     for (int t = 0; t < a.n_turns; ++t) {
         const int turn = a.turn_abs0 + t;
@@ -371,43 +510,29 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
             const double idl = flat ? 0.0 : 1.0 / dl;
             const double ip0 = 1.0 / p0;
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (!alive[p]) continue;
-                q[p].d = fma(wake_volt(q[p].l, lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q[p].d);
-                dirty[p] = true;
-                if (!inside(q[p], L)) {
-                    alive[p] = false;
-                    lt[p] = turn;
-                    le[p] = a.kick_wake;
-                }
-            }
+            for (int p = 0; p < P; ++p)
+                if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q.d[p]);
+            dirty = true;
+            apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here);
         }
         for (int e = a.e0; e < a.e1; ++e) {
-            const DevElem E = load_elem(elems + e);
-            double p01 = p0, ip01 = 0.0;
-            if (E.type == TRK_RFCA) {
-                p01 = p0 + E.p[3];
-                ip01 = 1.0 / p01;
+            const DevElem *E = elems + e;
+            const int type = __ldg(&E->type);
+            switch (type) {
+            case TRK_MAP: v_map<P>(q, E, L.terms, dirty); break;
+            case TRK_EDRIFT: v_edrift<P>(q, __ldg(&E->p[0])); break;
+            case TRK_KQUAD:
+            case TRK_KSEXT: v_kick_drift<P>(q, iP, dirty, E); break;
+            case TRK_THINSEXT: v_thin_sext<P>(q, E); break;
+            case TRK_RFCA: {
+                const double p01 = p0 + __ldg(&E->p[3]);
+                v_rfca<P>(q, E, p0, 1.0 / p01, dirty);
+                p0 = p01;
+                break;
             }
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (!alive[p]) continue;
-                switch (E.type) {
-                case TRK_MAP: apply_map(q[p], E, L.terms, dirty[p]); break;
-                case TRK_EDRIFT: edrift(q[p], E.p[0]); break;
-                case TRK_KQUAD:
-                case TRK_KSEXT: kick_drift(q[p], iP[p], dirty[p], E); break;
-                case TRK_THINSEXT: thin_sext(q[p], E); break;
-                case TRK_RFCA: rfca(q[p], E, p0, ip01, dirty[p]); break;
-                default: break;
-                }
-                if (!inside(q[p], L)) {
-                    alive[p] = false;
-                    lt[p] = turn;
-                    le[p] = e;
-                }
+            default: break;
             }
-            p0 = p01;
+            apply_aperture<P>(a, L, q, alive, base, turn, e, lost_here);
         }
         if (a.do_moments)
             tile_moments<P>(q, alive, sh, tot, K,
@@ -420,7 +545,7 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (!alive[p]) continue;
-            const unsigned long long k = dkey(q[p].l);
+            const unsigned long long k = dkey(q.l[p]);
             kmin = k < kmin ? k : kmin;
             kmax = k > kmax ? k : kmax;
         }
@@ -450,19 +575,10 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
     int na = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
+        if (!alive[p]) continue;
         const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
-        if (i >= n_alive) continue;
-        a.coords[i] = q[p].x;
-        a.coords[a.pitch + i] = q[p].xp;
-        a.coords[2 * a.pitch + i] = q[p].y;
-        a.coords[3 * a.pitch + i] = q[p].yp;
-        a.coords[4 * a.pitch + i] = q[p].l;
-        a.coords[5 * a.pitch + i] = q[p].d;
-        if (lt[p] >= 0) {
-            a.loss_turn[i] = lt[p];
-            a.loss_elem[i] = le[p];
-        }
-        na += alive[p] ? 1 : 0;
+        store_particle<P>(a, i, q, p);
+        ++na;
     }
     if (a.tile_alive) {
         na = __reduce_add_sync(0xffffffffu, na);
@@ -661,7 +777,9 @@ __global__ void k_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n
 
 cudaError_t launch_track(const TrackArgs &a, int block, int per_thread, int n_tiles, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (per_thread == 2)
+    if (per_thread == 4)
+        k_track<4><<<n_tiles, block, 0, s>>>(a);
+    else if (per_thread == 2)
         k_track<2><<<n_tiles, block, 0, s>>>(a);
     else
         k_track<1><<<n_tiles, block, 0, s>>>(a);
