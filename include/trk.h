@@ -194,6 +194,29 @@ typedef struct {
 trk_status trk_bunch_enable_timing(trk_bunch *b, int32_t on);
 trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t reset);
 
+/* The standalone wake of trk_wake for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it is an addition for code that runs
+ * where allocation is not allowed (inside a fixed memory pool, a host
+ * application that forbids cudaMalloc after start-up, or a device already
+ * full).  The caller passes the particles and the outputs; nothing is
+ * allocated.  The working arrays live in one file-scope device array of fixed
+ * size (nbins <= 16384, 320.25 KiB) that every GPU loading the library holds
+ * until the process exits.
+ *   d_coords   [6 * pitch] FP64 SoA coordinates; all n particles count as alive;
+ *              delta (coordinate 5) receives the kick in place
+ *   q_m        charge / n
+ *   d_hist     [nbins] uint32 counts, d_volt [nbins] FP64 voltages: optional
+ *              caller device outputs (NULL to skip)
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array and leaves its contents to
+ * the next; each call clears what must start at zero, and calls whose work
+ * overlaps on the GPU race on it.  Returns TRK_EINVAL for nbins outside
+ * 1..16384, n < 0, pitch < n or p0c_ev <= 0. */
+trk_status trk_wake_static(double *d_coords, int64_t pitch, int64_t n, int32_t nbins, double w0, double sc,
+                           double charge, double p0c_ev, uint32_t *d_hist, double *d_volt, void *stream);
+
 /* Text for the calling thread's last non-OK status ("" if none). */
 const char *trk_last_error(void);
 

@@ -654,4 +654,6 @@ extern "C" trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t rese
     return TRK_OK;
 }
 
+trk_status trk::set_error(trk_status s, const char *msg) { return fail(s, msg); }
+
 extern "C" const char *trk_last_error(void) { return g_err.c_str(); }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "trk.h"
 
 namespace trk {
@@ -100,6 +102,11 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
                              double w0, double sc, uint32_t *hist, double *wfun, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
                              cudaStream_t s);
+
+// Records the calling thread's error text (returned by trk_last_error) and
+// passes the status through.
+trk_status set_error(trk_status s, const char *msg);
+inline trk_status set_error(trk_status s, const std::string &msg) { return set_error(s, msg.c_str()); }
 
 // Order-preserving 64-bit key of a double (non-NaN) and its inverse.
 __host__ __device__ inline uint64_t dkey(double v) {

@@ -78,6 +78,7 @@ def lib():
             "trk_wake": [P, c_int32, c_double, c_double, c_double, c_double, P, P],
             "trk_bunch_enable_timing": [P, c_int32],
             "trk_bunch_stats": [P, P, c_int32],
+            "trk_wake_static": [P, c_int64, c_int64, c_int32, c_double, c_double, c_double, c_double, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -262,6 +263,15 @@ def trk_bunch_stats(b, reset=False):
     s = trk_stats()
     _check(lib().trk_bunch_stats(b.handle, ctypes.byref(s), 1 if reset else 0))
     return {"track_kernel_ms": s.track_kernel_ms, "track_launches": s.track_launches, "launches": s.launches}
+
+
+def trk_wake_static(coords, n, nbins, w0, sc, charge, p0c, hist=None, volt=None, stream=None):
+    """Allocation-free standalone wake on a (6, pitch) float64 CUDA tensor."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(coords.device)
+    _check(lib().trk_wake_static(_dptr(coords), coords.shape[1], n, nbins, w0, sc, charge, p0c,
+                                 _dptr(hist), _dptr(volt), c_void_p(stream.cuda_stream)))
 
 
 def download(b):
