@@ -208,3 +208,16 @@ def bunch(name, n=None, seed=None):
 def c4_bunch(v, n):
     """Bunch of c4 variant v (its own Philox key, disjoint from the variant draw)."""
     return gaussian_bunch(n, (4 << 16) + v, twiss("c1"))
+
+
+def mlp_init(seed=7):
+    """Initial surrogate weights, [(W (out, in) float32, b (out,) float32)] for
+    8 -> 256 -> 256 -> 256 -> 256 -> 1: W uniform on +-sqrt(6/fan_in) (He), b = 0."""
+    g = np.random.Generator(np.random.Philox(key=seed))
+    dims = [8, 256, 256, 256, 256, 1]
+    out = []
+    for i in range(5):
+        lim = math.sqrt(6.0 / dims[i])
+        W = g.uniform(-lim, lim, size=(dims[i + 1], dims[i])).astype(np.float32)
+        out.append((W, np.zeros(dims[i + 1], np.float32)))
+    return out
