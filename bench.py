@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--block", type=int, default=128)
-    p.add_argument("--per-thread", type=int, default=1)
+    p.add_argument("--per-thread", type=int, default=2)
     # smaller cases for profiling runs only (the bench line uses the defaults)
     p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
     p.add_argument("--particles", type=int, default=N_PARTICLES)

@@ -149,7 +149,9 @@ typedef struct {
     int32_t block;
     int32_t per_thread;
     int32_t chunk_turns;
-    int32_t pad;
+    int32_t growth;      /* batched calls: 0 = every chunk chunk_turns long; g >= 2 =
+                            chunks grow by g from chunk_turns up to 128 turns (dense
+                            warps while many particles are lost early) */
 } trk_schedule;
 trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s);
 
@@ -181,6 +183,107 @@ trk_status trk_n_alive(trk_bunch *b, int64_t *n_alive);
  * optional caller device outputs (NULL to skip).  Asynchronous. */
 trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc, double charge,
                     double p0c_ev, uint32_t *d_hist, double *d_volt);
+
+/* Batched tracking (many lattice variants with uneven particle counts in one
+ * launch per turn chunk; no counterpart in the paper, which tracks one beamline).
+ * A batch pairs bunch v with lattice v; every bunch must use the same stream and
+ * no lattice may contain TRK_WAKE (TRK_EUNSUPPORTED).  trk_batch_track runs
+ * n_turns turns of every pair: per chunk one fused launch over all (variant,
+ * tile) items, then moment finalisation and stable compaction of every variant;
+ * all chunks of a call are one CUDA graph, captured on the first call with a
+ * given n_turns and schedule and replayed afterwards.  Per-bunch results
+ * (trk_moments, trk_lost, trk_n_alive) are as after trk_track.  The batch only
+ * borrows the bunches and lattices; they must outlive it. */
+typedef struct trk_batch trk_batch;
+trk_status trk_batch_create(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                            trk_batch **out);
+trk_status trk_batch_set_schedule(trk_batch *B, const trk_schedule *s);
+trk_status trk_batch_get_schedule(const trk_batch *B, trk_schedule *s);
+trk_status trk_batch_track(trk_batch *B, int32_t n_turns);
+trk_status trk_batch_destroy(trk_batch *B);
+/* One-shot form: create, set the schedule (if sched != NULL), track, destroy. */
+trk_status trk_track_batch(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                           int32_t n_turns, const trk_schedule *sched);
+
+/* Dynamic-aperture survival (no counterpart in the paper).  Variant v's points
+ * are [offsets[v], offsets[v+1]) of the device arrays d_x0, d_y0 [m]; a particle
+ * starts at (x0, 0, y0, 0, 0, 0) and is tracked through lattice v for up to
+ * n_turns turns (batched, as trk_batch_track; the lattices' apertures decide
+ * losses; create them with moments = 0 to skip the moment sums).
+ * d_survival[p] (int32, device) receives the 1-based turn in which particle p
+ * was lost, or n_turns + 1 if it survived.  offsets is a HOST array of n_var+1
+ * entries starting at 0.  sched = NULL uses block 128, 2 particles per thread,
+ * chunks of 1, 2, 4, ... 128 turns.  Allocates its particle arrays and
+ * synchronises the stream before returning. */
+trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
+                           const double *d_x0, const double *d_y0, int32_t n_turns, const trk_schedule *sched,
+                           int32_t *d_survival, void *stream);
+
+/* MLP surrogate for dynamic-aperture triage (no counterpart in the paper).
+ * Fixed architecture 8 -> 4 x [Linear 256 + GELU(erf)] -> Linear 256 -> 1 logit.
+ * FP32 master weights and biases with BF16 copies; BF16 activations into the
+ * tensor-core products (mma.sync, FP32 accumulation); BCE loss on the logit;
+ * Adam (Kingma & Ba).  Rounding points: h0 = bf16(x), z = h W^T + b (FP32),
+ * h = bf16(gelu(z)); dz = dh * gelu'(z) (FP32) rounded to BF16 for dW = dz^T h
+ * and dh = dz W; db = sum dz (FP32).
+ *   W[l], b[l]   HOST FP32 arrays, W[l] row-major [out][in]: l = 0: 256 x 8,
+ *                l = 1..3: 256 x 256, l = 4: 1 x 256; b[l] [out]
+ *   d_X          device FP32 [M][8] inputs; d_y device FP32 [M] labels (0/1)
+ * trk_mlp_forward writes logits (device FP32 [M]); trk_mlp_grad computes the
+ * gradients of the mean loss of M rows (kept inside; d_loss device FP32 [1]
+ * or NULL); trk_mlp_adam applies one Adam step with them; trk_mlp_train runs
+ * epochs over n rows in batches (d_perm: device int32 [epochs][n] row order
+ * per epoch, or NULL for the stored order; d_loss_hist: device FP32, one
+ * entry per step, or NULL).  trk_mlp_get copies weights, biases and the last
+ * gradients to host arrays of the layout above (NULL entries skipped) and
+ * synchronises.  All calls are asynchronous on `stream` except trk_mlp_get and
+ * trk_mlp_train (which synchronises at the end). */
+typedef struct trk_mlp trk_mlp;
+trk_status trk_mlp_create(const float *const *W, const float *const *b, trk_mlp **out);
+trk_status trk_mlp_destroy(trk_mlp *net);
+trk_status trk_mlp_forward(trk_mlp *net, const float *d_X, int64_t M, float *d_logits, void *stream);
+trk_status trk_mlp_grad(trk_mlp *net, const float *d_X, const float *d_y, int32_t M, float *d_loss, void *stream);
+trk_status trk_mlp_adam(trk_mlp *net, float lr, float beta1, float beta2, float eps, void *stream);
+trk_status trk_mlp_train(trk_mlp *net, const float *d_X, const float *d_y, int64_t n, int32_t batch,
+                         int32_t epochs, const int32_t *d_perm, float lr, float *d_loss_hist, void *stream);
+trk_status trk_mlp_get(trk_mlp *net, float *const *W, float *const *b, float *const *gW, float *const *gb);
+
+/* Surrogate-triaged dynamic-aperture scan (no counterpart in the paper).  For
+ * every variant v and cell (ix, iy) of an nx x ny grid (cell centres
+ * -w + (i + 1/2) 2w/n, w = half_width):
+ *   1. the coarse cells (every coarse_stride-th cell from stride/2) are tracked
+ *      exactly (trk_da_survival);
+ *   2. use_mlp = 1: the network is trained on them (features x/w, y/w and the
+ *      variant's 6 normalised parameters d_params[v][6]; label = survives all
+ *      n_turns) with trk_mlp_train(epochs, batch, lr, d_perm) and predicts every
+ *      cell (logit > 0 = survives); use_mlp = 0: every cell takes the label of
+ *      its nearest coarse cell;
+ *   3. cells within Chebyshev distance band_radius of a predicted-boundary cell
+ *      (8-neighbourhood holding both classes), and the caller's audit cells
+ *      (d_audit[v][iy][ix] != 0, optional), are re-tracked exactly in FP64;
+ *   4. d_mask (uint8 [n_var][ny][nx], 1 = survives) and d_survival (int32,
+ *      1-based loss turn or n_turns + 1 where tracked; n_turns + 1 or 0 from the
+ *      prediction elsewhere) receive the merged result; stats (host) counts
+ *      cells and audit disagreements and times each phase.
+ * Allocates its working arrays and synchronises `stream`. */
+typedef struct {
+    int32_t nx, ny;
+    double half_width;
+    int32_t n_turns;
+    int32_t coarse_stride;
+    int32_t band_radius;
+    int32_t use_mlp;
+    int32_t epochs, batch;
+    float lr;
+    int32_t pad;
+} trk_triage_opts;
+typedef struct {
+    int64_t n_cells, n_coarse, n_band, n_audit, n_tracked, n_audit_wrong;
+    double ms_coarse, ms_train, ms_infer, ms_band, ms_retrack;
+} trk_triage_stats;
+trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_var, const float *d_params,
+                         const uint8_t *d_audit, trk_mlp *net, const int32_t *d_perm, const trk_triage_opts *opts,
+                         uint8_t *d_mask, int32_t *d_survival, trk_triage_stats *stats, void *stream);
 
 /* Launch statistics of a bunch.  With timing enabled the library records CUDA
  * events on the bunch's stream around every fused tracking launch; the summed

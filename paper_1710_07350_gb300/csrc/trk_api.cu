@@ -436,6 +436,25 @@ static double advance_p0(const trk_lattice *L, int e0, int e1, double p0) {
     return p0;
 }
 
+static CompactArgs compact_args(trk_bunch *b, int tile, int n_tiles) {
+    CompactArgs c;
+    c.coords = b->coords;
+    c.pitch = b->pitch;
+    c.ids = b->ids;
+    c.lt = b->lt;
+    c.le = b->le;
+    c.cb = b->cb;
+    c.ib = b->ib;
+    c.ltb = b->ltb;
+    c.leb = b->leb;
+    c.tile_alive = b->tile_alive;
+    c.tile_off = b->tile_off;
+    c.st = b->st;
+    c.tile = tile;
+    c.n_tiles = n_tiles;
+    return c;
+}
+
 static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     TrackArgs a;
     std::memset(&a, 0, sizeof a);
@@ -451,6 +470,7 @@ static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     a.kick_wake = -1;
     a.minmax_slot = -1;
     a.wake_V = b->V;
+    a.tile = b->block * b->per_thread;
     return a;
 }
 
@@ -539,8 +559,7 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                                              b->moments + (size_t)t0 * kMomentsN, b->stream));
             ++b->launches;
         }
-        TRK_CUDA(launch_compact(b->coords, b->pitch, b->ids, b->lt, b->le, b->cb, b->ib, b->ltb, b->leb,
-                                b->tile_alive, b->tile_off, n_tiles, tile, b->st, b->stream));
+        TRK_CUDA(launch_compact(compact_args(b, tile, n_tiles), n_tiles, b->stream));
         b->launches += 4;
     }
     b->turn += n_turns;
@@ -625,6 +644,299 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     if (d_volt)
         TRK_CUDA(cudaMemcpyAsync(d_volt, b->V, nbins * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     return TRK_OK;
+}
+
+
+// --------------------------------------------------------------- batch ----
+
+struct trk_batch {
+    std::vector<trk_bunch *> b;
+    std::vector<const trk_lattice *> L;
+    int n_var = 0;
+    cudaStream_t stream = nullptr;   // the first bunch's stream: work is launched there
+    cudaStream_t capture = nullptr;  // private stream used only to capture the graph
+    int block = 128, per_thread = 2, chunk = 100, growth = 0;
+    bool moments = false;
+    // device tables
+    TrackArgs *d_args = nullptr;
+    size_t args_cap = 0;
+    CompactArgs *d_cargs = nullptr;
+    int2 *d_items = nullptr;
+    int n_items = 0;
+    std::vector<TrackArgs> h_args;
+    // cached graph of one call of `planned_turns` turns
+    cudaGraphExec_t exec = nullptr;
+    int planned_turns = -1;
+    std::vector<int> chunks;
+};
+
+static std::vector<int> chunk_plan(int n_turns, int first, int growth) {
+    std::vector<int> c;
+    int len = first < 1 ? 1 : first;
+    for (int t = 0; t < n_turns;) {
+        const int k = len < n_turns - t ? len : n_turns - t;
+        c.push_back(k);
+        t += k;
+        if (growth >= 2 && len < 128) len = len * growth > 128 ? 128 : len * growth;
+    }
+    return c;
+}
+
+static void batch_free_graph(trk_batch *B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    B->planned_turns = -1;
+}
+
+extern "C" trk_status trk_batch_create(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                                       trk_batch **out) {
+    if (!out) return fail(TRK_EINVAL, "trk_batch_create: out is NULL");
+    *out = nullptr;
+    if (n_var < 1 || !bunches || !lats) return fail(TRK_EINVAL, "trk_batch_create: need n_var >= 1 bunches and lattices");
+    for (int v = 0; v < n_var; ++v) {
+        if (!bunches[v] || !lats[v]) return fail(TRK_EINVAL, "trk_batch_create: NULL bunch or lattice");
+        if (!lats[v]->wakes.empty())
+            return fail(TRK_EUNSUPPORTED, "trk_batch_create: lattices with TRK_WAKE are tracked with trk_track");
+        if (bunches[v]->stream != bunches[0]->stream)
+            return fail(TRK_EINVAL, "trk_batch_create: all bunches must use the same stream");
+        if (lats[v]->moments != lats[0]->moments)
+            return fail(TRK_EINVAL, "trk_batch_create: all lattices must agree on moments");
+    }
+    auto *B = new trk_batch();
+    B->b.assign(bunches, bunches + n_var);
+    B->L.assign(lats, lats + n_var);
+    B->n_var = n_var;
+    B->stream = bunches[0]->stream;
+    B->moments = lats[0]->moments != 0;
+    if (cudaStreamCreateWithFlags(&B->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        delete B;
+        return fail(TRK_ECUDA, "trk_batch_create: stream creation failed");
+    }
+    *out = B;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_batch_destroy(trk_batch *B) {
+    if (!B) return TRK_OK;
+    cudaStreamSynchronize(B->stream);
+    batch_free_graph(B);
+    cudaFree(B->d_args);
+    cudaFree(B->d_cargs);
+    cudaFree(B->d_items);
+    if (B->capture) cudaStreamDestroy(B->capture);
+    delete B;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_batch_set_schedule(trk_batch *B, const trk_schedule *s) {
+    if (!B || !s) return fail(TRK_EINVAL, "trk_batch_set_schedule: NULL argument");
+    if (s->block && (s->block < 64 || s->block > 256 || s->block % 32))
+        return fail(TRK_EINVAL, "trk_batch_set_schedule: block must be 64..256, a multiple of 32");
+    if (s->per_thread && s->per_thread != 1 && s->per_thread != 2 && s->per_thread != 4)
+        return fail(TRK_EINVAL, "trk_batch_set_schedule: per_thread must be 1, 2 or 4");
+    if (s->chunk_turns < 0 || s->growth < 0 || s->growth == 1)
+        return fail(TRK_EINVAL, "trk_batch_set_schedule: chunk_turns >= 0, growth 0 or >= 2");
+    if (s->block) B->block = s->block;
+    if (s->per_thread) B->per_thread = s->per_thread;
+    if (s->chunk_turns) B->chunk = s->chunk_turns;
+    B->growth = s->growth;
+    batch_free_graph(B);
+    B->n_items = 0;  // re-tile
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_batch_get_schedule(const trk_batch *B, trk_schedule *s) {
+    if (!B || !s) return fail(TRK_EINVAL, "trk_batch_get_schedule: NULL argument");
+    s->block = B->block;
+    s->per_thread = B->per_thread;
+    s->chunk_turns = B->chunk;
+    s->growth = B->growth;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_batch_track(trk_batch *B, int32_t n_turns) {
+    if (!B) return fail(TRK_EINVAL, "trk_batch_track: NULL batch");
+    if (n_turns < 0) return fail(TRK_EINVAL, "trk_batch_track: n_turns < 0");
+    const int nv = B->n_var;
+    const int tile = B->block * B->per_thread;
+    for (int v = 0; v < nv; ++v) {
+        trk_bunch *b = B->b[v];
+        if (b->turn + n_turns > 0x7fffffffll) return fail(TRK_EINVAL, "trk_batch_track: turn counter overflow");
+        if (!b->p0c_set) {
+            b->p0c = B->L[v]->p0c;
+            b->p0c_set = true;
+        }
+        b->moments_turns = 0;
+        b->block = B->block;
+        b->per_thread = B->per_thread;
+    }
+    if (n_turns == 0) return TRK_OK;
+    const std::vector<int> chunks = chunk_plan(n_turns, B->chunk, B->growth);
+    const int nc = (int)chunks.size();
+    int max_chunk = 0;
+    for (int c : chunks) max_chunk = c > max_chunk ? c : max_chunk;
+    // per-variant scratch and the (variant, tile) item table
+    std::vector<int2> items;
+    std::vector<CompactArgs> cargs(nv);
+    for (int v = 0; v < nv; ++v) {
+        trk_bunch *b = B->b[v];
+        const int nt = (int)((b->n + tile - 1) / tile);
+        if (B->moments) {
+            trk_status s = ensure_moments(b, n_turns, nt, max_chunk);
+            if (s != TRK_OK) return s;
+        }
+        for (int t = 0; t < nt; ++t) items.push_back(make_int2(v, t));
+        cargs[v] = compact_args(b, tile, nt);
+    }
+    const bool retile = B->n_items != (int)items.size() || !B->d_items;
+    if (retile) {
+        batch_free_graph(B);
+        cudaFree(B->d_items);
+        cudaFree(B->d_cargs);
+        B->d_items = nullptr;
+        B->d_cargs = nullptr;
+        if (dalloc(&B->d_items, items.size()) != cudaSuccess || dalloc(&B->d_cargs, nv) != cudaSuccess)
+            return fail(TRK_ENOMEM, "trk_batch_track: table allocation failed");
+        TRK_CUDA(cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        B->n_items = (int)items.size();
+    }
+    TRK_CUDA(cudaMemcpyAsync(B->d_cargs, cargs.data(), nv * sizeof(CompactArgs), cudaMemcpyHostToDevice, B->stream));
+    // per (variant, chunk) launch arguments, with the reference momentum and the
+    // absolute turn at the start of each chunk
+    const size_t na = (size_t)nv * nc;
+    if (na > B->args_cap) {
+        batch_free_graph(B);
+        cudaFree(B->d_args);
+        B->d_args = nullptr;
+        B->args_cap = 0;
+        if (dalloc(&B->d_args, na) != cudaSuccess) return fail(TRK_ENOMEM, "trk_batch_track: argument table allocation failed");
+        B->args_cap = na;
+    }
+    B->h_args.resize(na);
+    for (int v = 0; v < nv; ++v) {
+        trk_bunch *b = B->b[v];
+        const trk_lattice *L = B->L[v];
+        const int nt = cargs[v].n_tiles;
+        const int ne = L->view.n_elem;
+        int t0 = 0;
+        for (int c = 0; c < nc; ++c) {
+            TrackArgs a = base_args(b, L, nt);
+            a.e0 = 0;
+            a.e1 = ne;
+            a.n_turns = chunks[c];
+            a.turn_abs0 = (int32_t)(b->turn + t0);
+            a.local_turn0 = 0;
+            a.do_moments = L->moments;
+            a.p0c = b->p0c;
+            a.mom_out = b->moments ? b->moments + (size_t)t0 * kMomentsN : nullptr;
+            B->h_args[(size_t)v * nc + c] = a;
+            for (int t = 0; t < chunks[c]; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
+            t0 += chunks[c];
+        }
+    }
+    TRK_CUDA(cudaMemcpyAsync(B->d_args, B->h_args.data(), na * sizeof(TrackArgs), cudaMemcpyHostToDevice, B->stream));
+    // one CUDA graph holds every chunk of the call; it only reads the tables
+    // above, so it is captured once per (n_turns, schedule, tiling) and replayed
+    if (!B->exec || B->planned_turns != n_turns || B->chunks != chunks) {
+        batch_free_graph(B);
+        cudaGraph_t g = nullptr;
+        TRK_CUDA(cudaStreamBeginCapture(B->capture, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int c = 0; c < nc && e == cudaSuccess; ++c)
+            e = launch_batch_chunk(B->d_args, B->d_cargs, B->d_items, B->n_items, nv, nc, c, B->block,
+                                   B->per_thread, tile, chunks[c], B->moments, B->capture);
+        cudaError_t e2 = cudaStreamEndCapture(B->capture, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(TRK_ECUDA, std::string("trk_batch_track: graph capture failed: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&B->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            B->exec = nullptr;
+            return fail(TRK_ECUDA, std::string("trk_batch_track: graph instantiation failed: ") + cudaGetErrorString(e));
+        }
+        B->planned_turns = n_turns;
+        B->chunks = chunks;
+    }
+    TRK_CUDA(cudaGraphLaunch(B->exec, B->stream));
+    for (int v = 0; v < nv; ++v) {
+        trk_bunch *b = B->b[v];
+        b->turn += n_turns;
+        b->moments_turns = B->moments ? n_turns : 0;
+        b->track_launches += nc;
+        b->launches += (int64_t)nc * (B->moments ? 6 : 5);
+    }
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_track_batch(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                                      int32_t n_turns, const trk_schedule *sched) {
+    trk_batch *B = nullptr;
+    trk_status s = trk_batch_create(bunches, lats, n_var, &B);
+    if (s != TRK_OK) return s;
+    if (sched) s = trk_batch_set_schedule(B, sched);
+    if (s == TRK_OK) s = trk_batch_track(B, n_turns);
+    trk_batch_destroy(B);
+    return s;
+}
+
+
+// ----------------------------------------------------- dynamic aperture ----
+
+extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
+                                      const double *d_x0, const double *d_y0, int32_t n_turns,
+                                      const trk_schedule *sched, int32_t *d_survival, void *stream) {
+    if (n_var < 1 || !lats || !offsets) return fail(TRK_EINVAL, "trk_da_survival: need n_var >= 1, lattices, offsets");
+    if (n_turns < 1) return fail(TRK_EINVAL, "trk_da_survival: n_turns must be >= 1");
+    if (offsets[0] != 0) return fail(TRK_EINVAL, "trk_da_survival: offsets[0] must be 0");
+    for (int v = 0; v < n_var; ++v)
+        if (offsets[v + 1] < offsets[v] || offsets[v + 1] - offsets[v] > 0x7fffffffll)
+            return fail(TRK_EINVAL, "trk_da_survival: offsets must be non-decreasing, < 2^31 points per variant");
+    const int64_t total = offsets[n_var];
+    if (total == 0) return TRK_OK;
+    if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival: NULL point or output array");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *coords = nullptr;
+    int32_t *ids = nullptr;
+    if (dalloc(&coords, 6 * (size_t)total) != cudaSuccess || dalloc(&ids, total) != cudaSuccess) {
+        cudaFree(coords);
+        return fail(TRK_ENOMEM, "trk_da_survival: particle allocation failed");
+    }
+    std::vector<trk_bunch *> bunches;
+    std::vector<const trk_lattice *> L;
+    trk_batch *B = nullptr;
+    trk_status st = TRK_OK;
+    cudaError_t e = launch_da_init(coords, total, ids, d_x0, d_y0, total, s);
+    if (e != cudaSuccess) st = fail(TRK_ECUDA, std::string("trk_da_survival: ") + cudaGetErrorString(e));
+    for (int v = 0; v < n_var && st == TRK_OK; ++v) {
+        const int64_t n = offsets[v + 1] - offsets[v];
+        if (n == 0) continue;
+        trk_bunch *b = nullptr;
+        st = trk_bunch_wrap(coords + offsets[v], total, ids + offsets[v], n, stream, &b);
+        if (st == TRK_OK) {
+            bunches.push_back(b);
+            L.push_back(lats[v]);
+        }
+    }
+    if (st == TRK_OK && !bunches.empty()) st = trk_batch_create(bunches.data(), L.data(), (int32_t)bunches.size(), &B);
+    if (st == TRK_OK && B) {
+        trk_schedule def = {128, 2, 1, 2};  // short chunks first: most lost particles leave early
+        st = trk_batch_set_schedule(B, sched ? sched : &def);
+    }
+    if (st == TRK_OK && B) st = trk_batch_track(B, n_turns);
+    for (size_t k = 0; k < bunches.size() && st == TRK_OK; ++k) {
+        trk_bunch *b = bunches[k];
+        e = launch_da_survival(b->ids, b->lt, b->n, n_turns, d_survival, s);
+        if (e != cudaSuccess) st = fail(TRK_ECUDA, std::string("trk_da_survival: ") + cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(s);
+    if (B) trk_batch_destroy(B);
+    for (trk_bunch *b : bunches) trk_bunch_free(b);
+    cudaFree(coords);
+    cudaFree(ids);
+    return st;
 }
 
 extern "C" trk_status trk_bunch_enable_timing(trk_bunch *b, int32_t on) {

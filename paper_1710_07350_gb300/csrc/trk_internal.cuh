@@ -84,16 +84,34 @@ struct TrackArgs {
     int32_t *tile_alive;    // alive count per tile at the end (may be null)
     const double *wake_V;   // voltages of the kicking wake
     int32_t wake_nbins;
+    int32_t tile;           // particles per tile (block * per_thread)
+    double *mom_out;        // finalised moments of this launch's first turn (batched path)
+};
+
+// Arguments of the loss compaction of one bunch.
+struct CompactArgs {
+    double *coords;
+    int64_t pitch;
+    int32_t *ids, *lt, *le;
+    double *cb;
+    int32_t *ib, *ltb, *leb;
+    const int32_t *tile_alive;
+    int64_t *tile_off;
+    BunchState *st;
+    int32_t tile;
+    int32_t n_tiles;
 };
 
 // Launchers (trk_track.cu / trk_wake.cu); all asynchronous on `s`.
 cudaError_t launch_track(const TrackArgs &a, int block, int per_thread, int n_tiles, cudaStream_t s);
 cudaError_t launch_moments_finalize(const double *partials, int n_tiles, int n_turns, const BunchState *st,
                                     int tile, double *out, cudaStream_t s);
-cudaError_t launch_compact(double *coords, int64_t pitch, int32_t *ids, int32_t *lt, int32_t *le,
-                           double *coords_b, int32_t *ids_b, int32_t *lt_b, int32_t *le_b,
-                           const int32_t *tile_alive, int64_t *tile_off, int n_tiles, int tile,
-                           BunchState *st, cudaStream_t s);
+cudaError_t launch_compact(const CompactArgs &c, int n_tiles, cudaStream_t s);
+// One chunk of a batched call: fused tracking of every (variant, tile) item,
+// moment finalisation and compaction of every variant.
+cudaError_t launch_batch_chunk(const TrackArgs *args, const CompactArgs *cargs, const int2 *items, int n_items,
+                               int n_var, int n_chunks, int chunk, int block, int per_thread, int tile,
+                               int max_turns, bool moments, cudaStream_t s);
 cudaError_t launch_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n, cudaStream_t s);
 cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, int nbins, cudaStream_t s);
 cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
@@ -102,6 +120,12 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
                              double w0, double sc, uint32_t *hist, double *wfun, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
                              cudaStream_t s);
+
+// Dynamic-aperture helpers (trk_da.cu).
+cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0, int64_t n,
+                           cudaStream_t s);
+cudaError_t launch_da_survival(const int32_t *ids, const int32_t *lt, int64_t n, int32_t n_turns, int32_t *survival,
+                               cudaStream_t s);
 
 // Records the calling thread's error text (returned by trk_last_error) and
 // passes the status through.

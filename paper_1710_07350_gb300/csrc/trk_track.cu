@@ -51,12 +51,6 @@ __device__ __noinline__ double rsqrt_exact(double s) { return rsqrt(s); }
 
 __device__ __noinline__ double edrift_exact_g(double v) { return v / (sqrt(1.0 + v) + 1.0); }
 
-__device__ __noinline__ double2 drift_exact(double px, double py, double d, double h, double l) {
-    const double Pm = 1.0 + d;
-    const double t = h * rsqrt(fma(-px, px, fma(-py, py, Pm * Pm)));
-    return make_double2(t, fma(t, Pm, l - h));
-}
-
 __device__ __noinline__ bool ellipse_exact(double x, double y, double a, double b) {
     const double u = __ddiv_rn(x, a), v = __ddiv_rn(y, b);
     return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
@@ -131,67 +125,145 @@ __device__ __forceinline__ void v_edrift(Tile<P> &q, double L) {
 }
 
 // ------------------------------------------------ kick-drift multipole ----
-// Exact-Hamiltonian drift in canonical momenta: pz = P sqrt(1 - u),
-// u = (px^2 + py^2)/P^2, so h/pz = (h/P)(1 + g) and h (P/pz - 1) = h g with
-// g = (1 - u)^(-1/2) - 1 = u/2 + 3u^2/8 + 5u^3/16 + ... (exact form for u >= 2^-14).
+// Inside a kick-drift element the momenta are carried scaled by the particle's
+// total momentum, qx = px/(1+delta) (delta is constant through the element).
+// Exact-Hamiltonian drift: pz/(1+delta) = sqrt(1 - u), u = qx^2 + qy^2, so
+//   x += h qx (1 + g),  y += h qy (1 + g),  l += h g,
+//   g = (1 - u)^(-1/2) - 1 = u/2 + 3u^2/8 + 5u^3/16 + ...  (u < 2^-14; the
+// first dropped term is then below 4e-18), or rsqrt(1 - u) - 1 otherwise.
+__device__ __noinline__ double drift_g_exact(double u) { return rsqrt(1.0 - u) - 1.0; }
+
 template <int P>
-__device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (&l)[P], const double (&px)[P],
-                                        const double (&py)[P], const double (&d)[P], const double (&iP2)[P],
-                                        const double (&hiP)[P], double h) {
-    double t[P], ln[P];
+__device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (&l)[P], const double (&qx)[P],
+                                        const double (&qy)[P], double h) {
+    double g[P];
     bool need = false;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
-        const double u2 = u * u;
-        const double g = fma(u2, fma(u, 0.3125, 0.375), 0.5 * u);
-        t[p] = fma(hiP[p], g, hiP[p]);
-        ln[p] = fma(h, g, l[p]);
+        const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
+        g[p] = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
         need |= !series_ok(u);
     }
     if (need) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
-            if (!series_ok(u)) {
-                const double2 r = drift_exact(px[p], py[p], d[p], h, l[p]);
-                t[p] = r.x;
-                ln[p] = r.y;
-            }
+            const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
+            if (!series_ok(u)) g[p] = drift_g_exact(u);
         }
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        x[p] = fma(t[p], px[p], x[p]);
-        y[p] = fma(t[p], py[p], y[p]);
-        l[p] = ln[p];
+        const double t = fma(h, g[p], h);
+        x[p] = fma(t, qx[p], x[p]);
+        y[p] = fma(t, qy[p], y[p]);
+        l[p] = fma(h, g[p], l[p]);
     }
 }
 
-template <int P>
-__device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&px)[P], double (&py)[P],
-                                       uint32_t fl, const double *kp) {
-    const double a = __ldg(kp), hb = __ldg(kp + 2), b = __ldg(kp + 4);
-    if (fl & 1u) {
+// Kicks on the scaled momenta: quadrupole qx -= (K1 h/(1+delta)) x, qy += ...;
+// sextupole qx -= (K2 h/(2(1+delta)))(x^2 - y^2), qy += (K2 h/(1+delta)) x y.
+template <int P, uint32_t FL>
+__device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&qx)[P], double (&qy)[P],
+                                       const double (&a)[P], const double (&hb)[P], const double (&b)[P]) {
+    if (FL & 1u) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            px[p] = fma(-a, x[p], px[p]);
-            py[p] = fma(a, y[p], py[p]);
+            qx[p] = fma(-a[p], x[p], qx[p]);
+            qy[p] = fma(a[p], y[p], qy[p]);
         }
     }
-    if (fl & 2u) {
+    if (FL & 2u) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const double t = (x[p] - y[p]) * (x[p] + y[p]);
-            px[p] = fma(-hb, t, px[p]);
-            py[p] = fma(b, x[p] * y[p], py[p]);
+            qx[p] = fma(-hb[p], t, qx[p]);
+            qy[p] = fma(b[p], x[p] * y[p], qy[p]);
         }
     }
 }
 
 // n steps of the 4th-order Yoshida scheme D K D K D K D with adjacent drifts of
-// consecutive steps merged; slopes converted to canonical momenta at entry and
-// back at exit.
+// consecutive steps merged; slopes converted to scaled canonical momenta at
+// entry, qx = x' (1 + x'^2 + y'^2)^(-1/2), and back at exit, x' = qx (1 + g).
+// FL: bit 0 quadrupole kick, bit 1 sextupole kick (one instantiation each, so
+// that only the strengths in use occupy registers).
+template <int P, uint32_t FL>
+__device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P], const DevElem *__restrict__ E) {
+    const int n = __ldg(&E->n);
+    constexpr uint32_t fl = FL;
+    const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
+    double qx[P], qy[P], a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
+    if (fl & 1u) {
+        const double A1 = __ldg(&E->p[3]), A0 = __ldg(&E->p[4]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            a1[p] = A1 * iP[p];
+            a0[p] = A0 * iP[p];
+        }
+    }
+    if (fl & 2u) {
+        const double H1 = __ldg(&E->p[5]), H0 = __ldg(&E->p[6]), B1 = __ldg(&E->p[7]), B0 = __ldg(&E->p[8]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            hb1[p] = H1 * iP[p];
+            hb0[p] = H0 * iP[p];
+            b1[p] = B1 * iP[p];
+            b0[p] = B0 * iP[p];
+        }
+    }
+    bool need = false;
+    // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+        const double c = fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0);
+        qx[p] = c * q.xp[p];
+        qy[p] = c * q.yp[p];
+        need |= !series_ok(v);
+    }
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+            if (!series_ok(v)) {
+                const double c = rsqrt_exact(1.0 + v);
+                qx[p] = c * q.xp[p];
+                qy[p] = c * q.yp[p];
+            }
+        }
+    }
+    v_drift<P>(q.x, q.y, q.l, qx, qy, d1);
+    for (int s = 0; s < n; ++s) {
+        v_kick<P, FL>(q.x, q.y, qx, qy, a1, hb1, b1);
+        v_drift<P>(q.x, q.y, q.l, qx, qy, d2);
+        v_kick<P, FL>(q.x, q.y, qx, qy, a0, hb0, b0);
+        v_drift<P>(q.x, q.y, q.l, qx, qy, d2);
+        v_kick<P, FL>(q.x, q.y, qx, qy, a1, hb1, b1);
+        v_drift<P>(q.x, q.y, q.l, qx, qy, s + 1 < n ? dm : d1);
+    }
+    // x' = px/pz = qx (1 - u)^(-1/2) = qx (1 + g)
+    double g[P];
+    need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
+        g[p] = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
+        need |= !series_ok(u);
+    }
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
+            if (!series_ok(u)) g[p] = drift_g_exact(u);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        q.xp[p] = fma(qx[p], g[p], qx[p]);
+        q.yp[p] = fma(qy[p], g[p], qy[p]);
+    }
+}
+
 template <int P>
 __device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &dirty,
                                              const DevElem *__restrict__ E) {
@@ -200,69 +272,11 @@ __device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &
         for (int p = 0; p < P; ++p) iP[p] = 1.0 / (1.0 + q.d[p]);
         dirty = false;
     }
-    const int n = __ldg(&E->n);
-    const uint32_t fl = __ldg(&E->flags);
-    const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
-    const double *k1p = &E->p[3], *k0p = &E->p[4];  // a, hb, b at stride 2
-    double px[P], py[P], iP2[P], h1[P], h2[P], hm[P];
-    bool need = false;
-    // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        iP2[p] = iP[p] * iP[p];
-        h1[p] = d1 * iP[p];
-        h2[p] = d2 * iP[p];
-        hm[p] = dm * iP[p];
-        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
-        const double c = fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0);
-        const double pc = (1.0 + q.d[p]) * c;
-        px[p] = pc * q.xp[p];
-        py[p] = pc * q.yp[p];
-        need |= !series_ok(v);
-    }
-    if (need) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
-            if (!series_ok(v)) {
-                const double pc = (1.0 + q.d[p]) * rsqrt_exact(1.0 + v);
-                px[p] = pc * q.xp[p];
-                py[p] = pc * q.yp[p];
-            }
-        }
-    }
-    v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h1, d1);
-    for (int s = 0; s < n; ++s) {
-        v_kick<P>(q.x, q.y, px, py, fl, k1p);
-        v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h2, d2);
-        v_kick<P>(q.x, q.y, px, py, fl, k0p);
-        v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h2, d2);
-        v_kick<P>(q.x, q.y, px, py, fl, k1p);
-        if (s + 1 < n)
-            v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, hm, dm);
-        else
-            v_drift<P>(q.x, q.y, q.l, px, py, q.d, iP2, h1, d1);
-    }
-    need = false;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
-        const double ipz = fma(iP[p], u * fma(u, fma(u, 0.3125, 0.375), 0.5), iP[p]);
-        need |= !series_ok(u);
-        q.xp[p] = px[p] * ipz;
-        q.yp[p] = py[p] * ipz;
-    }
-    if (need) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const double u = fma(px[p], px[p], py[p] * py[p]) * iP2[p];
-            if (!series_ok(u)) {
-                const double Pm = 1.0 + q.d[p];
-                const double ipz = rsqrt_exact(fma(-px[p], px[p], fma(-py[p], py[p], Pm * Pm)));
-                q.xp[p] = px[p] * ipz;
-                q.yp[p] = py[p] * ipz;
-            }
-        }
+    switch (__ldg(&E->flags) & 3u) {
+    case 1u: v_kick_drift_t<P, 1u>(q, iP, E); break;
+    case 2u: v_kick_drift_t<P, 2u>(q, iP, E); break;
+    case 3u: v_kick_drift_t<P, 3u>(q, iP, E); break;
+    default: v_kick_drift_t<P, 0u>(q, iP, E); break;
     }
 }
 
@@ -459,17 +473,24 @@ __device__ __forceinline__ void apply_aperture(const TrackArgs &a, const Lattice
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_track(TrackArgs a) {
-    __shared__ double sh[(kMaxBlock / 32) * kMomentsN];
-    __shared__ double tot[kMomentsN];
-    __shared__ double K[6];
-    __shared__ unsigned long long mm[2];
-    __shared__ int cnt;
+struct TrackShared {
+    double sh[(kMaxBlock / 32) * kMomentsN];
+    double tot[kMomentsN];
+    double K[6];
+    unsigned long long mm[2];
+    int cnt;
+};
 
+// One tile of one bunch: load, track a.n_turns turns through [a.e0, a.e1),
+// per-turn moment partials, optional l window, store, alive count.
+template <int P>
+__device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, TrackShared &S) {
+    double *sh = S.sh, *tot = S.tot, *K = S.K;
+    unsigned long long *mm = S.mm;
+    int &cnt = S.cnt;
     const int64_t n_alive = a.st->n_alive;
     const int T = blockDim.x * P;
-    const int64_t base = (int64_t)blockIdx.x * T;
+    const int64_t base = (int64_t)tile * T;
     if (base >= n_alive) return;  // whole block beyond the alive range
 
     Tile<P> q;
@@ -536,7 +557,7 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
         }
         if (a.do_moments)
             tile_moments<P>(q, alive, sh, tot, K,
-                            a.partials + ((size_t)(a.local_turn0 + t) * a.n_tiles + blockIdx.x) * kMomentsN);
+                            a.partials + ((size_t)(a.local_turn0 + t) * a.n_tiles + tile) * kMomentsN);
     }
 
     if (a.minmax_slot >= 0) {
@@ -585,8 +606,24 @@ __global__ void __launch_bounds__(256) k_track(TrackArgs a) {
         __syncthreads();
         if ((threadIdx.x & 31) == 0) atomicAdd(&cnt, na);
         __syncthreads();
-        if (threadIdx.x == 0) a.tile_alive[blockIdx.x] = cnt;
+        if (threadIdx.x == 0) a.tile_alive[tile] = cnt;
     }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_track(TrackArgs a) {
+    __shared__ TrackShared S;
+    track_tile<P>(a, blockIdx.x, S);
+}
+
+// Batched form: block b tracks tile items[b].y of variant items[b].x with the
+// arguments args[variant * n_chunks + chunk].
+template <int P>
+__global__ void __launch_bounds__(256) k_track_batch(const TrackArgs *__restrict__ args,
+                                                      const int2 *__restrict__ items, int n_chunks, int chunk) {
+    __shared__ TrackShared S;
+    const int2 it = items[blockIdx.x];
+    track_tile<P>(args[(size_t)it.x * n_chunks + chunk], it.y, S);
 }
 
 // ---------------------------------------------------- moments finalise ----
@@ -619,11 +656,8 @@ __device__ __forceinline__ void acc_merge(Acc &a, const Acc &b) {
 
 constexpr int kFinThreads = 128;
 
-__global__ void __launch_bounds__(kFinThreads) k_moments_finalize(const double *__restrict__ partials, int n_tiles,
-                                                                   const BunchState *st, int tile,
-                                                                   double *__restrict__ out) {
-    __shared__ Acc sh[kFinThreads];
-    const int t = blockIdx.x;
+__device__ __forceinline__ void finalize_turn(const double *__restrict__ partials, int n_tiles, const BunchState *st,
+                                              int tile, double *__restrict__ out, int t, Acc *sh) {
     const int64_t n_alive = st->n_alive;
     const int n_act = (int)((n_alive + tile - 1) / tile);
     Acc a;
@@ -662,20 +696,33 @@ __global__ void __launch_bounds__(kFinThreads) k_moments_finalize(const double *
     }
 }
 
+__global__ void __launch_bounds__(kFinThreads) k_moments_finalize(const double *__restrict__ partials, int n_tiles,
+                                                                   const BunchState *st, int tile,
+                                                                   double *__restrict__ out) {
+    __shared__ Acc sh[kFinThreads];
+    finalize_turn(partials, n_tiles, st, tile, out, blockIdx.x, sh);
+}
+
+// Batched: block (t, v) finalises turn t of variant v's chunk.
+__global__ void __launch_bounds__(kFinThreads) k_moments_finalize_batch(const TrackArgs *__restrict__ args,
+                                                                         int n_chunks, int chunk) {
+    __shared__ Acc sh[kFinThreads];
+    const TrackArgs &a = args[(size_t)blockIdx.y * n_chunks + chunk];
+    if (!a.do_moments || (int)blockIdx.x >= a.n_turns) return;
+    finalize_turn(a.partials, a.n_tiles, a.st, a.tile, a.mom_out, blockIdx.x, sh);
+}
+
 // ------------------------------------------------------------ compaction ----
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ tile_alive,
-                                                              int64_t *__restrict__ tile_off, int tile,
-                                                              BunchState *st) {
-    __shared__ int64_t wsum[kScanThreads / 32];
+__device__ __forceinline__ void scan_tiles(const int32_t *__restrict__ tile_alive, int64_t *__restrict__ tile_off,
+                                           int tile, BunchState *st, int64_t *wsum) {
     const int64_t n_alive = st->n_alive;
     const int n_act = (int)((n_alive + tile - 1) / tile);
     const int per = (n_act + kScanThreads - 1) / kScanThreads;
     const int b = threadIdx.x * per, e = min(b + per, n_act);
     int64_t s = 0;
     for (int j = b; j < e; ++j) s += tile_alive[j];
-    // block exclusive scan of s
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t inc = s;
 #pragma unroll
@@ -703,21 +750,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__re
     if (threadIdx.x == kScanThreads - 1) st->n_alive_next = off;
 }
 
-// Stable partition of each tile into the compaction buffers: alive particles to
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t *__restrict__ tile_alive,
+                                                              int64_t *__restrict__ tile_off, int tile,
+                                                              BunchState *st) {
+    __shared__ int64_t wsum[kScanThreads / 32];
+    scan_tiles(tile_alive, tile_off, tile, st, wsum);
+}
+
+// Stable partition of one tile into the compaction buffers: alive particles to
 // [tile_off, ...), lost ones after all survivors, in slot order.
-__global__ void k_scatter(const double *__restrict__ coords, int64_t pitch, const int32_t *__restrict__ ids,
-                          const int32_t *__restrict__ lt, const int32_t *__restrict__ le, double *__restrict__ cb,
-                          int32_t *__restrict__ ib, int32_t *__restrict__ ltb, int32_t *__restrict__ leb,
-                          const int64_t *__restrict__ tile_off, const BunchState *st) {
-    __shared__ int wcnt[32];
+__device__ __forceinline__ void scatter_tile(const CompactArgs &c, int tile, int *wcnt) {
+    const BunchState *st = c.st;
     const int64_t n_alive = st->n_alive, n_next = st->n_alive_next;
     if (n_next == n_alive) return;  // nothing lost in this chunk
     const int T = blockDim.x;
-    const int64_t base = (int64_t)blockIdx.x * T;
+    const int64_t base = (int64_t)tile * T;
     if (base >= n_alive) return;
     const int64_t i = base + threadIdx.x;
     const bool valid = i < n_alive;
-    const bool al = valid && lt[i] < 0;
+    const bool al = valid && c.lt[i] < 0;
     const unsigned bal = __ballot_sync(0xffffffffu, al);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) wcnt[w] = __popc(bal);
@@ -726,33 +777,69 @@ __global__ void k_scatter(const double *__restrict__ coords, int64_t pitch, cons
     for (int j = 0; j < w; ++j) before += wcnt[j];
     const int rank = before + __popc(bal & ((1u << lane) - 1u));
     if (!valid) return;
-    const int64_t toff = tile_off[blockIdx.x];
-    int64_t dst;
-    if (al)
-        dst = toff + rank;
-    else
-        dst = n_next + (base - toff) + (threadIdx.x - rank);
+    const int64_t toff = c.tile_off[tile];
+    const int64_t dst = al ? toff + rank : n_next + (base - toff) + (threadIdx.x - rank);
+    const int64_t pitch = c.pitch;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) cb[c * pitch + dst] = coords[c * pitch + i];
-    ib[dst] = ids[i];
-    ltb[dst] = lt[i];
-    leb[dst] = le[i];
+    for (int k = 0; k < 6; ++k) c.cb[k * pitch + dst] = c.coords[k * pitch + i];
+    c.ib[dst] = c.ids[i];
+    c.ltb[dst] = c.lt[i];
+    c.leb[dst] = c.le[i];
 }
 
-__global__ void k_copyback(double *__restrict__ coords, int64_t pitch, int32_t *__restrict__ ids,
-                           int32_t *__restrict__ lt, int32_t *__restrict__ le, const double *__restrict__ cb,
-                           const int32_t *__restrict__ ib, const int32_t *__restrict__ ltb,
-                           const int32_t *__restrict__ leb, const BunchState *st) {
+__global__ void k_scatter(CompactArgs c) {
+    __shared__ int wcnt[32];
+    scatter_tile(c, blockIdx.x, wcnt);
+}
+
+__global__ void k_copyback(CompactArgs c) {
+    const BunchState *st = c.st;
     const int64_t n_alive = st->n_alive;
     if (st->n_alive_next == n_alive) return;
+    const int64_t pitch = c.pitch;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_alive;
          i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) coords[c * pitch + i] = cb[c * pitch + i];
-        ids[i] = ib[i];
-        lt[i] = ltb[i];
-        le[i] = leb[i];
+        for (int k = 0; k < 6; ++k) c.coords[k * pitch + i] = c.cb[k * pitch + i];
+        c.ids[i] = c.ib[i];
+        c.lt[i] = c.ltb[i];
+        c.le[i] = c.leb[i];
     }
+}
+
+// Batched compaction: one scan block per variant; scatter and copy-back per
+// (variant, tile) item; one commit thread per variant.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles_batch(const CompactArgs *__restrict__ cs) {
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const CompactArgs &c = cs[blockIdx.x];
+    scan_tiles(c.tile_alive, c.tile_off, c.tile, c.st, wsum);
+}
+
+__global__ void k_scatter_batch(const CompactArgs *__restrict__ cs, const int2 *__restrict__ items) {
+    __shared__ int wcnt[32];
+    const int2 it = items[blockIdx.x];
+    scatter_tile(cs[it.x], it.y, wcnt);
+}
+
+__global__ void k_copyback_batch(const CompactArgs *__restrict__ cs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const CompactArgs &c = cs[it.x];
+    const BunchState *st = c.st;
+    const int64_t n_alive = st->n_alive;
+    if (st->n_alive_next == n_alive) return;
+    const int64_t i = (int64_t)it.y * blockDim.x + threadIdx.x;
+    if (i >= n_alive) return;
+    const int64_t pitch = c.pitch;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.coords[k * pitch + i] = c.cb[k * pitch + i];
+    c.ids[i] = c.ib[i];
+    c.lt[i] = c.ltb[i];
+    c.le[i] = c.leb[i];
+}
+
+__global__ void k_commit_batch(const CompactArgs *__restrict__ cs, int n_var) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n_var) cs[v].st->n_alive = cs[v].st->n_alive_next;
 }
 
 __global__ void k_commit(BunchState *st) { st->n_alive = st->n_alive_next; }
@@ -793,16 +880,37 @@ cudaError_t launch_moments_finalize(const double *partials, int n_tiles, int n_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(double *coords, int64_t pitch, int32_t *ids, int32_t *lt, int32_t *le, double *coords_b,
-                           int32_t *ids_b, int32_t *lt_b, int32_t *le_b, const int32_t *tile_alive,
-                           int64_t *tile_off, int n_tiles, int tile, BunchState *st, cudaStream_t s) {
-    k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_alive, tile_off, tile, st);
-    k_scatter<<<n_tiles, tile, 0, s>>>(coords, pitch, ids, lt, le, coords_b, ids_b, lt_b, le_b, tile_off, st);
-    const int64_t n = (int64_t)n_tiles * tile;
+cudaError_t launch_compact(const CompactArgs &c, int n_tiles, cudaStream_t s) {
+    k_scan_tiles<<<1, kScanThreads, 0, s>>>(c.tile_alive, c.tile_off, c.tile, c.st);
+    k_scatter<<<n_tiles, c.tile, 0, s>>>(c);
+    const int64_t n = (int64_t)n_tiles * c.tile;
     int grid = (int)((n + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    k_copyback<<<grid, 256, 0, s>>>(coords, pitch, ids, lt, le, coords_b, ids_b, lt_b, le_b, st);
-    k_commit<<<1, 1, 0, s>>>(st);
+    if (grid < 1) grid = 1;
+    k_copyback<<<grid, 256, 0, s>>>(c);
+    k_commit<<<1, 1, 0, s>>>(c.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_chunk(const TrackArgs *args, const CompactArgs *cargs, const int2 *items, int n_items,
+                               int n_var, int n_chunks, int chunk, int block, int per_thread, int tile,
+                               int max_turns, bool moments, cudaStream_t s) {
+    if (n_items > 0) {
+        if (per_thread == 4)
+            k_track_batch<4><<<n_items, block, 0, s>>>(args, items, n_chunks, chunk);
+        else if (per_thread == 2)
+            k_track_batch<2><<<n_items, block, 0, s>>>(args, items, n_chunks, chunk);
+        else
+            k_track_batch<1><<<n_items, block, 0, s>>>(args, items, n_chunks, chunk);
+    }
+    if (moments && max_turns > 0)
+        k_moments_finalize_batch<<<dim3(max_turns, n_var), kFinThreads, 0, s>>>(args, n_chunks, chunk);
+    k_scan_tiles_batch<<<n_var, kScanThreads, 0, s>>>(cargs);
+    if (n_items > 0) {
+        k_scatter_batch<<<n_items, tile, 0, s>>>(cargs, items);
+        k_copyback_batch<<<n_items, tile, 0, s>>>(cargs, items);
+    }
+    k_commit_batch<<<(n_var + 127) / 128, 128, 0, s>>>(cargs, n_var);
     return cudaGetLastError();
 }
 

@@ -45,8 +45,20 @@ class trk_stats(ctypes.Structure):
     _fields_ = [("track_kernel_ms", c_double), ("track_launches", c_int64), ("launches", c_int64)]
 
 
+class trk_triage_opts(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("half_width", c_double), ("n_turns", c_int32),
+                ("coarse_stride", c_int32), ("band_radius", c_int32), ("use_mlp", c_int32),
+                ("epochs", c_int32), ("batch", c_int32), ("lr", ctypes.c_float), ("pad", c_int32)]
+
+
+class trk_triage_stats(ctypes.Structure):
+    _fields_ = [("n_cells", c_int64), ("n_coarse", c_int64), ("n_band", c_int64), ("n_audit", c_int64),
+                ("n_tracked", c_int64), ("n_audit_wrong", c_int64), ("ms_coarse", c_double),
+                ("ms_train", c_double), ("ms_infer", c_double), ("ms_band", c_double), ("ms_retrack", c_double)]
+
+
 class trk_schedule(ctypes.Structure):
-    _fields_ = [("block", c_int32), ("per_thread", c_int32), ("chunk_turns", c_int32), ("pad", c_int32)]
+    _fields_ = [("block", c_int32), ("per_thread", c_int32), ("chunk_turns", c_int32), ("growth", c_int32)]
 
 
 _lib = None
@@ -77,6 +89,21 @@ def lib():
             "trk_n_alive": [P, P],
             "trk_wake": [P, c_int32, c_double, c_double, c_double, c_double, P, P],
             "trk_bunch_enable_timing": [P, c_int32],
+            "trk_batch_create": [P, P, c_int32, P],
+            "trk_batch_set_schedule": [P, P],
+            "trk_batch_get_schedule": [P, P],
+            "trk_batch_track": [P, c_int32],
+            "trk_batch_destroy": [P],
+            "trk_track_batch": [P, P, c_int32, c_int32, P],
+            "trk_da_survival": [P, c_int32, P, P, P, c_int32, P, P, P],
+            "trk_mlp_create": [P, P, P],
+            "trk_mlp_destroy": [P],
+            "trk_mlp_forward": [P, P, c_int64, P, P],
+            "trk_mlp_grad": [P, P, P, c_int32, P, P],
+            "trk_mlp_adam": [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
+            "trk_mlp_train": [P, P, P, c_int64, c_int32, c_int32, P, ctypes.c_float, P, P],
+            "trk_mlp_get": [P, P, P, P, P],
+            "trk_da_triage": [P, c_int32, P, P, P, P, P, P, P, P, P],
             "trk_bunch_stats": [P, P, c_int32],
             "trk_wake_static": [P, c_int64, c_int64, c_int32, c_double, c_double, c_double, c_double, P, P, P],
         }
@@ -253,6 +280,177 @@ def trk_lost(b):
 
 def trk_wake(b, nbins, w0, sc, charge, p0c, hist=None, volt=None):
     _check(lib().trk_wake(b.handle, nbins, w0, sc, charge, p0c, _dptr(hist), _dptr(volt)))
+
+
+class Batch:
+    """Owns a trk_batch handle; keeps the bunches and lattices alive."""
+
+    def __init__(self, handle, bunches, lattices):
+        self.handle = handle
+        self.bunches = list(bunches)
+        self.lattices = list(lattices)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.trk_batch_destroy(self.handle)
+            self.handle = None
+
+
+def _handles(objs):
+    arr = (c_void_p * len(objs))()
+    for i, o in enumerate(objs):
+        arr[i] = o.handle
+    return arr
+
+
+def trk_batch_create(bunches, lattices):
+    if len(bunches) != len(lattices):
+        raise ValueError("one lattice per bunch")
+    h = c_void_p()
+    _check(lib().trk_batch_create(_handles(bunches), _handles(lattices), len(bunches), ctypes.byref(h)))
+    return Batch(h, bunches, lattices)
+
+
+def trk_batch_set_schedule(B, block=0, per_thread=0, chunk_turns=0, growth=0):
+    s = trk_schedule(block, per_thread, chunk_turns, growth)
+    _check(lib().trk_batch_set_schedule(B.handle, ctypes.byref(s)))
+
+
+def trk_batch_get_schedule(B):
+    s = trk_schedule()
+    _check(lib().trk_batch_get_schedule(B.handle, ctypes.byref(s)))
+    return {"block": s.block, "per_thread": s.per_thread, "chunk_turns": s.chunk_turns, "growth": s.growth}
+
+
+def trk_batch_track(B, n_turns):
+    _check(lib().trk_batch_track(B.handle, n_turns))
+
+
+def trk_track_batch(bunches, lattices, n_turns, schedule=None):
+    s = None
+    if schedule is not None:
+        s = ctypes.byref(trk_schedule(schedule.get("block", 0), schedule.get("per_thread", 0),
+                                      schedule.get("chunk_turns", 0), schedule.get("growth", 0)))
+    _check(lib().trk_track_batch(_handles(bunches), _handles(lattices), len(bunches), n_turns, s))
+
+
+def trk_da_survival(lattices, x0, y0, offsets, n_turns, schedule=None, stream=None):
+    """x0, y0: float64 CUDA tensors of all points; offsets: n_var + 1 host ints.
+    Returns an int32 CUDA tensor of survival turns (1-based loss turn, or
+    n_turns + 1)."""
+    import torch
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    surv = torch.empty(int(offs[-1]), dtype=torch.int32, device=x0.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(x0.device)
+    s = None
+    if schedule is not None:
+        s = ctypes.byref(trk_schedule(schedule.get("block", 0), schedule.get("per_thread", 0),
+                                      schedule.get("chunk_turns", 0), schedule.get("growth", 0)))
+    _check(lib().trk_da_survival(_handles(lattices), len(lattices), offs.ctypes.data_as(c_void_p), _dptr(x0),
+                                 _dptr(y0), n_turns, s, _dptr(surv), c_void_p(stream.cuda_stream)))
+    return surv
+
+
+MLP_SHAPES = [(256, 8), (256, 256), (256, 256), (256, 256), (1, 256)]
+
+
+class MLP:
+    """Owns a trk_mlp handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.trk_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def _fptrs(arrays):
+    arr = (c_void_p * len(arrays))()
+    for i, a in enumerate(arrays):
+        arr[i] = None if a is None else a.ctypes.data
+    return arr
+
+
+def trk_mlp_create(params):
+    """params: [(W (out, in), b (out,))] x 5 host arrays (converted to FP32)."""
+    Ws = [np.ascontiguousarray(W, dtype=np.float32) for W, _ in params]
+    bs = [np.ascontiguousarray(b, dtype=np.float32) for _, b in params]
+    for (o, i), W, b in zip(MLP_SHAPES, Ws, bs):
+        if W.shape != (o, i) or b.shape != (o,):
+            raise ValueError("MLP parameter shapes must be %s" % MLP_SHAPES)
+    h = c_void_p()
+    _check(lib().trk_mlp_create(_fptrs(Ws), _fptrs(bs), ctypes.byref(h)))
+    return MLP(h)
+
+
+def _stream(t, stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return c_void_p(s.cuda_stream)
+
+
+def trk_mlp_forward(net, X, stream=None):
+    """X: float32 CUDA tensor (M, 8) -> logits float32 CUDA tensor (M,)."""
+    import torch
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(lib().trk_mlp_forward(net.handle, _dptr(X), X.shape[0], _dptr(out), _stream(X, stream)))
+    return out
+
+
+def trk_mlp_grad(net, X, y, stream=None):
+    import torch
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    _check(lib().trk_mlp_grad(net.handle, _dptr(X), _dptr(y), X.shape[0], _dptr(loss), _stream(X, stream)))
+    return loss
+
+
+def trk_mlp_adam(net, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().trk_mlp_adam(net.handle, lr, beta1, beta2, eps, c_void_p(s.cuda_stream)))
+
+
+def trk_mlp_train(net, X, y, batch, epochs, perm=None, lr=1e-3, stream=None):
+    """Returns the per-step loss history (float32 CUDA tensor)."""
+    import torch
+    n = X.shape[0]
+    steps = epochs * ((n + batch - 1) // batch)
+    hist = torch.zeros(steps, dtype=torch.float32, device=X.device)
+    _check(lib().trk_mlp_train(net.handle, _dptr(X), _dptr(y), n, batch, epochs, _dptr(perm), lr, _dptr(hist),
+                               _stream(X, stream)))
+    return hist
+
+
+def trk_mlp_get(net):
+    """Host copies: (params [(W, b)], grads [(gW, gb)]) as float32 arrays."""
+    Ws = [np.zeros(s, np.float32) for s in MLP_SHAPES]
+    bs = [np.zeros(s[0], np.float32) for s in MLP_SHAPES]
+    gWs = [np.zeros(s, np.float32) for s in MLP_SHAPES]
+    gbs = [np.zeros(s[0], np.float32) for s in MLP_SHAPES]
+    _check(lib().trk_mlp_get(net.handle, _fptrs(Ws), _fptrs(bs), _fptrs(gWs), _fptrs(gbs)))
+    return list(zip(Ws, bs)), list(zip(gWs, gbs))
+
+
+def trk_da_triage(lattices, params, opts, net=None, audit=None, perm=None, stream=None):
+    """params: float32 CUDA tensor (n_var, 6); audit: uint8 CUDA tensor
+    (n_var, ny, nx) or None; opts: dict of trk_triage_opts fields.
+    Returns (mask uint8, survival int32 CUDA tensors (n_var, ny, nx), stats dict)."""
+    import torch
+    o = trk_triage_opts()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    nv = len(lattices)
+    mask = torch.zeros((nv, o.ny, o.nx), dtype=torch.uint8, device=params.device)
+    surv = torch.zeros((nv, o.ny, o.nx), dtype=torch.int32, device=params.device)
+    st = trk_triage_stats()
+    _check(lib().trk_da_triage(_handles(lattices), nv, _dptr(params), _dptr(audit),
+                               net.handle if net is not None else None, _dptr(perm), ctypes.byref(o),
+                               _dptr(mask), _dptr(surv), ctypes.byref(st), _stream(params, stream)))
+    stats = {f: getattr(st, f) for f, _ in trk_triage_stats._fields_}
+    return mask, surv, stats
 
 
 def trk_bunch_enable_timing(b, on=True):

@@ -101,3 +101,22 @@ def test_step_work_accounting():
     # kick-drift quad with 4 steps: entry 10 + 13 drifts x 16 + 12 kicks x 4 + exit 8
     assert flops.element_flops({"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}) == 274
     assert flops.element_flops({"type": "KSEXT", "L": 0.1, "K2": 20.0, "n_kicks": 4}) == 322
+
+
+def test_da_boundary_metric():
+    import numpy as np
+    from paper_1710_07350_gb300 import da_metrics as dm
+    exh = np.zeros((9, 9), bool)
+    exh[2:7, 2:7] = True
+    b = dm.boundary(exh)
+    assert b[2, 2] and b[1, 1] and b[4, 1] and not b[4, 4] and not b[0, 4]
+    ok, nd, r = dm.boundary_difference(exh, exh)
+    assert ok and nd == 0
+    tri = exh.copy()
+    tri[2, 4] = False            # on the boundary: distance 0
+    tri[1, 4] = True             # just outside: distance 0 (neighbour of the edge)
+    assert dm.boundary_difference(tri, exh)[0]
+    tri2 = exh.copy()
+    tri2[4, 4] = False           # deep inside: 2 cells from the boundary
+    ok, nd, r = dm.boundary_difference(tri2, exh)
+    assert not ok and nd == 1 and r == 2
