@@ -61,6 +61,11 @@ def parse():
     # smaller cases for profiling runs only (the bench line uses the defaults)
     p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
     p.add_argument("--particles", type=int, default=N_PARTICLES)
+    p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                   help="c2 (default, the headline line); c3 wake linac and c4 batched variants print "
+                        "their own measurement lines")
+    p.add_argument("--da-variants", type=int, default=64)
     return p.parse_args()
 
 
@@ -244,14 +249,8 @@ def run_ours(args):
     clk = clocks.stop()
     stats = trk.trk_bunch_stats(b)
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms, passes], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_all, passes_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_all, passes_all = total_ms, passes
+    from paper_1710_07350_gb300.dist import combine
+    total_ms_all, passes_all = combine(total_ms, passes, device="cuda")
     value = passes_all / (total_ms_all / 1e3)
     kernel_ms = stats["track_kernel_ms"]
     achieved = flop / (kernel_ms / 1e3) / 1e12
@@ -299,6 +298,7 @@ def run_ours(args):
         return 0
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = profiled_traffic_per_launch(npart, tps)
+    da = None if args.no_da else run_da(args.da_variants, trk, syn, torch)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -321,11 +321,72 @@ def run_ours(args):
         "clocks": clk,
         "passes": passes_all,
         "alive_end": n_alive,
+        "da": da,
     }
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_da(n_var, trk, syn, torch):
+    """DA scans/s on the 64-variant, 512^2-cell, 1000-turn workload: plain
+    (one lattice per call), batched (all variants in one call) and batched plus
+    surrogate triage; the same triage without the network as the ablation.
+    One scan = one variant's full grid."""
+    import numpy as np
+    from paper_1710_07350_gb300 import da_metrics as dm
+    n, turns = syn.DA_N, 1000
+    L = [trk.trk_create_lattice(syn.lattice_c5(v), moments=False) for v in range(n_var)]
+    z = syn.da_particles(n=n)
+    x0 = torch.from_numpy(z[:, 0].copy()).cuda()
+    y0 = torch.from_numpy(z[:, 2].copy()).cuda()
+    trk.trk_da_survival(L[:1], x0[:4096], y0[:4096], [0, 4096], 20)   # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for v in range(n_var):
+        trk.trk_da_survival([L[v]], x0, y0, [0, n * n], turns)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t
+    t = time.perf_counter()
+    exh = trk.trk_da_survival(L, torch.cat([x0] * n_var), torch.cat([y0] * n_var),
+                              [k * n * n for k in range(n_var + 1)], turns)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t
+    exh = (exh.cpu().numpy().reshape(n_var, n, n) == turns + 1)
+    params = torch.from_numpy(syn.c5_params()[:n_var].astype(np.float32)).cuda()
+    g = np.random.Generator(np.random.Philox(key=12))
+    audit = torch.from_numpy((g.uniform(size=(n_var, n, n)) < 0.005).astype(np.uint8)).cuda()
+    stride, epochs, batch = 8, 24, 4096
+    ncoarse = n_var * ((n - stride // 2 + stride - 1) // stride) ** 2
+    perm = torch.from_numpy(np.stack([g.permutation(ncoarse) for _ in range(epochs)]).astype(np.int32)).cuda()
+    out = {"variants": n_var, "grid": [n, n], "turns": turns, "coarse_stride": stride, "band_radius": 2,
+           "audit_fraction": 0.005}
+    res = {}
+    for name, use in (("surrogate", 1), ("nonlearned", 0)):
+        net = trk.trk_mlp_create(syn.mlp_init(7)) if use else None
+        opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
+                "band_radius": 2, "use_mlp": use, "epochs": epochs, "batch": batch, "lr": 2e-3}
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        mask, _, st = trk.trk_da_triage(L, params, opts, net=net, audit=audit, perm=perm if use else None)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        mask = mask.cpu().numpy().astype(bool)
+        diffs = [dm.boundary_difference(mask[v], exh[v]) for v in range(n_var)]
+        res[name] = {"seconds": dt, "scans_per_s": n_var / dt,
+                     "boundary_within_1_cell": all(d[0] for d in diffs),
+                     "cells_differing": int(sum(d[1] for d in diffs)),
+                     "max_cell_distance": int(max(d[2] for d in diffs)),
+                     "tracked_fraction": (st["n_tracked"] + st["n_coarse"]) / st["n_cells"],
+                     "audit_cells": st["n_audit"], "audit_wrong": st["n_audit_wrong"],
+                     "ms": {k: st[k] for k in ("ms_coarse", "ms_train", "ms_infer", "ms_band", "ms_retrack")}}
+    out["scans_per_s"] = {"plain": n_var / t_plain, "batched": n_var / t_batched,
+                          "batched_surrogate": res["surrogate"]["scans_per_s"],
+                          "batched_nonlearned_triage": res["nonlearned"]["scans_per_s"]}
+    out["surrogate_vs_plain"] = res["surrogate"]["scans_per_s"] / (n_var / t_plain)
+    out["triage"] = res
+    return out
 
 
 def profiled_traffic_per_launch(npart, tps):
@@ -343,10 +404,103 @@ def profiled_traffic_per_launch(npart, tps):
     return None
 
 
+def run_c3(args):
+    """Wake linac: 10M particles through 200 x [RF, WAKE(4096), drift, quad];
+    one step = one pass of the whole linac from the initial bunch."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import flops, trk
+    lat = syn.lattice_c3()
+    L = trk.trk_create_lattice(lat)
+    z0 = syn.bunch("c3")
+    coords0, ids0 = trk.upload(z0)
+    n = z0.shape[0]
+    times = []
+    for k in range(args.warmup + args.steps):
+        coords, ids = coords0.clone(), ids0.clone()
+        b = trk.trk_bunch_wrap(coords, ids)
+        trk.trk_bunch_set_schedule(b, block=args.block, per_thread=args.per_thread)
+        trk.trk_bunch_enable_timing(b, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        trk.trk_track(b, L, 1)
+        e1.record()
+        e1.synchronize()
+        st = trk.trk_bunch_stats(b)
+        if k >= args.warmup:
+            times.append((e0.elapsed_time(e1), st))
+        del b
+    ms = sum(t for t, _ in times) / len(times)
+    kms = sum(st["track_kernel_ms"] for _, st in times) / len(times)
+    passes = n * len(lat["elements"])
+    _, f = flops.step_work(lat, n, 1)
+    f += n * 200 * flops.WAKE_FLOPS_PER_PARTICLE + 200 * flops.wake_conv_flops(syn.C3_NBINS)
+    print(json.dumps({"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins, drift, quad], 1e7 particles",
+                      "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
+                      "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
+                      "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, "launches": times[0][1]["launches"],
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
+def run_c4(args):
+    """256 lattice variants (log-uniform 1000..65536 particles), 1000 turns:
+    batched (autotuned schedule, one CUDA graph per call) against one
+    lattice at a time."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import trk
+    vs = syn.c4_variants()
+    lats = [syn.lattice_c4(v) for v in vs]
+    Ls = [trk.trk_create_lattice(l) for l in lats]
+    inputs = [trk.upload(syn.c4_bunch(k, v[2])) for k, v in enumerate(vs)]
+    turns = 1000
+
+    def fresh():
+        return [trk.trk_bunch_wrap(c.clone(), i.clone()) for c, i in inputs]
+
+    tuned, probe_ms = trk.trk_autotune(fresh(), Ls, 20)
+    res = {}
+    for mode in ("batched", "plain"):
+        best = None
+        for k in range(args.warmup + 1):
+            bs = fresh()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if mode == "batched":
+                B = trk.trk_batch_create(bs, Ls)
+                trk.trk_batch_set_schedule(B, **tuned)
+                trk.trk_batch_track(B, turns)
+            else:
+                for b, L in zip(bs, Ls):
+                    trk.trk_bunch_set_schedule(b, block=128, per_thread=2, chunk_turns=100)
+                    trk.trk_track(b, L, turns)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            if k >= args.warmup:
+                best = dt
+            alive = sum(trk.trk_n_alive(b) for b in bs)
+        res[mode] = best
+    n_tot = sum(v[2] for v in vs)
+    passes = n_tot * 60 * turns
+    print(json.dumps({"workload": "c4: 256 variants of the FODO ring + thin sextupoles, %d particles, 1000 turns" % n_tot,
+                      "metric": UNIT, "batched_value": passes / res["batched"], "plain_value": passes / res["plain"],
+                      "batched_s": res["batched"], "plain_s": res["plain"], "speedup": res["plain"] / res["batched"],
+                      "autotuned_schedule": tuned, "alive_end": alive, "note": "passes counted as if all survive"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3":
+        return run_c3(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 

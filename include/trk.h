@@ -201,6 +201,14 @@ trk_status trk_batch_set_schedule(trk_batch *B, const trk_schedule *s);
 trk_status trk_batch_get_schedule(const trk_batch *B, trk_schedule *s);
 trk_status trk_batch_track(trk_batch *B, int32_t n_turns);
 trk_status trk_batch_destroy(trk_batch *B);
+/* Project-written autotuner for batched calls: times probe_turns turns of
+ * every candidate schedule -- (block, particles per thread) in {(128,1),
+ * (128,2), (64,2), (256,2), (128,4), (64,4)} x chunk plan {fixed chunks of
+ * probe_turns, growing chunks 1, 2, 4, ...} -- on shadow copies of the alive
+ * particles (the caller's bunches are not changed), and returns the fastest in
+ * *out (and its probe time in *best_ms if not NULL).  Synchronises. */
+trk_status trk_autotune(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                        int32_t probe_turns, trk_schedule *out, double *best_ms);
 /* One-shot form: create, set the schedule (if sched != NULL), track, destroy. */
 trk_status trk_track_batch(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
                            int32_t n_turns, const trk_schedule *sched);

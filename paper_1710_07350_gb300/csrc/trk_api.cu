@@ -898,9 +898,13 @@ extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_
     if (total == 0) return TRK_OK;
     if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival: NULL point or output array");
     cudaStream_t s = (cudaStream_t)stream;
+    // each variant's slice starts on a 32-byte boundary of the particle arrays
+    std::vector<int64_t> slot(n_var + 1, 0);
+    for (int v = 0; v < n_var; ++v) slot[v + 1] = slot[v] + (offsets[v + 1] - offsets[v] + 3) / 4 * 4;
+    const int64_t pitch = slot[n_var] > 0 ? slot[n_var] : 1;
     double *coords = nullptr;
     int32_t *ids = nullptr;
-    if (dalloc(&coords, 6 * (size_t)total) != cudaSuccess || dalloc(&ids, total) != cudaSuccess) {
+    if (dalloc(&coords, 6 * (size_t)pitch) != cudaSuccess || dalloc(&ids, pitch) != cudaSuccess) {
         cudaFree(coords);
         return fail(TRK_ENOMEM, "trk_da_survival: particle allocation failed");
     }
@@ -908,13 +912,15 @@ extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_
     std::vector<const trk_lattice *> L;
     trk_batch *B = nullptr;
     trk_status st = TRK_OK;
-    cudaError_t e = launch_da_init(coords, total, ids, d_x0, d_y0, total, s);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < n_var && e == cudaSuccess; ++v)
+        e = launch_da_init(coords + slot[v], pitch, ids + slot[v], d_x0, d_y0, offsets[v], offsets[v + 1] - offsets[v], s);
     if (e != cudaSuccess) st = fail(TRK_ECUDA, std::string("trk_da_survival: ") + cudaGetErrorString(e));
     for (int v = 0; v < n_var && st == TRK_OK; ++v) {
         const int64_t n = offsets[v + 1] - offsets[v];
         if (n == 0) continue;
         trk_bunch *b = nullptr;
-        st = trk_bunch_wrap(coords + offsets[v], total, ids + offsets[v], n, stream, &b);
+        st = trk_bunch_wrap(coords + slot[v], pitch, ids + slot[v], n, stream, &b);
         if (st == TRK_OK) {
             bunches.push_back(b);
             L.push_back(lats[v]);
@@ -937,6 +943,99 @@ extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_
     cudaFree(coords);
     cudaFree(ids);
     return st;
+}
+
+
+// ------------------------------------------------------------- autotune ----
+
+extern "C" trk_status trk_autotune(trk_bunch *const *bunches, const trk_lattice *const *lats, int32_t n_var,
+                                   int32_t probe_turns, trk_schedule *out, double *best_ms) {
+    if (!bunches || !lats || n_var < 1 || !out || probe_turns < 1)
+        return fail(TRK_EINVAL, "trk_autotune: bad argument");
+    cudaStream_t s = bunches[0]->stream;
+    // shadow copies of the alive particles, so the caller's bunches are untouched
+    std::vector<double *> sc(n_var, nullptr);
+    std::vector<int32_t *> si(n_var, nullptr);
+    std::vector<trk_bunch *> sb(n_var, nullptr);
+    trk_status st = TRK_OK;
+    auto cleanup = [&]() {
+        for (int v = 0; v < n_var; ++v) {
+            if (sb[v]) trk_bunch_free(sb[v]);
+            cudaFree(sc[v]);
+            cudaFree(si[v]);
+        }
+    };
+    for (int v = 0; v < n_var && st == TRK_OK; ++v) {
+        trk_bunch *b = bunches[v];
+        int64_t na = 0;
+        st = trk_n_alive(b, &na);
+        if (st != TRK_OK) break;
+        const int64_t n = na > 0 ? na : 1;
+        if (dalloc(&sc[v], 6 * (size_t)n) != cudaSuccess || dalloc(&si[v], n) != cudaSuccess) {
+            st = fail(TRK_ENOMEM, "trk_autotune: shadow allocation failed");
+            break;
+        }
+        if (na > 0) {
+            cudaError_t e = cudaMemcpy2DAsync(sc[v], n * sizeof(double), b->coords, b->pitch * sizeof(double),
+                                              na * sizeof(double), 6, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(si[v], b->ids, na * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) {
+                st = fail(TRK_ECUDA, std::string("trk_autotune: copy failed: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
+        st = trk_bunch_wrap(sc[v], n, si[v], na, s, &sb[v]);
+        if (st == TRK_OK) {
+            sb[v]->p0c = b->p0c_set ? b->p0c : lats[v]->p0c;
+            sb[v]->p0c_set = true;
+        }
+    }
+    if (st != TRK_OK) {
+        cleanup();
+        return st;
+    }
+    // candidate schedules: launch shape x chunk plan
+    const int shapes[][2] = {{128, 1}, {128, 2}, {64, 2}, {256, 2}, {128, 4}, {64, 4}};
+    const int plans[][2] = {{probe_turns, 0}, {1, 2}};
+    double best = 1e300;
+    trk_schedule best_s = {128, 2, probe_turns, 0};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (auto &sh : shapes) {
+        for (auto &pl : plans) {
+            trk_batch *B = nullptr;
+            st = trk_batch_create(sb.data(), lats, n_var, &B);
+            if (st != TRK_OK) break;
+            trk_schedule cand = {sh[0], sh[1], pl[0], pl[1]};
+            st = trk_batch_set_schedule(B, &cand);
+            // the shadows advance with every probe; each probe starts from their
+            // current state, which only shifts the turn counter
+            if (st == TRK_OK) st = trk_batch_track(B, probe_turns);  // warm-up and graph capture
+            if (st == TRK_OK) {
+                cudaEventRecord(e0, s);
+                st = trk_batch_track(B, probe_turns);
+                cudaEventRecord(e1, s);
+            }
+            trk_batch_destroy(B);
+            if (st != TRK_OK) break;
+            float ms = 0.0f;
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_s = cand;
+            }
+        }
+        if (st != TRK_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    if (st != TRK_OK) return st;
+    *out = best_s;
+    if (best_ms) *best_ms = best;
+    return TRK_OK;
 }
 
 extern "C" trk_status trk_bunch_enable_timing(trk_bunch *b, int32_t on) {

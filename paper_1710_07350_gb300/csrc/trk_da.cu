@@ -6,16 +6,17 @@
 namespace trk {
 namespace {
 
+// Particles i < n of one variant's slice from points first + i.
 __global__ void k_da_init(double *__restrict__ coords, int64_t pitch, int32_t *__restrict__ ids,
-                          const double *__restrict__ x0, const double *__restrict__ y0, int64_t n) {
+                          const double *__restrict__ x0, const double *__restrict__ y0, int64_t first, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        coords[i] = x0[i];
+        coords[i] = x0[first + i];
         coords[pitch + i] = 0.0;
-        coords[2 * pitch + i] = y0[i];
+        coords[2 * pitch + i] = y0[first + i];
         coords[3 * pitch + i] = 0.0;
         coords[4 * pitch + i] = 0.0;
         coords[5 * pitch + i] = 0.0;
-        ids[i] = (int32_t)i;
+        ids[i] = (int32_t)(first + i);
     }
 }
 
@@ -36,10 +37,10 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0, int64_t n,
-                           cudaStream_t s) {
+cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0,
+                           int64_t first, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_da_init<<<grid_for(n), 256, 0, s>>>(coords, pitch, ids, x0, y0, n);
+    k_da_init<<<grid_for(n), 256, 0, s>>>(coords, pitch, ids, x0, y0, first, n);
     return cudaGetLastError();
 }
 

@@ -122,8 +122,8 @@ cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins
                              cudaStream_t s);
 
 // Dynamic-aperture helpers (trk_da.cu).
-cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0, int64_t n,
-                           cudaStream_t s);
+cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0,
+                           int64_t first, int64_t n, cudaStream_t s);
 cudaError_t launch_da_survival(const int32_t *ids, const int32_t *lt, int64_t n, int32_t n_turns, int32_t *survival,
                                cudaStream_t s);
 

@@ -18,7 +18,11 @@
 namespace trk {
 namespace {
 
-__device__ __forceinline__ double cell_centre(int i, int n, double w) { return -w + (i + 0.5) * (2.0 * w / n); }
+// Cell centre -w + (i + 1/2)(2w/n), rounded operation by operation (no FMA
+// contraction) so that it equals the same expression evaluated on the host.
+__device__ __forceinline__ double cell_centre(int i, int n, double w) {
+    return __dadd_rn(-w, __dmul_rn(__dadd_rn((double)i, 0.5), __ddiv_rn(__dmul_rn(2.0, w), (double)n)));
+}
 
 // Coarse cells (ix, iy) with ix % stride == off, iy % stride == off, per variant.
 __global__ void k_coarse_points(int nx, int ny, int stride, int off, double w, int cx, int cy, int n_var,

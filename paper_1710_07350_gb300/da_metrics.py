@@ -38,9 +38,9 @@ def dilate(b, r):
     return out
 
 
-def boundary_difference(tri, exh):
+def boundary_difference(tri, exh, r_max=8):
     """(ok, n_diff, max Chebyshev distance in cells from a differing cell to the
-    nearest exhaustive boundary cell) for one variant's masks."""
+    nearest exhaustive boundary cell, capped at r_max + 1) for one variant's masks."""
     tri = np.asarray(tri, bool)
     exh = np.asarray(exh, bool)
     diff = tri != exh
@@ -49,7 +49,7 @@ def boundary_difference(tri, exh):
     b = boundary(exh)
     r = 0
     d = b.copy()
-    while np.any(diff & ~d) and r < max(tri.shape):
+    while np.any(diff & ~d) and r <= r_max:
         r += 1
         d = dilate(b, r)
     return r <= 1, int(diff.sum()), r

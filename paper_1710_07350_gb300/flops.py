@@ -23,6 +23,16 @@ Per particle and pass (alive particle entering the element):
 import numpy as np
 
 MOMENTS_FLOPS = 54
+# Wake element per alive particle: min/max (2 compares), bin index (sub, div,
+# floor: 3), kick (sub, div, sub, floor, sub, 2 for the interpolation, div by p0
+# and add: 9) -> 14; the convolution adds nbins^2/2 multiply-adds per wake.
+WAKE_FLOPS_PER_PARTICLE = 14
+
+
+def wake_conv_flops(nbins):
+    return float(nbins) * (nbins + 1)
+
+
 APERTURE_FLOPS = {None: 0, "rect": 4, "ellipse": 6}
 
 

@@ -95,6 +95,7 @@ def lib():
             "trk_batch_track": [P, c_int32],
             "trk_batch_destroy": [P],
             "trk_track_batch": [P, P, c_int32, c_int32, P],
+            "trk_autotune": [P, P, c_int32, c_int32, P, P],
             "trk_da_survival": [P, c_int32, P, P, P, c_int32, P, P, P],
             "trk_mlp_create": [P, P, P],
             "trk_mlp_destroy": [P],
@@ -324,6 +325,15 @@ def trk_batch_get_schedule(B):
 
 def trk_batch_track(B, n_turns):
     _check(lib().trk_batch_track(B.handle, n_turns))
+
+
+def trk_autotune(bunches, lattices, probe_turns):
+    """Fastest batched schedule for these pairs: (schedule dict, probe ms)."""
+    s = trk_schedule()
+    ms = c_double()
+    _check(lib().trk_autotune(_handles(bunches), _handles(lattices), len(bunches), probe_turns, ctypes.byref(s),
+                              ctypes.byref(ms)))
+    return {"block": s.block, "per_thread": s.per_thread, "chunk_turns": s.chunk_turns, "growth": s.growth}, ms.value
 
 
 def trk_track_batch(bunches, lattices, n_turns, schedule=None):

@@ -1,0 +1,43 @@
+"""The multi-rank bench path (replica bunches, max time / summed work) with two
+gloo ranks on the CPU."""
+import os
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1710_07350_gb300.dist import combine
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t, p = combine(100.0 + 50.0 * rank, 1e9 * (rank + 1))
+    q.put((rank, t, p))
+    dist.destroy_process_group()
+
+
+def test_combine_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, p in out:
+        assert t == 150.0 and p == 3e9
+
+
+def test_combine_single_process():
+    from paper_1710_07350_gb300.dist import combine
+    assert combine(12.5, 7.0) == (12.5, 7.0)

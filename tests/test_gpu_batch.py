@@ -116,3 +116,24 @@ def test_batch_rejects_wake_lattice():
     b = trk.trk_bunch_wrap(coords, ids)
     with pytest.raises(trk.TrkError):
         trk.trk_batch_create([b], [L])
+
+
+def test_autotune_leaves_bunches_untouched_and_returns_valid_schedule():
+    vs = variants(6)
+    lats, bunches, _ = make(vs)
+    before = [result(b) for b in bunches]
+    sched, ms = trk.trk_autotune(bunches, lats, 4)
+    assert sched["block"] in (64, 128, 256) and sched["per_thread"] in (1, 2, 4) and ms > 0
+    for b, r in zip(bunches, before):
+        a = result(b)
+        assert np.array_equal(a["z"], r["z"]) and a["n_alive"] == r["n_alive"]
+    # the chosen schedule runs and gives the same coordinates as the default one
+    B = trk.trk_batch_create(bunches, lats)
+    trk.trk_batch_set_schedule(B, **sched)
+    trk.trk_batch_track(B, 6)
+    lats2, bunches2, _ = make(vs)
+    trk.trk_track_batch(bunches2, lats2, 6, {"block": 128, "per_thread": 1, "chunk_turns": 6})
+    for b1, b2 in zip(bunches, bunches2):
+        z1, _, _, _ = by_id(result(b1), b1.n)
+        z2, _, _, _ = by_id(result(b2), b2.n)
+        assert np.array_equal(z1, z2)

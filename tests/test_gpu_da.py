@@ -67,7 +67,6 @@ def test_triage_matches_exhaustive_boundary(use_mlp):
         perm = torch.from_numpy(np.stack([g.permutation(ncoarse) for _ in range(60)]).astype(np.int32)).cuda()
     mask, surv, st = trk.trk_da_triage(L, params, opts, net=net, audit=audit, perm=perm)
     mask, surv = mask.cpu().numpy(), surv.cpu().numpy()
-    tracked = (surv != 0) & (surv != turns + 1) | np.isin(surv, [turns + 1])  # survival known or predicted
     for v in range(nv):
         ok, nd, r = dm.boundary_difference(mask[v], exh[v] == turns + 1)
         assert ok, (v, nd, r)
