@@ -22,8 +22,11 @@ namespace {
 // 4e-18 relative.  v >= 0 (a sum of squares) or NaN, so the test is an integer
 // compare of the high word (NaN fails it and takes the exact branch).
 constexpr int kSeriesMaxHi = 0x3F100000;  // high word of 2^-14
+// Below 2^-19 the cubic terms of the series are also below 2e-18 and dropped.
+constexpr int kQuadMaxHi = 0x3EC00000;    // high word of 2^-19
 
 __device__ __forceinline__ bool series_ok(double v) { return __double2hiint(v) < kSeriesMaxHi; }
+__device__ __forceinline__ bool quad_ok(double v) { return __double2hiint(v) < kQuadMaxHi; }
 
 // The P particles a thread owns, advanced in lock-step through every element so
 // that their independent FP64 chains interleave (the pipe's latency is long
@@ -141,14 +144,14 @@ __device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-        g[p] = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
-        need |= !series_ok(u);
+        g[p] = u * fma(u, 0.375, 0.5);
+        need |= !quad_ok(u);
     }
     if (need) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-            if (!series_ok(u)) g[p] = drift_g_exact(u);
+            if (!quad_ok(u)) g[p] = series_ok(u) ? u * fma(u, fma(u, 0.3125, 0.375), 0.5) : drift_g_exact(u);
         }
     }
 #pragma unroll
@@ -173,27 +176,85 @@ __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P
         }
     }
     if (FL & 2u) {
+        // qx -= hb (x^2 - y^2) and qy += b x y as three products and three FMAs
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double t = (x[p] - y[p]) * (x[p] + y[p]);
-            qx[p] = fma(-hb[p], t, qx[p]);
-            qy[p] = fma(b[p], x[p] * y[p], qy[p]);
+            const double hx = hb[p] * x[p], hy = hb[p] * y[p], bx = b[p] * x[p];
+            qx[p] = fma(hy, y[p], fma(-hx, x[p], qx[p]));
+            qy[p] = fma(bx, y[p], qy[p]);
         }
     }
 }
 
+// Slopes -> scaled canonical momenta: qx = x' (1 + x'^2 + y'^2)^(-1/2).
+template <int P>
+__device__ __forceinline__ void v_to_canonical(Tile<P> &q) {
+    double c[P];
+    bool need = false;
+    // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+        c[p] = fma(v, fma(v, 0.375, -0.5), 1.0);
+        need |= !quad_ok(v);
+    }
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+            if (!quad_ok(v))
+                c[p] = series_ok(v) ? fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0) : rsqrt_exact(1.0 + v);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        q.xp[p] = c[p] * q.xp[p];
+        q.yp[p] = c[p] * q.yp[p];
+    }
+}
+
+// Scaled canonical momenta -> slopes: x' = qx (1 - u)^(-1/2) = qx (1 + g).
+__device__ __forceinline__ double2 slopes_of(double qx, double qy) {
+    const double u = fma(qx, qx, qy * qy);
+    double g = u * fma(u, 0.375, 0.5);
+    if (!quad_ok(u)) g = series_ok(u) ? u * fma(u, fma(u, 0.3125, 0.375), 0.5) : drift_g_exact(u);
+    return make_double2(fma(qx, g, qx), fma(qy, g, qy));
+}
+
+template <int P>
+__device__ __forceinline__ void v_to_slopes(Tile<P> &q) {
+    double g[P];
+    bool need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double u = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+        g[p] = u * fma(u, 0.375, 0.5);
+        need |= !quad_ok(u);
+    }
+    if (need) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double u = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
+            if (!quad_ok(u)) g[p] = series_ok(u) ? u * fma(u, fma(u, 0.3125, 0.375), 0.5) : drift_g_exact(u);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        q.xp[p] = fma(q.xp[p], g[p], q.xp[p]);
+        q.yp[p] = fma(q.yp[p], g[p], q.yp[p]);
+    }
+}
+
 // n steps of the 4th-order Yoshida scheme D K D K D K D with adjacent drifts of
-// consecutive steps merged; slopes converted to scaled canonical momenta at
-// entry, qx = x' (1 + x'^2 + y'^2)^(-1/2), and back at exit, x' = qx (1 + g).
-// FL: bit 0 quadrupole kick, bit 1 sextupole kick (one instantiation each, so
-// that only the strengths in use occupy registers).
+// consecutive steps merged, on the scaled canonical momenta (q.xp, q.yp hold
+// qx, qy here).  FL: bit 0 quadrupole kick, bit 1 sextupole kick (one
+// instantiation each, so that only the strengths in use occupy registers).
 template <int P, uint32_t FL>
 __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P], const DevElem *__restrict__ E) {
     const int n = __ldg(&E->n);
-    constexpr uint32_t fl = FL;
     const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
-    double qx[P], qy[P], a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
-    if (fl & 1u) {
+    double a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
+    if (FL & 1u) {
         const double A1 = __ldg(&E->p[3]), A0 = __ldg(&E->p[4]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -201,7 +262,7 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
             a0[p] = A0 * iP[p];
         }
     }
-    if (fl & 2u) {
+    if (FL & 2u) {
         const double H1 = __ldg(&E->p[5]), H0 = __ldg(&E->p[6]), B1 = __ldg(&E->p[7]), B0 = __ldg(&E->p[8]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -211,66 +272,29 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
             b0[p] = B0 * iP[p];
         }
     }
-    bool need = false;
-    // (1 + v)^(-1/2) = 1 - v/2 + 3v^2/8 - 5v^3/16 + ...
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
-        const double c = fma(v, fma(v, fma(v, -0.3125, 0.375), -0.5), 1.0);
-        qx[p] = c * q.xp[p];
-        qy[p] = c * q.yp[p];
-        need |= !series_ok(v);
-    }
-    if (need) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
-            if (!series_ok(v)) {
-                const double c = rsqrt_exact(1.0 + v);
-                qx[p] = c * q.xp[p];
-                qy[p] = c * q.yp[p];
-            }
-        }
-    }
-    v_drift<P>(q.x, q.y, q.l, qx, qy, d1);
+    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1);
     for (int s = 0; s < n; ++s) {
-        v_kick<P, FL>(q.x, q.y, qx, qy, a1, hb1, b1);
-        v_drift<P>(q.x, q.y, q.l, qx, qy, d2);
-        v_kick<P, FL>(q.x, q.y, qx, qy, a0, hb0, b0);
-        v_drift<P>(q.x, q.y, q.l, qx, qy, d2);
-        v_kick<P, FL>(q.x, q.y, qx, qy, a1, hb1, b1);
-        v_drift<P>(q.x, q.y, q.l, qx, qy, s + 1 < n ? dm : d1);
-    }
-    // x' = px/pz = qx (1 - u)^(-1/2) = qx (1 + g)
-    double g[P];
-    need = false;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-        g[p] = u * fma(u, fma(u, 0.3125, 0.375), 0.5);
-        need |= !series_ok(u);
-    }
-    if (need) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-            if (!series_ok(u)) g[p] = drift_g_exact(u);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        q.xp[p] = fma(qx[p], g[p], qx[p]);
-        q.yp[p] = fma(qy[p], g[p], qy[p]);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0, b0);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, s + 1 < n ? dm : d1);
     }
 }
 
+// Kick-drift element; leaves the tile in the canonical representation.
 template <int P>
-__device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &dirty,
+__device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &dirty, bool &canon,
                                              const DevElem *__restrict__ E) {
     if (dirty) {
 #pragma unroll
         for (int p = 0; p < P; ++p) iP[p] = 1.0 / (1.0 + q.d[p]);
         dirty = false;
+    }
+    if (!canon) {
+        v_to_canonical<P>(q);
+        canon = true;
     }
     switch (__ldg(&E->flags) & 3u) {
     case 1u: v_kick_drift_t<P, 1u>(q, iP, E); break;
@@ -457,12 +481,19 @@ __device__ __forceinline__ void store_particle(const TrackArgs &a, int64_t i, co
 // record) and its registers are zeroed so that it keeps taking the fast paths.
 template <int P>
 __device__ __forceinline__ void apply_aperture(const TrackArgs &a, const LatticeView &L, Tile<P> &q,
-                                               bool (&alive)[P], int64_t base, int turn, int e, int &lost_here) {
+                                               bool (&alive)[P], int64_t base, int turn, int e, int &lost_here,
+                                               bool canon) {
     if (L.ap_type == TRK_APERTURE_NONE) return;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (alive[p] && !inside(q.x[p], q.y[p], L)) {
             const int64_t i = base + (int64_t)p * blockDim.x + threadIdx.x;
+            if (canon) {
+                // the record holds slopes whatever the representation in registers
+                const double2 sl = slopes_of(q.xp[p], q.yp[p]);
+                q.xp[p] = sl.x;
+                q.yp[p] = sl.y;
+            }
             store_particle<P>(a, i, q, p);
             a.loss_turn[i] = turn;
             a.loss_elem[i] = e;
@@ -519,6 +550,11 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
     const LatticeView &L = a.lat;
     const DevElem *__restrict__ elems = L.elems;
     int lost_here = 0;
+    // Between consecutive kick-drift and exact-drift elements the tile keeps the
+    // scaled canonical momenta qx = px/(1+delta) in q.xp, q.yp (x, y and l are
+    // the same in both representations); slopes are restored for every other
+    // element, the moments, loss records and the final store.
+    bool canon = false;
     double p0 = a.p0c;  // reference momentum, identical in every thread
     for (int t = 0; t < a.n_turns; ++t) {
         const int turn = a.turn_abs0 + t;
@@ -534,16 +570,27 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             for (int p = 0; p < P; ++p)
                 if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q.d[p]);
             dirty = true;
-            apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here);
+            apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here, canon);
         }
         for (int e = a.e0; e < a.e1; ++e) {
             const DevElem *E = elems + e;
             const int type = __ldg(&E->type);
+            if (canon && type != TRK_EDRIFT && type != TRK_KQUAD && type != TRK_KSEXT) {
+                v_to_slopes<P>(q);
+                canon = false;
+            }
             switch (type) {
             case TRK_MAP: v_map<P>(q, E, L.terms, dirty); break;
-            case TRK_EDRIFT: v_edrift<P>(q, __ldg(&E->p[0])); break;
+            case TRK_EDRIFT:
+                // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
+                // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
+                if (canon)
+                    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]));
+                else
+                    v_edrift<P>(q, __ldg(&E->p[0]));
+                break;
             case TRK_KQUAD:
-            case TRK_KSEXT: v_kick_drift<P>(q, iP, dirty, E); break;
+            case TRK_KSEXT: v_kick_drift<P>(q, iP, dirty, canon, E); break;
             case TRK_THINSEXT: v_thin_sext<P>(q, E); break;
             case TRK_RFCA: {
                 const double p01 = p0 + __ldg(&E->p[3]);
@@ -553,7 +600,11 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             }
             default: break;
             }
-            apply_aperture<P>(a, L, q, alive, base, turn, e, lost_here);
+            apply_aperture<P>(a, L, q, alive, base, turn, e, lost_here, canon);
+        }
+        if (a.do_moments && canon) {
+            v_to_slopes<P>(q);
+            canon = false;
         }
         if (a.do_moments)
             tile_moments<P>(q, alive, sh, tot, K,
@@ -593,6 +644,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
         }
     }
 
+    if (canon) v_to_slopes<P>(q);
     int na = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
