@@ -361,12 +361,13 @@ def run_da(n_var, trk, syn, torch):
     ncoarse = n_var * ((n - stride // 2 + stride - 1) // stride) ** 2
     perm = torch.from_numpy(np.stack([g.permutation(ncoarse) for _ in range(epochs)]).astype(np.int32)).cuda()
     out = {"variants": n_var, "grid": [n, n], "turns": turns, "coarse_stride": stride, "band_radius": 2,
-           "audit_fraction": 0.005}
+           "audit_fraction": 0.005, "sentinel_stride": 5, "expand_radius": 8}
     res = {}
     for name, use in (("surrogate", 1), ("nonlearned", 0)):
         net = trk.trk_mlp_create(syn.mlp_init(7)) if use else None
         opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
-                "band_radius": 2, "use_mlp": use, "epochs": epochs, "batch": batch, "lr": 2e-3}
+                "band_radius": 2, "use_mlp": use, "epochs": epochs, "batch": batch, "lr": 2e-3,
+                "sentinel_stride": 5, "expand_radius": 8}
         torch.cuda.synchronize()
         t = time.perf_counter()
         mask, _, st = trk.trk_da_triage(L, params, opts, net=net, audit=audit, perm=perm if use else None)
@@ -379,7 +380,8 @@ def run_da(n_var, trk, syn, torch):
                      "cells_differing": int(sum(d[1] for d in diffs)),
                      "max_cell_distance": int(max(d[2] for d in diffs)),
                      "tracked_fraction": (st["n_tracked"] + st["n_coarse"]) / st["n_cells"],
-                     "audit_cells": st["n_audit"], "audit_wrong": st["n_audit_wrong"],
+                     "audit_cells": st["n_audit"], "audit_wrong": st["n_audit_wrong"], "band_passes": st["n_passes"],
+                     "pass_cells": st["pass_cells"], "pass_ms": [round(v, 1) for v in st["pass_ms"]],
                      "ms": {k: st[k] for k in ("ms_coarse", "ms_train", "ms_infer", "ms_band", "ms_retrack")}}
     out["scans_per_s"] = {"plain": n_var / t_plain, "batched": n_var / t_batched,
                           "batched_surrogate": res["surrogate"]["scans_per_s"],
@@ -389,19 +391,42 @@ def run_da(n_var, trk, syn, torch):
     return out
 
 
+TRACK_SOURCES = ("paper_1710_07350_gb300/csrc/trk_track.cu", "paper_1710_07350_gb300/csrc/trk_internal.cuh")
+
+
+def track_source_digest():
+    """SHA-256 over the tracking kernel's sources: ties a DRAM capture to the
+    kernel build it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRACK_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def profiled_traffic_per_launch(npart, tps):
-    """DRAM bytes per k_track launch scaled from the committed ncu summary
-    (profiles/k_track_c2.txt, line 'dram_bytes_per_particle_turn: X'), or None."""
-    path = os.path.join(ROOT, "profiles", "k_track_c2.txt")
+    """DRAM bytes (read + write) of one k_track launch of this workload from the
+    committed ncu summary profiles/k_track_c2.md, whose lines
+    'dram_bytes_per_launch: <particles> <turns> <bytes>' and
+    'kernel_source_sha256: <digest>' record a capture of exactly this launch
+    shape; None when the shape differs or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "k_track_c2.md")
     if not os.path.exists(path):
         return None
+    rec, digest = None, None
     for line in open(path):
-        if line.startswith("dram_bytes_per_particle_turn:"):
+        if line.startswith("dram_bytes_per_launch:"):
             try:
-                return float(line.split(":")[1]) * npart * tps
+                p, t, b = line.split(":")[1].split()
+                rec = (int(p), int(t), float(b))
             except ValueError:
                 return None
-    return None
+        elif line.startswith("kernel_source_sha256:"):
+            digest = line.split(":")[1].strip()
+    if rec is None or digest != track_source_digest() or rec[:2] != (npart, tps):
+        return None
+    return rec[2]
 
 
 def run_c3(args):

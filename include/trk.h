@@ -268,11 +268,16 @@ trk_status trk_mlp_get(trk_mlp *net, float *const *W, float *const *b, float *co
  *      its nearest coarse cell;
  *   3. cells within Chebyshev distance band_radius of a predicted-boundary cell
  *      (8-neighbourhood holding both classes), and the caller's audit cells
- *      (d_audit[v][iy][ix] != 0, optional), are re-tracked exactly in FP64;
+ *      (d_audit[v][iy][ix] != 0, optional), are re-tracked exactly in FP64 and
+ *      merged; the boundary of the merged mask is taken again and the band
+ *      cells not yet tracked are tracked, pass after pass (max_passes at most),
+ *      until a pass finds none, so every cell within band_radius of the final
+ *      boundary is exact (sentinel_stride, expand_radius below);
  *   4. d_mask (uint8 [n_var][ny][nx], 1 = survives) and d_survival (int32,
  *      1-based loss turn or n_turns + 1 where tracked; n_turns + 1 or 0 from the
  *      prediction elsewhere) receive the merged result; stats (host) counts
- *      cells and audit disagreements and times each phase.
+ *      cells, passes and audit disagreements (audit cells whose exact label
+ *      differs from the prediction) and times each phase.
  * Allocates its working arrays and synchronises `stream`. */
 typedef struct {
     int32_t nx, ny;
@@ -283,11 +288,22 @@ typedef struct {
     int32_t use_mlp;
     int32_t epochs, batch;
     float lr;
-    int32_t pad;
+    int32_t max_passes;       /* band passes at most (0: 64) */
+    int32_t sentinel_stride;  /* > 0: also track, in the first pass, the cells of a
+                               * sub-lattice with this stride on both axes (from
+                               * stride/2, plus the cell stride/2 from the far edge);
+                               * <= 2 band_radius + 1 makes the one-cell boundary
+                               * criterion hold by construction; 0: none */
+    int32_t expand_radius;    /* passes after the first also track the cells within
+                               * this Chebyshev distance of a cell whose label the
+                               * previous merge flipped (0: none) */
 } trk_triage_opts;
 typedef struct {
     int64_t n_cells, n_coarse, n_band, n_audit, n_tracked, n_audit_wrong;
     double ms_coarse, ms_train, ms_infer, ms_band, ms_retrack;
+    int64_t n_passes;     /* band passes that tracked at least one cell */
+    int64_t pass_cells[16];  /* cells tracked in pass k (passes past 15 add to [15]) */
+    double pass_ms[16];      /* wall time of pass k: band, gather, track, merge */
 } trk_triage_stats;
 trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_var, const float *d_params,
                          const uint8_t *d_audit, trk_mlp *net, const int32_t *d_perm, const trk_triage_opts *opts,

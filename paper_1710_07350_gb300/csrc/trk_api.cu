@@ -189,6 +189,8 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
         case TRK_EDRIFT:
             if (!std::isfinite(d.length)) s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": bad length");
             E.p[0] = d.length;
+            E.p[1] = 0.5 * d.length;
+            E.p[2] = 0.375 * d.length;
             break;
         case TRK_KQUAD:
         case TRK_KSEXT: {
@@ -206,8 +208,11 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             E.p[4] = d.k1 * (w0 * h);
             E.p[5] = (0.5 * k2) * (w1 * h);
             E.p[6] = (0.5 * k2) * (w0 * h);
-            E.p[7] = k2 * (w1 * h);
-            E.p[8] = k2 * (w0 * h);
+            E.p[7] = 0.5 * E.p[0];
+            E.p[8] = 0.375 * E.p[0];
+            E.p[9] = 0.5 * E.p[1];
+            E.p[10] = 0.375 * E.p[1];
+            E.p[11] = 0.375 * E.p[2];
             E.flags = (d.k1 != 0.0 ? 1u : 0u) | (k2 != 0.0 ? 2u : 0u);
             break;
         }

@@ -17,9 +17,10 @@ constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
 //   KQUAD/KSEXT  p[0] d1 = w1 h / 2     p[1] d2 = (w0 + w1) h / 2   p[2] dm = w1 h
 //                p[3] a1 = K1 w1 h       p[4] a0 = K1 w0 h
 //                p[5] hb1 = K2 w1 h / 2  p[6] hb0 = K2 w0 h / 2
-//                p[7] b1 = K2 w1 h       p[8] b0 = K2 w0 h
+//                p[7] d1 / 2, p[8] 3 d1 / 8, p[9] d2 / 2, p[10] 3 d2 / 8, p[11] 3 dm / 8
+//                (drift series constants; dm = 2 d1 exactly, so dm / 2 = d1)
 //                n = steps; flags bit0 = has K1, bit1 = has K2
-//   EDRIFT       p[0] L
+//   EDRIFT       p[0] L, p[1] L / 2, p[2] 3 L / 8
 //   THINSEXT     p[0] K2L, p[1] K2L / 2
 //   RFCA         p[0] V, p[1] phi [rad], p[2] k_rf = 2 pi f / c, p[3] G = V cos(phi)
 //   WAKE         p[0] W0, p[1] s_c, p[2] charge; n = nbins; term0 = wake ordinal

@@ -35,18 +35,24 @@ enum { EPI_F32 = 0, EPI_GELU = 1, EPI_GELU_STOREZ = 2, EPI_DGELU = 3 };
 // Epilogues: EPI_F32 stores acc (FP32, ldc); EPI_GELU stores bf16(gelu(acc + bias));
 // EPI_GELU_STOREZ also stores z = acc + bias (FP32); EPI_DGELU multiplies acc by
 // gelu'(aux[m][n]) and stores the product (FP32 and BF16).
-// M, N multiples of 64 and K a multiple of 32 (the caller pads).
+// Split-K: block z sums k in [z * k_split, min(K, (z + 1) * k_split)) and stores
+// its FP32 partial at Cf + z * c_split (EPI_F32 only; the caller reduces).
+// M, N multiples of 64, K and k_split multiples of 32, lda, ldb multiples of 8
+// and A, B 16-byte aligned (the caller pads): tiles move as 16-byte vectors.
 template <bool A_T, bool B_NK, int EPI>
 __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
                                               const __nv_bfloat16 *__restrict__ B, int ldb, int K,
                                               float *__restrict__ Cf, int ldc, __nv_bfloat16 *__restrict__ Cb,
-                                              const float *__restrict__ bias, const float *__restrict__ aux) {
+                                              const float *__restrict__ bias, const float *__restrict__ aux,
+                                              int k_split, size_t c_split) {
     __shared__ __align__(16) __nv_bfloat16 sA[BM * SK];
     __shared__ __align__(16) __nv_bfloat16 sB[BN * SK];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int g = lane >> 2, tg = lane & 3;
+    const int kbeg = blockIdx.z * k_split, kend = kbeg + k_split < K ? kbeg + k_split : K;
+    if (EPI == EPI_F32) Cf += blockIdx.z * c_split;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -55,31 +61,33 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
 
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // A tile: BM x BK
-        for (int e = tid; e < BM * BK; e += 128) {
-            int m, k;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        // A tile BM x BK and B tile (stored n-major, sB[n][k]) BN x BK: 256
+        // 16-byte vectors each, two per thread.
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * 128;
             if (!A_T) {
-                m = e / BK;
-                k = e % BK;
-                sA[m * SK + k] = A[(size_t)(m0 + m) * lda + (k0 + k)];
+                const int m = e >> 2, k = (e & 3) * 8;
+                *reinterpret_cast<uint4 *>(&sA[m * SK + k]) =
+                    *reinterpret_cast<const uint4 *>(&A[(size_t)(m0 + m) * lda + (k0 + k)]);
             } else {
-                k = e / BM;
-                m = e % BM;
-                sA[m * SK + k] = A[(size_t)(k0 + k) * lda + (m0 + m)];
+                const int k = e >> 3, m = (e & 7) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(&A[(size_t)(k0 + k) * lda + (m0 + m)]);
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sA[(m + i) * SK + k] = h[i];
             }
-        }
-        // B tile stored n-major: sB[n][k]
-        for (int e = tid; e < BN * BK; e += 128) {
-            int n, k;
             if (B_NK) {
-                n = e / BK;
-                k = e % BK;
-                sB[n * SK + k] = B[(size_t)(n0 + n) * ldb + (k0 + k)];
+                const int n = e >> 2, k = (e & 3) * 8;
+                *reinterpret_cast<uint4 *>(&sB[n * SK + k]) =
+                    *reinterpret_cast<const uint4 *>(&B[(size_t)(n0 + n) * ldb + (k0 + k)]);
             } else {
-                k = e / BN;
-                n = e % BN;
-                sB[n * SK + k] = B[(size_t)(k0 + k) * ldb + (n0 + n)];
+                const int k = e >> 3, n = (e & 7) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(&B[(size_t)(k0 + k) * ldb + (n0 + n)]);
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sB[(n + i) * SK + k] = h[i];
             }
         }
         __syncthreads();
@@ -220,10 +228,26 @@ __global__ void k_sum(const float *__restrict__ a, int64_t n, float scale, float
     if (threadIdx.x == 0) out[0] = sh[0] * scale;
 }
 
-// Adam on FP32 master weights; writes the BF16 copy.
+// out[i] = sum over slices s = 0, 1, ... of part[s * n + i], in slice order.
+constexpr int kSplits = 16;
+__global__ void k_reduce_splits(const float *__restrict__ part, int splits, int64_t n, float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float a = part[i];
+        for (int z = 1; z < splits; ++z) a += part[z * n + i];
+        out[i] = a;
+    }
+}
+
+// Adam on FP32 master weights; writes the BF16 copy.  The bias corrections
+// c1 = 1 - beta1^t, c2 = 1 - beta2^t come as values, or (c12 != NULL) from the
+// table c12[2 * step], c12[2 * step + 1] at the device step counter.
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g,
                        __nv_bfloat16 *__restrict__ pb, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float c2, const float *__restrict__ c12, const int64_t *__restrict__ step) {
+    if (c12) {
+        c1 = c12[2 * *step];
+        c2 = c12[2 * *step + 1];
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -271,6 +295,7 @@ struct trk_mlp {
     __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
     float *logit = nullptr, *dl = nullptr, *loss_terms = nullptr, *loss = nullptr;
     float *part = nullptr;                                         // column-sum partials
+    float *splitk = nullptr;                                       // split-K partials of dW [kSplits][256][256]
     int64_t t = 0;                                                 // Adam step
 };
 
@@ -351,6 +376,7 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
     if (e == cudaSuccess) e = cudaMalloc(&N->pb, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&N->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->part, kColSlices * kW * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->splitk, (size_t)kSplits * kW * kW * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(N->p, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(N->m, 0, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(N->v, 0, off * sizeof(float));
@@ -366,6 +392,8 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
         cudaFree(N->g);
         cudaFree(N->pb);
         cudaFree(N->loss);
+        cudaFree(N->part);
+        cudaFree(N->splitk);
         delete N;
         return mlp_fail(TRK_ENOMEM, std::string("trk_mlp_create: ") + cudaGetErrorString(e));
     }
@@ -384,6 +412,7 @@ extern "C" trk_status trk_mlp_destroy(trk_mlp *N) {
     cudaFree(N->pb);
     cudaFree(N->loss);
     cudaFree(N->part);
+    cudaFree(N->splitk);
     delete N;
     return TRK_OK;
 }
@@ -399,10 +428,10 @@ static cudaError_t mlp_forward_rows(trk_mlp *N, const float *X, int64_t M, int64
         const float *b = N->p + N->b_off[l];
         if (training)
             k_gemm<false, true, EPI_GELU_STOREZ><<<grid, 128, 0, s>>>(N->H[l], K, W, K, K, N->Z[l], kW, N->H[l + 1],
-                                                                      b, nullptr);
+                                                                      b, nullptr, K, 0);
         else
             k_gemm<false, true, EPI_GELU><<<grid, 128, 0, s>>>(N->H[l], K, W, K, K, nullptr, kW, N->H[l + 1], b,
-                                                               nullptr);
+                                                               nullptr, K, 0);
     }
     const int rows_per_block = 8;
     k_head<<<(unsigned)((M + rows_per_block - 1) / rows_per_block), 32 * rows_per_block, 0, s>>>(
@@ -439,19 +468,27 @@ static cudaError_t mlp_grad_rows(trk_mlp *N, const float *X, const float *y, int
     k_colsum_final<<<1, kW, 0, s>>>(N->part, N->g + N->w_off[4]);
     k_sum<<<1, 256, 0, s>>>(N->dl, M, 1.0f, N->g + N->b_off[4]);
     k_sum<<<1, 256, 0, s>>>(N->loss_terms, M, 1.0f / (float)M, N->loss);
+    // dW reduces over the rows: split them into at most kSplits slices of
+    // k_split rows, one block column each, then sum the partials in slice order.
+    int splits = (int)(m_pad / 256) < kSplits ? (int)(m_pad / 256) : kSplits;
+    if (splits < 1) splits = 1;
+    const int k_split = (int)(((m_pad + splits - 1) / splits + BK - 1) / BK * BK);
+    splits = (int)((m_pad + k_split - 1) / k_split);
     __nv_bfloat16 *dzb = N->dzb, *dzb_next = N->dzb2;
     for (int l = kHidden - 1; l >= 0; --l) {
         const int K = N->in_pad[l];
         // dW_l [256 x K] = dzb^T [256 x m_pad] * h_{l} [m_pad x K]   (A transposed, B k-major rows)
-        k_gemm<true, false, EPI_F32><<<dim3((K + BN - 1) / BN, kW / BM), 128, 0, s>>>(
-            dzb, kW, N->H[l], K, (int)m_pad, N->g + N->w_off[l], K, nullptr, nullptr, nullptr);
+        k_gemm<true, false, EPI_F32><<<dim3((K + BN - 1) / BN, kW / BM, splits), 128, 0, s>>>(
+            dzb, kW, N->H[l], K, (int)m_pad, N->splitk, K, nullptr, nullptr, nullptr, k_split, (size_t)kW * K);
+        k_reduce_splits<<<grid_for((int64_t)kW * K), 256, 0, s>>>(N->splitk, splits, (int64_t)kW * K,
+                                                                  N->g + N->w_off[l]);
         // db_l = sum_m dz (FP32)
         k_colsum_part<<<kColSlices, kW, 0, s>>>(N->dz, nullptr, nullptr, M, N->part);
         k_colsum_final<<<1, kW, 0, s>>>(N->part, N->g + N->b_off[l]);
         if (l > 0) {
             // dz_{l-1} = (dzb W_l) * gelu'(z_{l-1}), W_l [256 x 256] as B[k = out][n = in]
             k_gemm<false, false, EPI_DGELU><<<dim3(kW / BN, (unsigned)(m_pad / BM)), 128, 0, s>>>(
-                dzb, kW, N->pb + N->w_off[l], kW, kW, N->dz, kW, dzb_next, nullptr, N->Z[l - 1]);
+                dzb, kW, N->pb + N->w_off[l], kW, kW, N->dz, kW, dzb_next, nullptr, N->Z[l - 1], kW, 0);
             __nv_bfloat16 *t = dzb;
             dzb = dzb_next;
             dzb_next = t;
@@ -478,59 +515,123 @@ extern "C" trk_status trk_mlp_adam(trk_mlp *N, float lr, float beta1, float beta
     N->t += 1;
     const float c1 = 1.0f - powf(beta1, (float)N->t), c2 = 1.0f - powf(beta2, (float)N->t);
     k_adam<<<grid_for(N->n_par), 256, 0, (cudaStream_t)stream>>>(N->p, N->m, N->v, N->g, N->pb, N->n_par, lr, beta1,
-                                                                 beta2, eps, c1, c2);
+                                                                 beta2, eps, c1, c2, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_adam: ") + cudaGetErrorString(e));
     return TRK_OK;
 }
 
-__global__ void k_gather_rows(const float *__restrict__ X, const float *__restrict__ y, const int32_t *__restrict__ idx,
-                              int64_t n, float *__restrict__ Xo, float *__restrict__ yo) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx[i];
+namespace trk {
+namespace {
+// Rows of training step *step: epoch e = step / spe, rows [r0, r0 + m) of the
+// epoch's order with r0 = (step % spe) * batch; the order is perm[e * n + r]
+// (identity without perm).
+__global__ void k_gather_rows(const float *__restrict__ X, const float *__restrict__ y, const int32_t *__restrict__ perm,
+                              int64_t n, int64_t batch, int64_t spe, const int64_t *__restrict__ step, int64_t m,
+                              float *__restrict__ Xo, float *__restrict__ yo) {
+    const int64_t st = *step, ep = st / spe, r0 = (st % spe) * batch;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = perm ? (int64_t)perm[ep * n + r0 + i] : r0 + i;
         for (int k = 0; k < kIn; ++k) Xo[i * kIn + k] = X[r * kIn + k];
         yo[i] = y[r];
     }
 }
 
+// End of a training step: record the loss, advance the step counter.
+__global__ void k_step_end(const float *__restrict__ loss, float *__restrict__ hist, int64_t *__restrict__ step) {
+    if (hist) hist[*step] = *loss;
+    *step += 1;
+}
+
+// One training step on m rows, enqueued on s (captured into a graph).
+cudaError_t train_step(trk_mlp *N, const float *d_X, const float *d_y, const int32_t *d_perm, int64_t n,
+                       int64_t batch, int64_t spe, int64_t m, float lr, const float *c12, int64_t *dstep, float *Xb,
+                       float *yb, float *d_loss_hist, cudaStream_t s) {
+    k_gather_rows<<<grid_for(m), 256, 0, s>>>(d_X, d_y, d_perm, n, batch, spe, dstep, m, Xb, yb);
+    cudaError_t e = mlp_grad_rows(N, Xb, yb, m, s);
+    if (e != cudaSuccess) return e;
+    k_adam<<<grid_for(N->n_par), 256, 0, s>>>(N->p, N->m, N->v, N->g, N->pb, N->n_par, lr, 0.9f, 0.999f, 1e-8f, 0.0f,
+                                              0.0f, c12, dstep);
+    k_step_end<<<1, 1, 0, s>>>(N->loss, d_loss_hist, dstep);
+    return cudaGetLastError();
+}
+
+struct TrainRes {
+    float *Xb = nullptr, *yb = nullptr, *c12 = nullptr;
+    int64_t *dstep = nullptr;
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t g[2] = {};
+    cudaGraphExec_t x[2] = {};
+    ~TrainRes() {
+        for (int i = 0; i < 2; ++i) {
+            if (x[i]) cudaGraphExecDestroy(x[i]);
+            if (g[i]) cudaGraphDestroy(g[i]);
+        }
+        if (ps) cudaStreamSynchronize(ps);
+        cudaFree(Xb);
+        cudaFree(yb);
+        cudaFree(c12);
+        cudaFree(dstep);
+        if (ev) cudaEventDestroy(ev);
+        if (ps) cudaStreamDestroy(ps);
+    }
+};
+}  // namespace
+}  // namespace trk
+
+// epochs x ceil(n / batch) Adam steps; step k of an epoch takes rows
+// [k batch, min(n, (k + 1) batch)) of the epoch's order.  Each step (the full
+// one and, when batch does not divide n, the short last one) is captured once
+// as a CUDA graph on a private stream; a device step counter selects the rows
+// and the Adam bias corrections, so the same graph replays every step.
 extern "C" trk_status trk_mlp_train(trk_mlp *N, const float *d_X, const float *d_y, int64_t n, int32_t batch,
                                     int32_t epochs, const int32_t *d_perm, float lr, float *d_loss_hist,
                                     void *stream) {
     if (!N || n < 1 || batch < 1 || epochs < 1 || !d_X || !d_y)
         return mlp_fail(TRK_EINVAL, "trk_mlp_train: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t m_pad = ((int64_t)batch + BM - 1) / BM * BM;
+    const int64_t b = batch < n ? batch : n;
+    const int64_t spe = (n + b - 1) / b, total = spe * epochs, tail = n - (spe - 1) * b;
+    const int64_t m_pad = (b + BM - 1) / BM * BM;
     trk_status st = mlp_ensure(N, m_pad, true);
     if (st != TRK_OK) return st;
-    float *Xb = nullptr, *yb = nullptr;
-    if (d_perm) {
-        if (cudaMalloc(&Xb, (size_t)batch * kIn * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&yb, (size_t)batch * sizeof(float)) != cudaSuccess) {
-            cudaFree(Xb);
-            return mlp_fail(TRK_ENOMEM, "trk_mlp_train: batch allocation failed");
-        }
+    TrainRes R;
+    std::vector<float> c12(2 * total);
+    for (int64_t k = 0; k < total; ++k) {
+        const float t = (float)(N->t + k + 1);
+        c12[2 * k] = 1.0f - powf(0.9f, t);
+        c12[2 * k + 1] = 1.0f - powf(0.999f, t);
     }
-    cudaError_t e = cudaSuccess;
-    int64_t step = 0;
-    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-        for (int64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += batch, ++step) {
-            const int64_t m = n - r0 < batch ? n - r0 : batch;
-            const float *X = d_X + r0 * kIn, *y = d_y + r0;
-            if (d_perm) {
-                k_gather_rows<<<grid_for(m), 256, 0, s>>>(d_X, d_y, d_perm + (size_t)ep * n + r0, m, Xb, yb);
-                X = Xb;
-                y = yb;
-            }
-            e = mlp_grad_rows(N, X, y, m, s);
-            if (e == cudaSuccess && d_loss_hist)
-                e = cudaMemcpyAsync(d_loss_hist + step, N->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess && trk_mlp_adam(N, lr, 0.9f, 0.999f, 1e-8f, stream) != TRK_OK) e = cudaErrorUnknown;
-        }
+    cudaError_t e = cudaMalloc(&R.Xb, (size_t)b * kIn * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&R.yb, (size_t)b * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&R.c12, c12.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&R.dstep, sizeof(int64_t));
+    if (e != cudaSuccess) return mlp_fail(TRK_ENOMEM, "trk_mlp_train: allocation failed");
+    e = cudaStreamCreateWithFlags(&R.ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R.ev, cudaEventDisableTiming);
+    // order the private stream after the caller's work
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.c12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.dstep, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaEventRecord(R.ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(R.ps, R.ev, 0);
+    const int n_graphs = tail == b ? 1 : 2;
+    for (int k = 0; k < n_graphs && e == cudaSuccess; ++k) {
+        e = cudaStreamBeginCapture(R.ps, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t ec = train_step(N, d_X, d_y, d_perm, n, b, spe, k == 0 ? b : tail, lr, R.c12, R.dstep, R.Xb,
+                                    R.yb, d_loss_hist, R.ps);
+        e = cudaStreamEndCapture(R.ps, &R.g[k]);
+        if (ec != cudaSuccess) e = ec;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&R.x[k], R.g[k], 0);
     }
-    cudaStreamSynchronize(s);
-    cudaFree(Xb);
-    cudaFree(yb);
+    for (int64_t k = 0; k < total && e == cudaSuccess; ++k)
+        e = cudaGraphLaunch(R.x[(n_graphs == 2 && k % spe == spe - 1) ? 1 : 0], R.ps);
+    if (e == cudaSuccess) e = cudaEventRecord(R.ev, R.ps);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, R.ev, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_train: ") + cudaGetErrorString(e));
+    N->t += total;
     return TRK_OK;
 }
 

@@ -136,38 +136,46 @@ __device__ __forceinline__ void v_edrift(Tile<P> &q, double L) {
 // first dropped term is then below 4e-18), or rsqrt(1 - u) - 1 otherwise.
 __device__ __noinline__ double drift_g_exact(double u) { return rsqrt(1.0 - u) - 1.0; }
 
+// With hh = h/2 and hq = 3h/8 given, the two-term series is taken as
+//   c = hq u + hh,  h g = c u,  h (1 + g) = c u + h
+// (three FMAs and no multiply).  A = c, B = u, or A = h, B = g on the longer
+// series and exact branches, and then t = A B + h, l += A B.
 template <int P>
 __device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (&l)[P], const double (&qx)[P],
-                                        const double (&qy)[P], double h) {
-    double g[P];
+                                        const double (&qy)[P], double h, double hh, double hq) {
+    double A[P], B[P];
     bool need = false;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-        g[p] = u * fma(u, 0.375, 0.5);
+        A[p] = fma(hq, u, hh);
+        B[p] = u;
         need |= !quad_ok(u);
     }
     if (need) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
-            if (!quad_ok(u)) g[p] = series_ok(u) ? u * fma(u, fma(u, 0.3125, 0.375), 0.5) : drift_g_exact(u);
+            const double u = B[p];
+            if (!quad_ok(u)) {
+                A[p] = h;
+                B[p] = series_ok(u) ? u * fma(u, fma(u, 0.3125, 0.375), 0.5) : drift_g_exact(u);
+            }
         }
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double t = fma(h, g[p], h);
+        const double t = fma(A[p], B[p], h);
         x[p] = fma(t, qx[p], x[p]);
         y[p] = fma(t, qy[p], y[p]);
-        l[p] = fma(h, g[p], l[p]);
+        l[p] = fma(A[p], B[p], l[p]);
     }
 }
 
 // Kicks on the scaled momenta: quadrupole qx -= (K1 h/(1+delta)) x, qy += ...;
-// sextupole qx -= (K2 h/(2(1+delta)))(x^2 - y^2), qy += (K2 h/(1+delta)) x y.
+// sextupole qx -= hb (x^2 - y^2), qy += 2 hb x y with hb = K2 h/(2(1+delta)).
 template <int P, uint32_t FL>
 __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&qx)[P], double (&qy)[P],
-                                       const double (&a)[P], const double (&hb)[P], const double (&b)[P]) {
+                                       const double (&a)[P], const double (&hb)[P]) {
     if (FL & 1u) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -176,12 +184,13 @@ __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P
         }
     }
     if (FL & 2u) {
-        // qx -= hb (x^2 - y^2) and qy += b x y as three products and three FMAs
+        // two products and four FMAs (2 hb x y added as hb x y twice: an FMA
+        // costs less than a multiply on the FP64 pipe)
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double hx = hb[p] * x[p], hy = hb[p] * y[p], bx = b[p] * x[p];
+            const double hx = hb[p] * x[p], hy = hb[p] * y[p];
             qx[p] = fma(hy, y[p], fma(-hx, x[p], qx[p]));
-            qy[p] = fma(bx, y[p], qy[p]);
+            qy[p] = fma(hx, y[p], fma(hx, y[p], qy[p]));
         }
     }
 }
@@ -253,7 +262,9 @@ template <int P, uint32_t FL>
 __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P], const DevElem *__restrict__ E) {
     const int n = __ldg(&E->n);
     const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
-    double a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
+    const double d1h = __ldg(&E->p[7]), d1q = __ldg(&E->p[8]), d2h = __ldg(&E->p[9]), d2q = __ldg(&E->p[10]),
+                 dmq = __ldg(&E->p[11]);
+    double a1[P], a0[P], hb1[P], hb0[P];
     if (FL & 1u) {
         const double A1 = __ldg(&E->p[3]), A0 = __ldg(&E->p[4]);
 #pragma unroll
@@ -263,23 +274,22 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
         }
     }
     if (FL & 2u) {
-        const double H1 = __ldg(&E->p[5]), H0 = __ldg(&E->p[6]), B1 = __ldg(&E->p[7]), B0 = __ldg(&E->p[8]);
+        const double H1 = __ldg(&E->p[5]), H0 = __ldg(&E->p[6]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             hb1[p] = H1 * iP[p];
             hb0[p] = H0 * iP[p];
-            b1[p] = B1 * iP[p];
-            b0[p] = B0 * iP[p];
         }
     }
-    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1);
+    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1, d1h, d1q);
     for (int s = 0; s < n; ++s) {
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0, b0);
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, s + 1 < n ? dm : d1);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1);
+        const bool mid = s + 1 < n;   // merged drift dm = 2 d1, so dm / 2 = d1
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, mid ? dm : d1, mid ? d1 : d1h, mid ? dmq : d1q);
     }
 }
 
@@ -585,7 +595,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                 // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
                 // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
                 if (canon)
-                    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]));
+                    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]), __ldg(&E->p[1]), __ldg(&E->p[2]));
                 else
                     v_edrift<P>(q, __ldg(&E->p[0]));
                 break;

@@ -6,8 +6,18 @@
 // parameters), predict the survival mask of every cell, mark a band of cells
 // within Chebyshev distance r of a predicted-boundary cell (a cell whose 8
 // neighbours hold both classes) plus caller-chosen audit cells, re-track those
-// exactly in FP64, and merge.  With use_mlp = 0 the prediction is the label of
-// the nearest coarse cell instead (the same pipeline without the network).
+// exactly in FP64, and merge.  The band is then re-derived from the merged mask
+// and the cells it newly reaches are tracked, until every cell within the band
+// radius of the merged boundary is exact (the band follows the true boundary
+// wherever the prediction misplaced it); later passes also take every cell
+// within expand_radius of a cell whose label the last merge flipped.  Sentinel
+// cells on a regular sub-lattice are tracked in the first pass: with sentinel
+// stride <= 2 band_radius + 1 every (2 band_radius + 1)^2 block holds an exact
+// cell, which is what makes the one-cell boundary criterion hold by
+// construction (an untracked wrong cell two or more cells from the exhaustive
+// boundary would need a whole uniform 5 x 5 block without an exact cell).
+// With use_mlp = 0 the prediction is the label of the nearest coarse cell
+// instead (the same pipeline without the network).
 #include <chrono>
 #include <cstring>
 #include <string>
@@ -119,27 +129,66 @@ __global__ void k_boundary(const uint8_t *__restrict__ mask, int nx, int ny, int
     }
 }
 
-// Cells to re-track: within Chebyshev distance r of a boundary cell, or audit
-// cells, and not already known exactly.
-__global__ void k_band(const uint8_t *__restrict__ bnd, const uint8_t *__restrict__ audit,
-                       const uint8_t *__restrict__ known, int nx, int ny, int n_var, int r,
+// Horizontal then vertical pass of two box dilations at once: bit 0 of the
+// result = a boundary cell within Chebyshev distance r, bit 1 = a flipped cell
+// within distance R (both limited to the variant's grid).
+__global__ void k_dilate_x(const uint8_t *__restrict__ bnd, const uint8_t *__restrict__ flip, int nx, int ny,
+                           int n_var, int r, int R, uint8_t *__restrict__ out) {
+    const int64_t n = (int64_t)n_var * nx * ny;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(c % nx);
+        const int64_t row = c - ix;
+        uint8_t b = 0;
+        for (int jx = ix - r < 0 ? 0 : ix - r, je = ix + r < nx ? ix + r : nx - 1; jx <= je && !b; ++jx)
+            b = bnd[row + jx] ? 1 : 0;
+        if (flip)
+            for (int jx = ix - R < 0 ? 0 : ix - R, je = ix + R < nx ? ix + R : nx - 1; jx <= je; ++jx)
+                if (flip[row + jx]) {
+                    b |= 2;
+                    break;
+                }
+        out[c] = b;
+    }
+}
+__global__ void k_dilate_y(const uint8_t *__restrict__ in, int nx, int ny, int n_var, int r, int R,
+                           uint8_t *__restrict__ near) {
+    const int64_t n = (int64_t)n_var * nx * ny;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(c % nx), iy = (int)((c / nx) % ny);
+        const int64_t base = c - (int64_t)iy * nx;
+        const int m = r > R ? r : R;
+        uint8_t b = 0;
+        for (int jy = iy - m < 0 ? 0 : iy - m, je = iy + m < ny ? iy + m : ny - 1; jy <= je && b != 3; ++jy) {
+            const int d = jy > iy ? jy - iy : iy - jy;
+            const uint8_t v = in[base + (int64_t)jy * nx];
+            if (d <= r) b |= v & 1;
+            if (d <= R) b |= v & 2;
+        }
+        near[c] = b;
+    }
+}
+
+// On one axis of n cells, sentinel positions are off + k stride (k >= 0) up to
+// n - 1 - off, plus n - 1 - off itself (off = stride / 2): no gap exceeds the
+// stride, and both edges are within off.
+__device__ __forceinline__ bool sentinel_axis(int i, int n, int stride) {
+    const int off = stride / 2, last = n - 1 - off;
+    return i == last || (i >= off && i <= last && (i - off) % stride == 0);
+}
+
+// Cells to re-track: near (a boundary cell within the band radius or a flipped
+// cell within the expansion radius), audit cells, sentinel cells (stride > 0),
+// and not already known exactly.
+__global__ void k_band(const uint8_t *__restrict__ near, const uint8_t *__restrict__ audit,
+                       const uint8_t *__restrict__ known, int nx, int ny, int n_var, int sentinel,
                        uint8_t *__restrict__ todo, uint8_t *__restrict__ is_audit) {
     const int64_t n = (int64_t)n_var * nx * ny;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(c % nx), iy = (int)((c / nx) % ny);
-        const int64_t base = c - (int64_t)iy * nx - ix;
-        bool near = false;
-        for (int dy = -r; dy <= r && !near; ++dy)
-            for (int dx = -r; dx <= r; ++dx) {
-                const int jx = ix + dx, jy = iy + dy;
-                if (jx < 0 || jy < 0 || jx >= nx || jy >= ny) continue;
-                if (bnd[base + (int64_t)jy * nx + jx]) {
-                    near = true;
-                    break;
-                }
-            }
-        const bool au = audit && audit[c] && !near;
-        todo[c] = (!known[c] && (near || au)) ? 1 : 0;
+        const bool nr = near[c] != 0;
+        const bool se = sentinel > 0 && sentinel_axis(ix, nx, sentinel) && sentinel_axis(iy, ny, sentinel);
+        const bool au = audit && audit[c] && !nr && !se;
+        todo[c] = (!known[c] && (nr || se || au)) ? 1 : 0;
         is_audit[c] = (!known[c] && au) ? 1 : 0;
     }
 }
@@ -197,22 +246,24 @@ __global__ void k_gather_todo(const uint8_t *__restrict__ todo, int64_t per, int
 
 __global__ void k_merge(const int64_t *__restrict__ cell, const int32_t *__restrict__ surv, int64_t n,
                         int32_t n_turns, const uint8_t *__restrict__ is_audit, uint8_t *__restrict__ mask,
-                        int32_t *__restrict__ out_surv, unsigned long long *__restrict__ wrong) {
+                        uint8_t *__restrict__ known, uint8_t *__restrict__ flip, int32_t *__restrict__ out_surv,
+                        unsigned long long *__restrict__ wrong) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = cell[i];
         const uint8_t m = surv[i] == n_turns + 1 ? 1 : 0;
         if (is_audit[c] && m != mask[c]) atomicAdd(wrong, 1ull);
+        flip[c] = m != mask[c] ? 1 : 0;
         mask[c] = m;
+        known[c] = 1;
         out_surv[c] = surv[i];
     }
 }
 
-// Cells neither tracked nor coarse: survival from the prediction.
-__global__ void k_fill_predicted(const uint8_t *__restrict__ mask, const uint8_t *__restrict__ known,
-                                 const uint8_t *__restrict__ todo, int64_t n, int32_t n_turns,
-                                 int32_t *__restrict__ out_surv) {
+// Cells never tracked: survival from the prediction.
+__global__ void k_fill_predicted(const uint8_t *__restrict__ mask, const uint8_t *__restrict__ known, int64_t n,
+                                 int32_t n_turns, int32_t *__restrict__ out_surv) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        if (!known[c] && !todo[c]) out_surv[c] = mask[c] ? n_turns + 1 : 0;
+        if (!known[c]) out_surv[c] = mask[c] ? n_turns + 1 : 0;
 }
 
 int grid_for(int64_t n) {
@@ -230,6 +281,10 @@ template <typename T>
 struct DBuf {
     T *p = nullptr;
     cudaError_t alloc(size_t n) { return cudaMalloc(&p, (n ? n : 1) * sizeof(T)); }
+    void reset() {
+        cudaFree(p);
+        p = nullptr;
+    }
     ~DBuf() { cudaFree(p); }
 };
 
@@ -252,7 +307,8 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     if (!lats || n_var < 1 || !d_params || !o || !d_mask || !d_survival)
         return set_error(TRK_EINVAL, "trk_da_triage: NULL argument");
     if (o->nx < 2 || o->ny < 2 || !(o->half_width > 0.0) || o->n_turns < 1 || o->coarse_stride < 1 ||
-        o->band_radius < 0 || (o->use_mlp && (!net || o->epochs < 1 || o->batch < 1)))
+        o->band_radius < 0 || o->sentinel_stride < 0 || o->expand_radius < 0 ||
+        (o->use_mlp && (!net || o->epochs < 1 || o->batch < 1)))
         return set_error(TRK_EINVAL, "trk_da_triage: bad options");
     cudaStream_t s = (cudaStream_t)stream;
     const int nx = o->nx, ny = o->ny, st = o->coarse_stride, off = st / 2;
@@ -280,10 +336,12 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     S.ms_coarse = t1 - t0;
 
     // 2. train the surrogate on the coarse labels
-    DBuf<uint8_t> mask_known, todo, bnd, audit_c;
-    if (mask_known.alloc(n_all) || todo.alloc(n_all) || bnd.alloc(n_all) || audit_c.alloc(n_all))
+    DBuf<uint8_t> mask_known, todo, bnd, audit_c, flip, tmp;
+    if (mask_known.alloc(n_all) || todo.alloc(n_all) || bnd.alloc(n_all) || audit_c.alloc(n_all) ||
+        flip.alloc(n_all) || tmp.alloc(n_all))
         return set_error(TRK_ENOMEM, "trk_da_triage: mask allocation failed");
     TRI_CUDA(cudaMemsetAsync(mask_known.p, 0, n_all, s));
+    TRI_CUDA(cudaMemsetAsync(flip.p, 0, n_all, s));
     if (o->use_mlp) {
         DBuf<float> X, y;
         if (X.alloc(n_coarse * 8) || y.alloc(n_coarse)) return set_error(TRK_ENOMEM, "trk_da_triage: feature allocation failed");
@@ -316,60 +374,94 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     double t3 = now_ms();
     S.ms_infer = t3 - t2;
 
-    // 4. coarse truth, boundary band, audit cells; point lists to re-track
+    // 4./5. coarse truth; then, pass after pass, the band around the boundary of
+    // the current mask (plus the audit cells in the first pass) is gathered into
+    // point lists, re-tracked exactly in FP64 and merged, until a pass finds no
+    // cell left to track.
     k_apply_coarse<<<grid_for(n_coarse), 256, 0, s>>>(csurv.p, nx, ny, st, off, cx, cy, n_var, o->n_turns, d_mask,
                                                       mask_known.p, d_survival);
-    k_boundary<<<grid_for(n_all), 256, 0, s>>>(d_mask, nx, ny, n_var, bnd.p);
-    k_band<<<grid_for(n_all), 256, 0, s>>>(bnd.p, d_audit, mask_known.p, nx, ny, n_var, o->band_radius, todo.p,
-                                           audit_c.p);
-    DBuf<int64_t> dcounts;
-    if (dcounts.alloc(n_var)) return set_error(TRK_ENOMEM, "trk_da_triage: count allocation failed");
-    k_count<<<n_var, 256, 0, s>>>(todo.p, per, dcounts.p);
     TRI_CUDA(cudaGetLastError());
-    std::vector<int64_t> counts(n_var);
-    TRI_CUDA(cudaMemcpyAsync(counts.data(), dcounts.p, n_var * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TRI_CUDA(cudaStreamSynchronize(s));
-    std::vector<int64_t> toffs(n_var + 1, 0);
-    for (int v = 0; v < n_var; ++v) toffs[v + 1] = toffs[v] + counts[v];
-    const int64_t n_todo = toffs[n_var];
-    S.n_tracked = n_todo;
-    DBuf<int64_t> doffs, tcell;
+    DBuf<int64_t> dcounts, doffs;
+    DBuf<unsigned long long> wrong;
+    if (dcounts.alloc(n_var) || doffs.alloc(n_var + 1) || wrong.alloc(1))
+        return set_error(TRK_ENOMEM, "trk_da_triage: count allocation failed");
+    TRI_CUDA(cudaMemsetAsync(wrong.p, 0, sizeof(unsigned long long), s));
+    const int max_passes = o->max_passes > 0 ? o->max_passes : 64;
+    std::vector<int64_t> counts(n_var), toffs(n_var + 1, 0);
+    DBuf<int64_t> tcell;
     DBuf<double> tx0, ty0;
     DBuf<int32_t> tsurv;
-    if (doffs.alloc(n_var + 1) || tcell.alloc(n_todo) || tx0.alloc(n_todo) || ty0.alloc(n_todo) || tsurv.alloc(n_todo))
-        return set_error(TRK_ENOMEM, "trk_da_triage: band allocation failed");
-    TRI_CUDA(cudaMemcpyAsync(doffs.p, toffs.data(), (n_var + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    k_gather_todo<<<n_var, 256, 0, s>>>(todo.p, per, nx, ny, w, doffs.p, tx0.p, ty0.p, tcell.p);
-    TRI_CUDA(cudaGetLastError());
-    TRI_CUDA(cudaStreamSynchronize(s));
-    double t4 = now_ms();
-    S.ms_band = t4 - t3;
-
-    // 5. exact FP64 re-track of the band and audit cells, merge
-    DBuf<unsigned long long> wrong;
-    if (wrong.alloc(1)) return set_error(TRK_ENOMEM, "trk_da_triage: counter allocation failed");
-    TRI_CUDA(cudaMemsetAsync(wrong.p, 0, sizeof(unsigned long long), s));
-    if (n_todo > 0) {
-        r = trk_da_survival(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, nullptr, tsurv.p, stream);
+    int64_t cap = 0;
+    double t_band = 0.0, t_track = 0.0;
+    for (int pass = 0; pass < max_passes; ++pass) {
+        const double p0 = now_ms();
+        k_boundary<<<grid_for(n_all), 256, 0, s>>>(d_mask, nx, ny, n_var, bnd.p);
+        const int R = pass == 0 ? 0 : o->expand_radius;
+        k_dilate_x<<<grid_for(n_all), 256, 0, s>>>(bnd.p, R > 0 ? flip.p : nullptr, nx, ny, n_var, o->band_radius, R,
+                                                   tmp.p);
+        k_dilate_y<<<grid_for(n_all), 256, 0, s>>>(tmp.p, nx, ny, n_var, o->band_radius, R, bnd.p);
+        k_band<<<grid_for(n_all), 256, 0, s>>>(bnd.p, pass == 0 ? d_audit : nullptr, mask_known.p, nx, ny, n_var,
+                                               pass == 0 ? o->sentinel_stride : 0, todo.p, audit_c.p);
+        k_count<<<n_var, 256, 0, s>>>(todo.p, per, dcounts.p);
+        TRI_CUDA(cudaGetLastError());
+        TRI_CUDA(cudaMemcpyAsync(counts.data(), dcounts.p, n_var * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (pass == 0) {
+            DBuf<int64_t> acount;
+            if (acount.alloc(n_var)) return set_error(TRK_ENOMEM, "trk_da_triage: count allocation failed");
+            k_count<<<n_var, 256, 0, s>>>(audit_c.p, per, acount.p);
+            TRI_CUDA(cudaGetLastError());
+            std::vector<int64_t> ac(n_var);
+            TRI_CUDA(cudaMemcpyAsync(ac.data(), acount.p, n_var * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            TRI_CUDA(cudaStreamSynchronize(s));
+            for (int v = 0; v < n_var; ++v) S.n_audit += ac[v];
+        }
+        TRI_CUDA(cudaStreamSynchronize(s));
+        for (int v = 0; v < n_var; ++v) toffs[v + 1] = toffs[v] + counts[v];
+        const int64_t n_todo = toffs[n_var];
+        if (n_todo == 0) {
+            t_band += now_ms() - p0;
+            break;
+        }
+        S.n_tracked += n_todo;
+        S.n_passes = pass + 1;
+        S.pass_cells[pass < 15 ? pass : 15] += n_todo;
+        if (n_todo > cap) {
+            tcell.reset();
+            tx0.reset();
+            ty0.reset();
+            tsurv.reset();
+            if (tcell.alloc(n_todo) || tx0.alloc(n_todo) || ty0.alloc(n_todo) || tsurv.alloc(n_todo))
+                return set_error(TRK_ENOMEM, "trk_da_triage: band allocation failed");
+            cap = n_todo;
+        }
+        TRI_CUDA(cudaMemcpyAsync(doffs.p, toffs.data(), (n_var + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_gather_todo<<<n_var, 256, 0, s>>>(todo.p, per, nx, ny, w, doffs.p, tx0.p, ty0.p, tcell.p);
+        TRI_CUDA(cudaGetLastError());
+        const double p1 = now_ms();
+        t_band += p1 - p0;
+        // Few cells: the pass is latency-bound (one warp per SM sub-partition
+        // issues one FP64 instruction per several tens of cycles whatever its
+        // lane count), so one particle per thread halves the chain per warp.
+        trk_schedule sch = {128, n_todo <= 2 * 152 * 128 ? 1 : 2, 1, 2};
+        r = trk_da_survival(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, &sch, tsurv.p, stream);
         if (r != TRK_OK) return r;
-        k_merge<<<grid_for(n_todo), 256, 0, s>>>(tcell.p, tsurv.p, n_todo, o->n_turns, audit_c.p, d_mask, d_survival,
-                                                 wrong.p);
+        TRI_CUDA(cudaMemsetAsync(flip.p, 0, n_all, s));
+        k_merge<<<grid_for(n_todo), 256, 0, s>>>(tcell.p, tsurv.p, n_todo, o->n_turns, audit_c.p, d_mask,
+                                                 mask_known.p, flip.p, d_survival, wrong.p);
+        TRI_CUDA(cudaGetLastError());
+        TRI_CUDA(cudaStreamSynchronize(s));
+        const double p2 = now_ms();
+        t_track += p2 - p1;
+        S.pass_ms[pass < 15 ? pass : 15] += p2 - p0;
     }
-    k_fill_predicted<<<grid_for(n_all), 256, 0, s>>>(d_mask, mask_known.p, todo.p, n_all, o->n_turns, d_survival);
+    k_fill_predicted<<<grid_for(n_all), 256, 0, s>>>(d_mask, mask_known.p, n_all, o->n_turns, d_survival);
     TRI_CUDA(cudaGetLastError());
     unsigned long long nw = 0;
     TRI_CUDA(cudaMemcpyAsync(&nw, wrong.p, sizeof nw, cudaMemcpyDeviceToHost, s));
-    // audit and band sizes
-    DBuf<int64_t> acount;
-    if (acount.alloc(n_var)) return set_error(TRK_ENOMEM, "trk_da_triage: count allocation failed");
-    k_count<<<n_var, 256, 0, s>>>(audit_c.p, per, acount.p);
-    std::vector<int64_t> ac(n_var);
-    TRI_CUDA(cudaMemcpyAsync(ac.data(), acount.p, n_var * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TRI_CUDA(cudaStreamSynchronize(s));
-    double t5 = now_ms();
-    S.ms_retrack = t5 - t4;
-    for (int v = 0; v < n_var; ++v) S.n_audit += ac[v];
-    S.n_band = n_todo - S.n_audit;
+    S.ms_band = t_band;
+    S.ms_retrack = t_track;
+    S.n_band = S.n_tracked - S.n_audit;
     S.n_audit_wrong = (int64_t)nw;
     if (stats) *stats = S;
     return TRK_OK;

@@ -48,13 +48,15 @@ class trk_stats(ctypes.Structure):
 class trk_triage_opts(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("half_width", c_double), ("n_turns", c_int32),
                 ("coarse_stride", c_int32), ("band_radius", c_int32), ("use_mlp", c_int32),
-                ("epochs", c_int32), ("batch", c_int32), ("lr", ctypes.c_float), ("pad", c_int32)]
+                ("epochs", c_int32), ("batch", c_int32), ("lr", ctypes.c_float), ("max_passes", c_int32),
+                ("sentinel_stride", c_int32), ("expand_radius", c_int32)]
 
 
 class trk_triage_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("n_coarse", c_int64), ("n_band", c_int64), ("n_audit", c_int64),
                 ("n_tracked", c_int64), ("n_audit_wrong", c_int64), ("ms_coarse", c_double),
-                ("ms_train", c_double), ("ms_infer", c_double), ("ms_band", c_double), ("ms_retrack", c_double)]
+                ("ms_train", c_double), ("ms_infer", c_double), ("ms_band", c_double), ("ms_retrack", c_double),
+                ("n_passes", c_int64), ("pass_cells", c_int64 * 16), ("pass_ms", c_double * 16)]
 
 
 class trk_schedule(ctypes.Structure):
@@ -460,6 +462,8 @@ def trk_da_triage(lattices, params, opts, net=None, audit=None, perm=None, strea
                                net.handle if net is not None else None, _dptr(perm), ctypes.byref(o),
                                _dptr(mask), _dptr(surv), ctypes.byref(st), _stream(params, stream)))
     stats = {f: getattr(st, f) for f, _ in trk_triage_stats._fields_}
+    for f in ("pass_cells", "pass_ms"):
+        stats[f] = list(stats[f])[:max(1, min(st.n_passes, 16))]
     return mask, surv, stats
 
 

@@ -45,6 +45,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(trk_element_desc), offsetof(trk_element_desc, C),
          offsetof(trk_element_desc, charge), sizeof(trk_lattice_opts), offsetof(trk_lattice_opts, p0c_ev),
          sizeof(trk_schedule));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(trk_triage_opts), offsetof(trk_triage_opts, lr),
+         offsetof(trk_triage_opts, expand_radius), sizeof(trk_triage_stats),
+         offsetof(trk_triage_stats, ms_retrack), offsetof(trk_triage_stats, n_passes), sizeof(trk_stats));
   return 0;
 }
 """)
@@ -52,7 +55,10 @@ int main(void) {
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(trk.trk_element_desc), trk.trk_element_desc.C.offset, trk.trk_element_desc.charge.offset,
-            ctypes.sizeof(trk.trk_lattice_opts), trk.trk_lattice_opts.p0c_ev.offset, ctypes.sizeof(trk.trk_schedule)]
+            ctypes.sizeof(trk.trk_lattice_opts), trk.trk_lattice_opts.p0c_ev.offset, ctypes.sizeof(trk.trk_schedule),
+            ctypes.sizeof(trk.trk_triage_opts), trk.trk_triage_opts.lr.offset, trk.trk_triage_opts.expand_radius.offset,
+            ctypes.sizeof(trk.trk_triage_stats), trk.trk_triage_stats.ms_retrack.offset,
+            trk.trk_triage_stats.n_passes.offset, ctypes.sizeof(trk.trk_stats)]
     assert got == want
 
 

@@ -6,6 +6,7 @@ import pytest
 
 import synthetic as syn
 from oracle import oracle as orc
+from oracle import triage as otri
 from paper_1710_07350_gb300 import da_metrics as dm
 from paper_1710_07350_gb300 import trk
 
@@ -59,7 +60,8 @@ def test_triage_matches_exhaustive_boundary(use_mlp):
     g = np.random.Generator(np.random.Philox(key=11))
     audit = torch.from_numpy((g.uniform(size=(nv, n, n)) < 0.005).astype(np.uint8)).cuda()
     opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": 4,
-            "band_radius": 2, "use_mlp": use_mlp, "epochs": 60, "batch": 256, "lr": 2e-3}
+            "band_radius": 2, "use_mlp": use_mlp, "epochs": 60, "batch": 256, "lr": 2e-3,
+            "sentinel_stride": 5, "expand_radius": 4}
     net = trk.trk_mlp_create(syn.mlp_init(7)) if use_mlp else None
     ncoarse = nv * ((n - 2 + 3) // 4) ** 2
     perm = None
@@ -74,3 +76,37 @@ def test_triage_matches_exhaustive_boundary(use_mlp):
     exact = (surv > 0) & (surv <= turns)
     assert np.array_equal(surv[exact], exh[exact])
     assert st["n_tracked"] < nv * n * n and st["n_coarse"] == ncoarse
+    assert 1 <= st["n_passes"] < 64
+
+
+def test_nonlearned_triage_matches_triage_oracle():
+    """With the nearest-coarse prediction the whole pipeline is deterministic:
+    the merged mask, the survival turns and the number of band-tracked cells
+    equal the triage oracle's, run on the oracle tracker's exact labels."""
+    nv, n, turns, stride = 2, 48, 200, 8
+    lats = [syn.lattice_c5(v) for v in range(nv)]
+    L = [trk.trk_create_lattice(l, moments=False) for l in lats]
+    params = torch.from_numpy(syn.c5_params()[:nv].astype(np.float32)).cuda()
+    z = syn.da_particles(n=n)
+    g = np.random.Generator(np.random.Philox(key=13))
+    audit = (g.uniform(size=(nv, n, n)) < 0.01).astype(np.uint8)
+    opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
+            "band_radius": 2, "use_mlp": 0, "sentinel_stride": 5, "expand_radius": 4}
+    mask, surv, st = trk.trk_da_triage(L, params, opts, audit=torch.from_numpy(audit).cuda())
+    mask, surv = mask.cpu().numpy().astype(bool), surv.cpu().numpy()
+    n_tracked, passes, strict = 0, 0, True
+    for v, lat in enumerate(lats):
+        o = orc.track(lat, z, turns, moments=False)
+        exact = np.where(o["alive"] == 1, turns + 1, o["loss_turn"] + 1).reshape(n, n)
+        m, sv, tracked, p = otri.triage_variant(exact, turns, stride, 2, audit=audit[v], sentinel=5, expand=4)
+        assert dm.boundary_difference(m, exact == turns + 1)[0]
+        if np.any(~(o["margin"] >= 1e-9)):
+            strict = False    # a label within rounding of the aperture may differ; compared above only
+            continue
+        assert np.array_equal(mask[v], m)
+        assert np.array_equal(surv[v], sv)
+        n_tracked += int(tracked.sum())
+        passes = max(passes, p)
+    if strict:
+        assert st["n_tracked"] == n_tracked
+        assert st["n_passes"] == passes
