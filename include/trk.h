@@ -344,6 +344,14 @@ trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t reset);
 trk_status trk_wake_static(double *d_coords, int64_t pitch, int64_t n, int32_t nbins, double w0, double sc,
                            double charge, double p0c_ev, uint32_t *d_hist, double *d_volt, void *stream);
 
+/* Measured FP64 issue rates of the current device (no counterpart in the
+ * paper; the measured denominator beside the derived FP64 peak of a roofline).
+ * out[0], out[1], out[2] (host) receive thread-level DFMA, DMUL and DADD
+ * operations per second of a kernel with 4 blocks of 256 threads per SM, each
+ * thread running 8 independent dependent chains.  Allocates a small scratch
+ * array, launches on `stream` and synchronises it. */
+trk_status trk_probe_fp64(double *out, void *stream);
+
 /* Text for the calling thread's last non-OK status ("" if none). */
 const char *trk_last_error(void);
 

@@ -61,42 +61,51 @@ __device__ __noinline__ bool ellipse_exact(double x, double y, double a, double 
 
 // ---------------------------------------------------------------- map ----
 // x_i <- C_i + R x + T x x + U x x x from the input vector (simultaneous).
+// The six rows are independent sums; they are stepped through together (term k
+// of every row that has one, then term k + 1), so that their FMA chains
+// interleave and one particle's latency is the longest row, not the sum of all
+// rows (which is what bounds a lightly occupied GPU).
 template <int P>
 __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E, const DevTerm *__restrict__ terms,
                                       bool &dirty) {
-    const Tile<P> in = q;
     const uint32_t flags = __ldg(&E->flags);
     const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
     const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
     const double2 *t = reinterpret_cast<const double2 *>(terms + __ldg(&E->term0));
+    double acc[6][P];
+    int len[6], n = 0;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-        double acc[P];
+        len[r] = rb[r + 1] - rb[r];
+        n = len[r] > n ? len[r] : n;
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[p] = ((flags >> r) & 1u) ? tget(in, p, r) : 0.0;
-        const int kb = rb[r], ke = rb[r + 1];
-        for (int k = kb; k < ke; ++k) {
-            const double2 tv = __ldg(t + k);
+        for (int p = 0; p < P; ++p) acc[r][p] = ((flags >> r) & 1u) ? tget(q, p, r) : 0.0;
+    }
+    for (int k = 0; k < n; ++k) {
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            if (k >= len[r]) continue;
+            const double2 tv = __ldg(t + rb[r] + k);
             const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
             const int deg = code & 3, j = (code >> 2) & 7, jk = (code >> 5) & 7, jl = (code >> 8) & 7;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 double m = 1.0;
-                if (deg >= 1) m = tget(in, p, j);
-                if (deg >= 2) m *= tget(in, p, jk);
-                if (deg >= 3) m *= tget(in, p, jl);
-                acc[p] = fma(tv.x, m, acc[p]);
+                if (deg >= 1) m = tget(q, p, j);
+                if (deg >= 2) m *= tget(q, p, jk);
+                if (deg >= 3) m *= tget(q, p, jl);
+                acc[r][p] = fma(tv.x, m, acc[r][p]);
             }
         }
+    }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            if (r == 0) q.x[p] = acc[p];
-            if (r == 1) q.xp[p] = acc[p];
-            if (r == 2) q.y[p] = acc[p];
-            if (r == 3) q.yp[p] = acc[p];
-            if (r == 4) q.l[p] = acc[p];
-            if (r == 5) q.d[p] = acc[p];
-        }
+    for (int p = 0; p < P; ++p) {
+        q.x[p] = acc[0][p];
+        q.xp[p] = acc[1][p];
+        q.y[p] = acc[2][p];
+        q.yp[p] = acc[3][p];
+        q.l[p] = acc[4][p];
+        q.d[p] = acc[5][p];
     }
     if (flags & 64u) dirty = true;
 }
@@ -172,10 +181,10 @@ __device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (
 }
 
 // Kicks on the scaled momenta: quadrupole qx -= (K1 h/(1+delta)) x, qy += ...;
-// sextupole qx -= hb (x^2 - y^2), qy += 2 hb x y with hb = K2 h/(2(1+delta)).
+// sextupole qx -= hb (x^2 - y^2), qy += b x y with hb = K2 h/(2(1+delta)), b = 2 hb.
 template <int P, uint32_t FL>
 __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&qx)[P], double (&qy)[P],
-                                       const double (&a)[P], const double (&hb)[P]) {
+                                       const double (&a)[P], const double (&hb)[P], const double (&b)[P]) {
     if (FL & 1u) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -184,13 +193,12 @@ __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P
         }
     }
     if (FL & 2u) {
-        // two products and four FMAs (2 hb x y added as hb x y twice: an FMA
-        // costs less than a multiply on the FP64 pipe)
+        // two products and three FMAs: w = x^2 - y^2 = fma(x, x, -y^2)
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double hx = hb[p] * x[p], hy = hb[p] * y[p];
-            qx[p] = fma(hy, y[p], fma(-hx, x[p], qx[p]));
-            qy[p] = fma(hx, y[p], fma(hx, y[p], qy[p]));
+            const double w = fma(x[p], x[p], -(y[p] * y[p]));
+            qx[p] = fma(-hb[p], w, qx[p]);
+            qy[p] = fma(b[p] * y[p], x[p], qy[p]);
         }
     }
 }
@@ -264,7 +272,7 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
     const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
     const double d1h = __ldg(&E->p[7]), d1q = __ldg(&E->p[8]), d2h = __ldg(&E->p[9]), d2q = __ldg(&E->p[10]),
                  dmq = __ldg(&E->p[11]);
-    double a1[P], a0[P], hb1[P], hb0[P];
+    double a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
     if (FL & 1u) {
         const double A1 = __ldg(&E->p[3]), A0 = __ldg(&E->p[4]);
 #pragma unroll
@@ -279,15 +287,17 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
         for (int p = 0; p < P; ++p) {
             hb1[p] = H1 * iP[p];
             hb0[p] = H0 * iP[p];
+            b1[p] = hb1[p] + hb1[p];
+            b0[p] = hb0[p] + hb0[p];
         }
     }
     v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1, d1h, d1q);
     for (int s = 0; s < n; ++s) {
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
         v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0, b0);
         v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
         const bool mid = s + 1 < n;   // merged drift dm = 2 d1, so dm / 2 = d1
         v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, mid ? dm : d1, mid ? d1 : d1h, mid ? dmq : d1q);
     }
@@ -582,9 +592,11 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             dirty = true;
             apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here, canon);
         }
+        int type_next = a.e0 < a.e1 ? __ldg(&elems[a.e0].type) : 0;
         for (int e = a.e0; e < a.e1; ++e) {
             const DevElem *E = elems + e;
-            const int type = __ldg(&E->type);
+            const int type = type_next;   // loaded one element ahead
+            if (e + 1 < a.e1) type_next = __ldg(&elems[e + 1].type);
             if (canon && type != TRK_EDRIFT && type != TRK_KQUAD && type != TRK_KSEXT) {
                 v_to_slopes<P>(q);
                 canon = false;

@@ -109,6 +109,7 @@ def lib():
             "trk_da_triage": [P, c_int32, P, P, P, P, P, P, P, P, P],
             "trk_bunch_stats": [P, P, c_int32],
             "trk_wake_static": [P, c_int64, c_int64, c_int32, c_double, c_double, c_double, c_double, P, P, P],
+            "trk_probe_fp64": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -484,6 +485,17 @@ def trk_wake_static(coords, n, nbins, w0, sc, charge, p0c, hist=None, volt=None,
         stream = torch.cuda.current_stream(coords.device)
     _check(lib().trk_wake_static(_dptr(coords), coords.shape[1], n, nbins, w0, sc, charge, p0c,
                                  _dptr(hist), _dptr(volt), c_void_p(stream.cuda_stream)))
+
+
+def trk_probe_fp64(stream=None):
+    """Measured FP64 rates of the current device: (DFMA, DMUL, DADD) thread
+    operations per second."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = (c_double * 3)()
+    _check(lib().trk_probe_fp64(out, c_void_p(stream.cuda_stream)))
+    return tuple(out)
 
 
 def download(b):

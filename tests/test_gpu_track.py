@@ -6,6 +6,7 @@ import pytest
 
 import synthetic as syn
 from oracle import oracle as orc
+from paper_1710_07350_gb300 import trk
 
 from gpu_util import (MARGIN, TOL_100, TOL_PASS, by_id, compare_moments, compare_tracking, gpu_track,
                       reduction_check)
@@ -177,3 +178,13 @@ def test_order3_maps_ring():
     err = compare_tracking(g, o, TOL_100)
     compare_moments(g["moments"], o["moments"], coord_err=err)
     reduction_check(g)
+
+
+def test_fp64_probe_rates_are_plausible():
+    """The measured DFMA rate backs the derived FP64 peak of the roofline:
+    152 SMs x 2 lanes x 2.07 GHz = 6.3e11 FMA/s at most, and a working
+    device reaches a large part of it."""
+    fma_rate, mul_rate, add_rate = trk.trk_probe_fp64()
+    assert 2e11 < fma_rate < 7e11
+    assert 0.3 * fma_rate < mul_rate <= 1.05 * fma_rate
+    assert 0.3 * fma_rate < add_rate <= 1.05 * fma_rate
