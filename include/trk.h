@@ -233,7 +233,9 @@ trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const 
  * tensor-core products (mma.sync, FP32 accumulation); BCE loss on the logit;
  * Adam (Kingma & Ba).  Rounding points: h0 = bf16(x), z = h W^T + b (FP32),
  * h = bf16(gelu(z)); dz = dh * gelu'(z) (FP32) rounded to BF16 for dW = dz^T h
- * and dh = dz W; db = sum dz (FP32).
+ * and dh = dz W; db = sum dz (FP32).  Inference (trk_mlp_forward) runs its
+ * hidden layers on tcgen05 (128 x 256 tiles, FP32 accumulators in tensor
+ * memory); training on mma.sync; the rounding points are the same.
  *   W[l], b[l]   HOST FP32 arrays, W[l] row-major [out][in]: l = 0: 256 x 8,
  *                l = 1..3: 256 x 256, l = 4: 1 x 256; b[l] [out]
  *   d_X          device FP32 [M][8] inputs; d_y device FP32 [M] labels (0/1)
@@ -244,8 +246,10 @@ trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const 
  * per epoch, or NULL for the stored order; d_loss_hist: device FP32, one
  * entry per step, or NULL).  trk_mlp_get copies weights, biases and the last
  * gradients to host arrays of the layout above (NULL entries skipped) and
- * synchronises.  All calls are asynchronous on `stream` except trk_mlp_get and
- * trk_mlp_train (which synchronises at the end). */
+ * synchronises.  All calls are asynchronous on `stream` except trk_mlp_get,
+ * trk_mlp_train and trk_mlp_forward, which synchronise at the end
+ * (trk_mlp_forward returns TRK_ETIMEOUT if a tensor-core layer gave up a
+ * bounded wait). */
 typedef struct trk_mlp trk_mlp;
 trk_status trk_mlp_create(const float *const *W, const float *const *b, trk_mlp **out);
 trk_status trk_mlp_destroy(trk_mlp *net);

@@ -123,6 +123,14 @@ cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins
                              cudaStream_t s);
 
 // Dynamic-aperture helpers (trk_da.cu).
+// tcgen05 surrogate inference layers (trk_mlp_umma.cu); BF16 passed as uint16_t.
+size_t umma_layer_smem(int K);
+cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, const float *bias, int K,
+                              int64_t n_tiles, uint16_t *out_tiled, int *d_err, cudaStream_t s);
+cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s);
+cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s);
+cudaError_t launch_head_tiled(const uint16_t *H4, const uint16_t *w5, const float *b5, int64_t M, float *logit,
+                              cudaStream_t s);
 cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0,
                            int64_t first, int64_t n, cudaStream_t s);
 cudaError_t launch_da_survival(const int32_t *ids, const int32_t *lt, int64_t n, int32_t n_turns, int32_t *survival,

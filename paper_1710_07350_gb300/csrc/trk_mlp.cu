@@ -296,6 +296,11 @@ struct trk_mlp {
     float *logit = nullptr, *dl = nullptr, *loss_terms = nullptr, *loss = nullptr;
     float *part = nullptr;                                         // column-sum partials
     float *splitk = nullptr;                                       // split-K partials of dW [kSplits][256][256]
+    uint16_t *wt = nullptr;                                        // BF16 weights of layers 0..3, tcgen05 tiled layout
+    size_t wt_off[kHidden] = {};
+    uint16_t *act[2] = {nullptr, nullptr};                         // tiled activations for inference (ping-pong)
+    int64_t act_rows = 0;
+    int *d_err = nullptr;                                          // device error flag of the tcgen05 layers
     int64_t t = 0;                                                 // Adam step
 };
 
@@ -377,6 +382,16 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
     if (e == cudaSuccess) e = cudaMalloc(&N->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->part, kColSlices * kW * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->splitk, (size_t)kSplits * kW * kW * sizeof(float));
+    {
+        size_t o = 0;
+        for (int l = 0; l < kHidden; ++l) {
+            N->wt_off[l] = o;
+            o += (size_t)kW * N->in_pad[l];
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&N->wt, o * sizeof(uint16_t));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&N->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(N->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(N->p, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(N->m, 0, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(N->v, 0, off * sizeof(float));
@@ -394,6 +409,8 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
         cudaFree(N->loss);
         cudaFree(N->part);
         cudaFree(N->splitk);
+        cudaFree(N->wt);
+        cudaFree(N->d_err);
         delete N;
         return mlp_fail(TRK_ENOMEM, std::string("trk_mlp_create: ") + cudaGetErrorString(e));
     }
@@ -413,6 +430,10 @@ extern "C" trk_status trk_mlp_destroy(trk_mlp *N) {
     cudaFree(N->loss);
     cudaFree(N->part);
     cudaFree(N->splitk);
+    cudaFree(N->wt);
+    cudaFree(N->d_err);
+    cudaFree(N->act[0]);
+    cudaFree(N->act[1]);
     delete N;
     return TRK_OK;
 }
@@ -439,19 +460,45 @@ static cudaError_t mlp_forward_rows(trk_mlp *N, const float *X, int64_t M, int64
     return cudaGetLastError();
 }
 
+// Inference on the tcgen05 layers: inputs and activations in the tiled layout
+// of trk_mlp_umma.cu, 2^18-row chunks (a multiple of the 128-row tile).
 extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, float *d_logits, void *stream) {
     if (!N || M < 0 || (M > 0 && (!d_X || !d_logits))) return mlp_fail(TRK_EINVAL, "trk_mlp_forward: bad argument");
+    if (M == 0) return TRK_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t chunk = 1 << 18;
-    trk_status st = mlp_ensure(N, chunk, false);
-    if (st != TRK_OK) return st;
-    for (int64_t r0 = 0; r0 < M; r0 += chunk) {
+    const int64_t rows = M < chunk ? (M + 127) / 128 * 128 : chunk;
+    cudaError_t e = cudaSuccess;
+    if (rows > N->act_rows) {
+        cudaFree(N->act[0]);
+        cudaFree(N->act[1]);
+        N->act[0] = N->act[1] = nullptr;
+        N->act_rows = 0;
+        e = cudaMalloc(&N->act[0], (size_t)rows * kW * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&N->act[1], (size_t)rows * kW * sizeof(uint16_t));
+        if (e != cudaSuccess) return mlp_fail(TRK_ENOMEM, "trk_mlp_forward: activation allocation failed");
+        N->act_rows = rows;
+    }
+    const uint16_t *pb = reinterpret_cast<const uint16_t *>(N->pb);
+    for (int l = 0; l < kHidden && e == cudaSuccess; ++l)
+        e = launch_to_tiled(pb + N->w_off[l], kW, N->in_pad[l], kW, N->wt + N->wt_off[l], s);
+    for (int64_t r0 = 0; r0 < M && e == cudaSuccess; r0 += chunk) {
         const int64_t m = M - r0 < chunk ? M - r0 : chunk;
-        const int64_t m_pad = (m + BM - 1) / BM * BM;
-        cudaError_t e = mlp_forward_rows(N, d_X + r0 * kIn, m, m_pad, false, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_logits + r0, N->logit, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_forward: ") + cudaGetErrorString(e));
+        const int64_t m_pad = (m + 127) / 128 * 128;
+        e = launch_input_tiled(d_X + r0 * kIn, m, m_pad, N->act[0], s);
+        int cur = 0;
+        for (int l = 0; l < kHidden && e == cudaSuccess; ++l, cur ^= 1)
+            e = launch_umma_layer(N->act[cur], N->wt + N->wt_off[l], N->p + N->b_off[l], N->in_pad[l], m_pad / 128,
+                                  N->act[cur ^ 1], N->d_err, s);
+        if (e == cudaSuccess) e = launch_head_tiled(N->act[cur], pb + N->w_off[4], N->p + N->b_off[4], m, d_logits + r0, s);
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, N->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_forward: ") + cudaGetErrorString(e));
+    if (herr) {
+        cudaMemsetAsync(N->d_err, 0, sizeof(int), s);
+        return mlp_fail(TRK_ETIMEOUT, "trk_mlp_forward: a tensor-core layer gave up waiting on a barrier");
     }
     return TRK_OK;
 }
