@@ -221,11 +221,23 @@ trk_status trk_track_batch(trk_bunch *const *bunches, const trk_lattice *const *
  * d_survival[p] (int32, device) receives the 1-based turn in which particle p
  * was lost, or n_turns + 1 if it survived.  offsets is a HOST array of n_var+1
  * entries starting at 0.  sched = NULL uses block 128, 2 particles per thread,
- * chunks of 1, 2, 4, ... 128 turns.  Allocates its particle arrays and
- * synchronises the stream before returning. */
+ * chunks of 1, 2, 4, ... 128 turns, or, for at most 16384 points on lattices of
+ * MAP, EDRIFT and THINSEXT elements, trk_da_survival_lanes.  Allocates its
+ * particle arrays and synchronises the stream before returning. */
 trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
                            const double *d_x0, const double *d_y0, int32_t n_turns, const trk_schedule *sched,
                            int32_t *d_survival, void *stream);
+
+/* The same survival turns (bit-identical) for few points: each particle gets 8
+ * GPU lanes, lane r holding coordinate r, so the rows of a map are evaluated in
+ * parallel and one particle's chain of dependent operations per turn is
+ * shorter; one launch covers all n_turns turns, lost particles stop at once.
+ * Lattices may hold MAP, EDRIFT and THINSEXT elements only (TRK_EUNSUPPORTED
+ * otherwise); at most 2^28 points.  Arguments as trk_da_survival.
+ * Synchronises the stream before returning. */
+trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
+                                 const double *d_x0, const double *d_y0, int32_t n_turns, int32_t *d_survival,
+                                 void *stream);
 
 /* MLP surrogate for dynamic-aperture triage (no counterpart in the paper).
  * Fixed architecture 8 -> 4 x [Linear 256 + GELU(erf)] -> Linear 256 -> 1 logit.
@@ -263,13 +275,15 @@ trk_status trk_mlp_get(trk_mlp *net, float *const *W, float *const *b, float *co
 /* Surrogate-triaged dynamic-aperture scan (no counterpart in the paper).  For
  * every variant v and cell (ix, iy) of an nx x ny grid (cell centres
  * -w + (i + 1/2) 2w/n, w = half_width):
- *   1. the coarse cells (every coarse_stride-th cell from stride/2) are tracked
- *      exactly (trk_da_survival);
- *   2. use_mlp = 1: the network is trained on them (features x/w, y/w and the
+ *   1. the coarse cells (every coarse_stride-th cell from stride/2) and the
+ *      sentinel cells (sentinel_stride below) are tracked exactly in one scan
+ *      (trk_da_survival);
+ *   2. use_mlp = 1: the network is trained on the coarse cells (features x/w, y/w and the
  *      variant's 6 normalised parameters d_params[v][6]; label = survives all
  *      n_turns) with trk_mlp_train(epochs, batch, lr, d_perm) and predicts every
  *      cell (logit > 0 = survives); use_mlp = 0: every cell takes the label of
- *      its nearest coarse cell;
+ *      its nearest known cell (the nearest coarse cell, or the nearest sentinel
+ *      cell where that is strictly closer); the known labels override either;
  *   3. cells within Chebyshev distance band_radius of a predicted-boundary cell
  *      (8-neighbourhood holding both classes), and the caller's audit cells
  *      (d_audit[v][iy][ix] != 0, optional), are re-tracked exactly in FP64 and
@@ -293,8 +307,8 @@ typedef struct {
     int32_t epochs, batch;
     float lr;
     int32_t max_passes;       /* band passes at most (0: 64) */
-    int32_t sentinel_stride;  /* > 0: also track, in the first pass, the cells of a
-                               * sub-lattice with this stride on both axes (from
+    int32_t sentinel_stride;  /* > 0: also track, with the coarse cells, the cells of
+                               * a sub-lattice with this stride on both axes (from
                                * stride/2, plus the cell stride/2 from the far edge);
                                * <= 2 band_radius + 1 makes the one-cell boundary
                                * criterion hold by construction; 0: none */
@@ -308,6 +322,7 @@ typedef struct {
     int64_t n_passes;     /* band passes that tracked at least one cell */
     int64_t pass_cells[16];  /* cells tracked in pass k (passes past 15 add to [15]) */
     double pass_ms[16];      /* wall time of pass k: band, gather, track, merge */
+    int64_t n_sentinel;      /* sentinel cells tracked with the coarse cells */
 } trk_triage_stats;
 trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_var, const float *d_params,
                          const uint8_t *d_audit, trk_mlp *net, const int32_t *d_perm, const trk_triage_opts *opts,

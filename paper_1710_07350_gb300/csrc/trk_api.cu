@@ -890,6 +890,49 @@ extern "C" trk_status trk_track_batch(trk_bunch *const *bunches, const trk_latti
 
 // ----------------------------------------------------- dynamic aperture ----
 
+// Below this many points a scan is bound by one particle's latency: 8 lanes per
+// particle (k_da_lanes) then finish sooner than the batched tracker.
+constexpr int64_t kLanePoints = 16384;
+
+static bool lane_capable(const trk_lattice *L) {
+    for (const DevElem &E : L->elems)
+        if (E.type != TRK_MAP && E.type != TRK_EDRIFT && E.type != TRK_THINSEXT) return false;
+    return true;
+}
+
+extern "C" trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
+                                            const double *d_x0, const double *d_y0, int32_t n_turns,
+                                            int32_t *d_survival, void *stream) {
+    if (n_var < 1 || !lats || !offsets) return fail(TRK_EINVAL, "trk_da_survival_lanes: need n_var >= 1, lattices, offsets");
+    if (n_turns < 1) return fail(TRK_EINVAL, "trk_da_survival_lanes: n_turns must be >= 1");
+    if (offsets[0] != 0) return fail(TRK_EINVAL, "trk_da_survival_lanes: offsets[0] must be 0");
+    for (int v = 0; v < n_var; ++v) {
+        if (!lats[v]) return fail(TRK_EINVAL, "trk_da_survival_lanes: NULL lattice");
+        if (offsets[v + 1] < offsets[v]) return fail(TRK_EINVAL, "trk_da_survival_lanes: offsets must be non-decreasing");
+        if (!lane_capable(lats[v]))
+            return fail(TRK_EUNSUPPORTED, "trk_da_survival_lanes: lattices may hold MAP, EDRIFT and THINSEXT only");
+    }
+    const int64_t total = offsets[n_var];
+    if (total == 0) return TRK_OK;
+    if (total > ((int64_t)1 << 28)) return fail(TRK_EINVAL, "trk_da_survival_lanes: more than 2^28 points");
+    if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival_lanes: NULL point or output array");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<LatticeView> hv(n_var);
+    for (int v = 0; v < n_var; ++v) hv[v] = lats[v]->view;
+    LatticeView *dv = nullptr;
+    int64_t *doff = nullptr;
+    cudaError_t e = cudaMalloc(&dv, n_var * sizeof(LatticeView));
+    if (e == cudaSuccess) e = cudaMalloc(&doff, (n_var + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, hv.data(), n_var * sizeof(LatticeView), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offsets, (n_var + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_da_lanes(dv, n_var, doff, d_x0, d_y0, total, n_turns, d_survival, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dv);
+    cudaFree(doff);
+    if (e != cudaSuccess) return fail(TRK_ECUDA, std::string("trk_da_survival_lanes: ") + cudaGetErrorString(e));
+    return TRK_OK;
+}
+
 extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
                                       const double *d_x0, const double *d_y0, int32_t n_turns,
                                       const trk_schedule *sched, int32_t *d_survival, void *stream) {
@@ -902,6 +945,11 @@ extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_
     const int64_t total = offsets[n_var];
     if (total == 0) return TRK_OK;
     if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival: NULL point or output array");
+    if (!sched && total <= kLanePoints) {
+        bool ok = true;
+        for (int v = 0; v < n_var && ok; ++v) ok = lats[v] && lane_capable(lats[v]);
+        if (ok) return trk_da_survival_lanes(lats, n_var, offsets, d_x0, d_y0, n_turns, d_survival, stream);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // each variant's slice starts on a 32-byte boundary of the particle arrays
     std::vector<int64_t> slot(n_var + 1, 0);

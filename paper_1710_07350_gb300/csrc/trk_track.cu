@@ -9,24 +9,15 @@
 // the slope/canonical conversions are replaced, for the small arguments that
 // occur in practice, by truncated binomial series that agree with the exact
 // expressions to FP64 rounding (the exact path runs otherwise); aperture tests
-// run on integer bit patterns or an FP32 pre-filter with an FP64 fallback near
-// the edge, so they cost no FP64 instructions.
+// compare integer bit patterns (the ellipse takes its exact FP64 test only
+// outside an inner box), so they cost almost no FP64 instructions.
 #include <cmath>
 
+#include "trk_device.cuh"
 #include "trk_internal.cuh"
 
 namespace trk {
 namespace {
-
-// Series are used below 2^-14: the first dropped binomial term is then below
-// 4e-18 relative.  v >= 0 (a sum of squares) or NaN, so the test is an integer
-// compare of the high word (NaN fails it and takes the exact branch).
-constexpr int kSeriesMaxHi = 0x3F100000;  // high word of 2^-14
-// Below 2^-19 the cubic terms of the series are also below 2e-18 and dropped.
-constexpr int kQuadMaxHi = 0x3EC00000;    // high word of 2^-19
-
-__device__ __forceinline__ bool series_ok(double v) { return __double2hiint(v) < kSeriesMaxHi; }
-__device__ __forceinline__ bool quad_ok(double v) { return __double2hiint(v) < kQuadMaxHi; }
 
 // The P particles a thread owns, advanced in lock-step through every element so
 // that their independent FP64 chains interleave (the pipe's latency is long
@@ -45,18 +36,6 @@ __device__ __forceinline__ double tget(const Tile<P> &q, int p, int j) {
     r = (j == 4) ? q.l[p] : r;
     r = (j == 5) ? q.d[p] : r;
     return r;
-}
-
-// Exact fallbacks for arguments outside the series range.  They are kept out of
-// line so that the compiler cannot if-convert them into the hot path (where they
-// would execute for every particle); they run only when a particle needs them.
-__device__ __noinline__ double rsqrt_exact(double s) { return rsqrt(s); }
-
-__device__ __noinline__ double edrift_exact_g(double v) { return v / (sqrt(1.0 + v) + 1.0); }
-
-__device__ __noinline__ bool ellipse_exact(double x, double y, double a, double b) {
-    const double u = __ddiv_rn(x, a), v = __ddiv_rn(y, b);
-    return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
 }
 
 // ---------------------------------------------------------------- map ----
@@ -368,24 +347,6 @@ __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, b
 }
 
 // Aperture: edge counts as inside, NaN as outside.
-__device__ __forceinline__ bool inside(double x, double y, const LatticeView &L) {
-    if (L.ap_type == TRK_APERTURE_RECT) {
-        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
-        return (ax <= L.ap_a_bits) & (ay <= L.ap_b_bits);
-    }
-    if (L.ap_type == TRK_APERTURE_ELLIPSE) {
-        // |x| <= 0.7 a and |y| <= 0.7 b is inside ((0.7)^2 + (0.7)^2 < 1): integer
-        // compares of the bit patterns; otherwise the exact test, rounded as
-        // (x/a)^2 + (y/b)^2 <= 1 in IEEE double.
-        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
-        if ((ax <= L.ap_ia_bits) & (ay <= L.ap_ib_bits)) return true;
-        return ellipse_exact(x, y, L.ap_a, L.ap_b);
-    }
-    return true;
-}
-
 // -------------------------------------------------------- block sums ----
 // Sum 28 per-thread values over the block; the totals land in tot[0..27].
 __device__ __forceinline__ void block_sum28(double (&v)[kMomentsN], double *sh, double *tot) {

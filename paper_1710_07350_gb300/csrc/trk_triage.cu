@@ -11,14 +11,16 @@
 // radius of the merged boundary is exact (the band follows the true boundary
 // wherever the prediction misplaced it); later passes also take every cell
 // within expand_radius of a cell whose label the last merge flipped.  Sentinel
-// cells on a regular sub-lattice are tracked in the first pass: with sentinel
-// stride <= 2 band_radius + 1 every (2 band_radius + 1)^2 block holds an exact
-// cell, which is what makes the one-cell boundary criterion hold by
-// construction (an untracked wrong cell two or more cells from the exhaustive
-// boundary would need a whole uniform 5 x 5 block without an exact cell).
-// With use_mlp = 0 the prediction is the label of the nearest coarse cell
-// instead (the same pipeline without the network).
+// cells on a regular sub-lattice are tracked with the coarse cells, before any
+// prediction: with sentinel stride <= 2 band_radius + 1 every
+// (2 band_radius + 1)^2 block holds an exact cell, which is what makes the
+// one-cell boundary criterion hold by construction (an untracked wrong cell two
+// or more cells from the exhaustive boundary would need a whole uniform 5 x 5
+// block without an exact cell).  With use_mlp = 0 the prediction is the label
+// of the nearest known (coarse or sentinel) cell instead: the same pipeline
+// without the network.
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,29 +36,33 @@ __device__ __forceinline__ double cell_centre(int i, int n, double w) {
     return __dadd_rn(-w, __dmul_rn(__dadd_rn((double)i, 0.5), __ddiv_rn(__dmul_rn(2.0, w), (double)n)));
 }
 
-// Coarse cells (ix, iy) with ix % stride == off, iy % stride == off, per variant.
-__global__ void k_coarse_points(int nx, int ny, int stride, int off, double w, int cx, int cy, int n_var,
-                                double *__restrict__ x0, double *__restrict__ y0) {
-    const int64_t n = (int64_t)n_var * cx * cy;
+// Known cells of every variant: cells[j] (j < per_v) is the j-th known cell of
+// a variant -- the coarse cells first (row by row), then the sentinel cells.
+// Points i = v * per_v + j.
+__global__ void k_known_points(const int2 *__restrict__ cells, int per_v, int n_var, int nx, int ny, double w,
+                               double *__restrict__ x0, double *__restrict__ y0) {
+    const int64_t n = (int64_t)n_var * per_v;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i % ((int64_t)cx * cy);
-        const int jx = (int)(c % cx), jy = (int)(c / cx);
-        x0[i] = cell_centre(off + jx * stride, nx, w);
-        y0[i] = cell_centre(off + jy * stride, ny, w);
+        const int2 c = cells[i % per_v];
+        x0[i] = cell_centre(c.x, nx, w);
+        y0[i] = cell_centre(c.y, ny, w);
     }
 }
 
-// Training features and labels of the coarse cells.
+// Training features and labels of the coarse cells (the first n_c known cells
+// of each variant); feature row v * n_c + j.
 __global__ void k_coarse_features(const double *__restrict__ x0, const double *__restrict__ y0,
-                                  const int32_t *__restrict__ surv, const float *__restrict__ params, int cx, int cy,
-                                  int n_var, double w, int32_t n_turns, float *__restrict__ X, float *__restrict__ y) {
-    const int64_t per = (int64_t)cx * cy, n = per * n_var;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int v = (int)(i / per);
-        X[i * 8 + 0] = (float)(x0[i] / w);
-        X[i * 8 + 1] = (float)(y0[i] / w);
-        for (int k = 0; k < 6; ++k) X[i * 8 + 2 + k] = params[v * 6 + k];
-        y[i] = surv[i] == n_turns + 1 ? 1.0f : 0.0f;
+                                  const int32_t *__restrict__ surv, const float *__restrict__ params, int n_c,
+                                  int per_v, int n_var, double w, int32_t n_turns, float *__restrict__ X,
+                                  float *__restrict__ y) {
+    const int64_t n = (int64_t)n_c * n_var;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(k / n_c);
+        const int64_t i = (int64_t)v * per_v + k % n_c;
+        X[k * 8 + 0] = (float)(x0[i] / w);
+        X[k * 8 + 1] = (float)(y0[i] / w);
+        for (int q = 0; q < 6; ++q) X[k * 8 + 2 + q] = params[v * 6 + q];
+        y[k] = surv[i] == n_turns + 1 ? 1.0f : 0.0f;
     }
 }
 
@@ -79,10 +85,16 @@ __global__ void k_threshold(const float *__restrict__ logit, int64_t m, uint8_t 
         mask[i] = logit[i] > 0.0f ? 1 : 0;
 }
 
-// Prediction without the network: label of the coarse cell nearest to each cell.
-__global__ void k_nearest_coarse(const int32_t *__restrict__ surv, int nx, int ny, int stride, int off, int cx, int cy,
-                                 int n_var, int32_t n_turns, uint8_t *__restrict__ mask) {
+// Prediction without the network: label of the nearest known cell -- the
+// nearest coarse cell (per axis j = (i - off + stride/2) / stride, clamped), or
+// the nearest sentinel cell (per-axis tables nsx, nsy of sentinel indices,
+// sx_n sentinels per row) where its squared index distance is strictly smaller.
+__global__ void k_nearest_known(const int32_t *__restrict__ surv, const int2 *__restrict__ cells, int nx, int ny,
+                                int stride, int off, int cx, int cy, int per_v, const int *__restrict__ nsx,
+                                const int *__restrict__ nsy, int sx_n, int n_var, int32_t n_turns,
+                                uint8_t *__restrict__ mask) {
     const int64_t n = (int64_t)n_var * nx * ny;
+    const int n_c = cx * cy;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(c % nx), iy = (int)((c / nx) % ny), v = (int)(c / ((int64_t)nx * ny));
         int jx = (ix - off + stride / 2) / stride, jy = (iy - off + stride / 2) / stride;
@@ -90,24 +102,32 @@ __global__ void k_nearest_coarse(const int32_t *__restrict__ surv, int nx, int n
         if (iy < off) jy = 0;
         jx = jx < cx - 1 ? jx : cx - 1;
         jy = jy < cy - 1 ? jy : cy - 1;
-        mask[c] = surv[((int64_t)v * cy + jy) * cx + jx] == n_turns + 1 ? 1 : 0;
+        int j = jy * cx + jx;
+        if (per_v > n_c) {
+            const int2 pc = cells[j];
+            const int k = n_c + nsy[iy] * sx_n + nsx[ix];
+            const int2 ps = cells[k];
+            const int dc = (pc.x - ix) * (pc.x - ix) + (pc.y - iy) * (pc.y - iy);
+            const int ds = (ps.x - ix) * (ps.x - ix) + (ps.y - iy) * (ps.y - iy);
+            if (ds < dc) j = k;
+        }
+        mask[c] = surv[(int64_t)v * per_v + j] == n_turns + 1 ? 1 : 0;
     }
 }
 
-// Coarse truth overrides the prediction; survival of coarse cells is exact.
-__global__ void k_apply_coarse(const int32_t *__restrict__ surv, int nx, int ny, int stride, int off, int cx, int cy,
-                               int n_var, int32_t n_turns, uint8_t *__restrict__ mask, uint8_t *__restrict__ known,
-                               int32_t *__restrict__ out_surv) {
-    const int64_t n = (int64_t)n_var * cx * cy;
+// Known labels override the prediction; their survival is exact.
+__global__ void k_apply_known(const int32_t *__restrict__ surv, const int2 *__restrict__ cells, int per_v, int nx,
+                              int ny, int n_var, int32_t n_turns, uint8_t *__restrict__ mask,
+                              uint8_t *__restrict__ known, int32_t *__restrict__ out_surv) {
+    const int64_t n = (int64_t)n_var * per_v;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t per = (int64_t)cx * cy;
-        const int v = (int)(i / per);
-        const int jx = (int)((i % per) % cx), jy = (int)((i % per) / cx);
-        const int64_t c = ((int64_t)v * ny + off + jy * stride) * nx + off + jx * stride;
-        const int32_t s = surv[i];
-        mask[c] = s == n_turns + 1 ? 1 : 0;
+        const int v = (int)(i / per_v);
+        const int2 cl = cells[i % per_v];
+        const int64_t c = ((int64_t)v * ny + cl.y) * nx + cl.x;
+        const int32_t sv = surv[i];
+        mask[c] = sv == n_turns + 1 ? 1 : 0;
         known[c] = 1;
-        out_surv[c] = s;
+        out_surv[c] = sv;
     }
 }
 
@@ -168,27 +188,15 @@ __global__ void k_dilate_y(const uint8_t *__restrict__ in, int nx, int ny, int n
     }
 }
 
-// On one axis of n cells, sentinel positions are off + k stride (k >= 0) up to
-// n - 1 - off, plus n - 1 - off itself (off = stride / 2): no gap exceeds the
-// stride, and both edges are within off.
-__device__ __forceinline__ bool sentinel_axis(int i, int n, int stride) {
-    const int off = stride / 2, last = n - 1 - off;
-    return i == last || (i >= off && i <= last && (i - off) % stride == 0);
-}
-
 // Cells to re-track: near (a boundary cell within the band radius or a flipped
-// cell within the expansion radius), audit cells, sentinel cells (stride > 0),
-// and not already known exactly.
+// cell within the expansion radius) or audit cells, and not already known.
 __global__ void k_band(const uint8_t *__restrict__ near, const uint8_t *__restrict__ audit,
-                       const uint8_t *__restrict__ known, int nx, int ny, int n_var, int sentinel,
-                       uint8_t *__restrict__ todo, uint8_t *__restrict__ is_audit) {
-    const int64_t n = (int64_t)n_var * nx * ny;
+                       const uint8_t *__restrict__ known, int64_t n, uint8_t *__restrict__ todo,
+                       uint8_t *__restrict__ is_audit) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(c % nx), iy = (int)((c / nx) % ny);
         const bool nr = near[c] != 0;
-        const bool se = sentinel > 0 && sentinel_axis(ix, nx, sentinel) && sentinel_axis(iy, ny, sentinel);
-        const bool au = audit && audit[c] && !nr && !se;
-        todo[c] = (!known[c] && (nr || se || au)) ? 1 : 0;
+        const bool au = audit && audit[c] && !nr;
+        todo[c] = (!known[c] && (nr || au)) ? 1 : 0;
         is_audit[c] = (!known[c] && au) ? 1 : 0;
     }
 }
@@ -266,6 +274,27 @@ __global__ void k_fill_predicted(const uint8_t *__restrict__ mask, const uint8_t
         if (!known[c]) out_surv[c] = mask[c] ? n_turns + 1 : 0;
 }
 
+constexpr int64_t kLaneCells = 16384;
+
+// Sentinel positions on an axis of n cells: off, off + stride, ... up to
+// n - 1 - off, plus n - 1 - off itself (off = stride / 2), inside [0, n).
+void sentinel_positions(int n, int stride, std::vector<int> &pos) {
+    const int off = stride / 2, last = n - 1 - off;
+    pos.clear();
+    for (int p = off; p <= last; p += stride) pos.push_back(p);
+    if (last >= 0 && last < n && (pos.empty() || pos.back() != last)) pos.push_back(last);
+}
+
+// For every cell of the axis the index of the closest position (the lower on a tie).
+void nearest_positions(const std::vector<int> &pos, std::vector<int> &out) {
+    for (int i = 0; i < (int)out.size(); ++i) {
+        int best = 0;
+        for (int k = 1; k < (int)pos.size(); ++k)
+            if (std::abs(pos[k] - i) < std::abs(pos[best] - i)) best = k;
+        out[i] = best;
+    }
+}
+
 int grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -314,23 +343,46 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     const int nx = o->nx, ny = o->ny, st = o->coarse_stride, off = st / 2;
     const int cx = (nx - off + st - 1) / st, cy = (ny - off + st - 1) / st;
     const double w = o->half_width;
-    const int64_t per = (int64_t)nx * ny, n_all = per * n_var, n_coarse = (int64_t)cx * cy * n_var;
+    const int64_t per = (int64_t)nx * ny, n_all = per * n_var;
+    const int n_c = cx * cy;
     trk_triage_stats S;
     std::memset(&S, 0, sizeof S);
     S.n_cells = n_all;
-    S.n_coarse = n_coarse;
+    S.n_coarse = (int64_t)n_c * n_var;
     double t0 = now_ms();
 
-    // 1. exact survival of the coarse cells
-    DBuf<double> cx0, cy0;
-    DBuf<int32_t> csurv;
-    if (cx0.alloc(n_coarse) || cy0.alloc(n_coarse) || csurv.alloc(n_coarse))
-        return set_error(TRK_ENOMEM, "trk_da_triage: coarse allocation failed");
-    k_coarse_points<<<grid_for(n_coarse), 256, 0, s>>>(nx, ny, st, off, w, cx, cy, n_var, cx0.p, cy0.p);
+    // 1. exact survival of the known cells of every variant: the coarse cells
+    // (row by row), then the sentinel cells (row by row), in one scan
+    std::vector<int2> cells;
+    for (int jy = 0; jy < cy; ++jy)
+        for (int jx = 0; jx < cx; ++jx) cells.push_back(make_int2(off + jx * st, off + jy * st));
+    std::vector<int> sxp, syp, nsx(nx, 0), nsy(ny, 0);
+    if (o->sentinel_stride > 0) {
+        sentinel_positions(nx, o->sentinel_stride, sxp);
+        sentinel_positions(ny, o->sentinel_stride, syp);
+        for (int b = 0; b < (int)syp.size(); ++b)
+            for (int a = 0; a < (int)sxp.size(); ++a) cells.push_back(make_int2(sxp[a], syp[b]));
+        nearest_positions(sxp, nsx);
+        nearest_positions(syp, nsy);
+    }
+    const int per_v = (int)cells.size();
+    const int64_t n_known = (int64_t)per_v * n_var;
+    S.n_sentinel = (int64_t)(per_v - n_c) * n_var;
+    DBuf<int2> dcells;
+    DBuf<int> dnsx, dnsy;
+    DBuf<double> kx0, ky0;
+    DBuf<int32_t> ksurv;
+    if (dcells.alloc(per_v) || dnsx.alloc(nx) || dnsy.alloc(ny) || kx0.alloc(n_known) || ky0.alloc(n_known) ||
+        ksurv.alloc(n_known))
+        return set_error(TRK_ENOMEM, "trk_da_triage: known-cell allocation failed");
+    TRI_CUDA(cudaMemcpyAsync(dcells.p, cells.data(), per_v * sizeof(int2), cudaMemcpyHostToDevice, s));
+    TRI_CUDA(cudaMemcpyAsync(dnsx.p, nsx.data(), nx * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRI_CUDA(cudaMemcpyAsync(dnsy.p, nsy.data(), ny * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_known_points<<<grid_for(n_known), 256, 0, s>>>(dcells.p, per_v, n_var, nx, ny, w, kx0.p, ky0.p);
     TRI_CUDA(cudaGetLastError());
     std::vector<int64_t> offs(n_var + 1);
-    for (int v = 0; v <= n_var; ++v) offs[v] = (int64_t)v * cx * cy;
-    trk_status r = trk_da_survival(lats, n_var, offs.data(), cx0.p, cy0.p, o->n_turns, nullptr, csurv.p, stream);
+    for (int v = 0; v <= n_var; ++v) offs[v] = (int64_t)v * per_v;
+    trk_status r = trk_da_survival(lats, n_var, offs.data(), kx0.p, ky0.p, o->n_turns, nullptr, ksurv.p, stream);
     if (r != TRK_OK) return r;
     double t1 = now_ms();
     S.ms_coarse = t1 - t0;
@@ -343,12 +395,13 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     TRI_CUDA(cudaMemsetAsync(mask_known.p, 0, n_all, s));
     TRI_CUDA(cudaMemsetAsync(flip.p, 0, n_all, s));
     if (o->use_mlp) {
+        const int64_t n_train = S.n_coarse;
         DBuf<float> X, y;
-        if (X.alloc(n_coarse * 8) || y.alloc(n_coarse)) return set_error(TRK_ENOMEM, "trk_da_triage: feature allocation failed");
-        k_coarse_features<<<grid_for(n_coarse), 256, 0, s>>>(cx0.p, cy0.p, csurv.p, d_params, cx, cy, n_var, w,
-                                                             o->n_turns, X.p, y.p);
+        if (X.alloc(n_train * 8) || y.alloc(n_train)) return set_error(TRK_ENOMEM, "trk_da_triage: feature allocation failed");
+        k_coarse_features<<<grid_for(n_train), 256, 0, s>>>(kx0.p, ky0.p, ksurv.p, d_params, n_c, per_v, n_var, w,
+                                                            o->n_turns, X.p, y.p);
         TRI_CUDA(cudaGetLastError());
-        r = trk_mlp_train(net, X.p, y.p, n_coarse, o->batch, o->epochs, d_perm, o->lr, nullptr, stream);
+        r = trk_mlp_train(net, X.p, y.p, n_train, o->batch, o->epochs, d_perm, o->lr, nullptr, stream);
         if (r != TRK_OK) return r;
     }
     double t2 = now_ms();
@@ -367,19 +420,20 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
             k_threshold<<<grid_for(m), 256, 0, s>>>(logit.p, m, d_mask + c0);
         }
     } else {
-        k_nearest_coarse<<<grid_for(n_all), 256, 0, s>>>(csurv.p, nx, ny, st, off, cx, cy, n_var, o->n_turns, d_mask);
+        k_nearest_known<<<grid_for(n_all), 256, 0, s>>>(ksurv.p, dcells.p, nx, ny, st, off, cx, cy, per_v, dnsx.p,
+                                                        dnsy.p, (int)sxp.size(), n_var, o->n_turns, d_mask);
     }
     TRI_CUDA(cudaGetLastError());
     TRI_CUDA(cudaStreamSynchronize(s));
     double t3 = now_ms();
     S.ms_infer = t3 - t2;
 
-    // 4./5. coarse truth; then, pass after pass, the band around the boundary of
+    // 4./5. known labels; then, pass after pass, the band around the boundary of
     // the current mask (plus the audit cells in the first pass) is gathered into
     // point lists, re-tracked exactly in FP64 and merged, until a pass finds no
     // cell left to track.
-    k_apply_coarse<<<grid_for(n_coarse), 256, 0, s>>>(csurv.p, nx, ny, st, off, cx, cy, n_var, o->n_turns, d_mask,
-                                                      mask_known.p, d_survival);
+    k_apply_known<<<grid_for(n_known), 256, 0, s>>>(ksurv.p, dcells.p, per_v, nx, ny, n_var, o->n_turns, d_mask,
+                                                    mask_known.p, d_survival);
     TRI_CUDA(cudaGetLastError());
     DBuf<int64_t> dcounts, doffs;
     DBuf<unsigned long long> wrong;
@@ -400,8 +454,8 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
         k_dilate_x<<<grid_for(n_all), 256, 0, s>>>(bnd.p, R > 0 ? flip.p : nullptr, nx, ny, n_var, o->band_radius, R,
                                                    tmp.p);
         k_dilate_y<<<grid_for(n_all), 256, 0, s>>>(tmp.p, nx, ny, n_var, o->band_radius, R, bnd.p);
-        k_band<<<grid_for(n_all), 256, 0, s>>>(bnd.p, pass == 0 ? d_audit : nullptr, mask_known.p, nx, ny, n_var,
-                                               pass == 0 ? o->sentinel_stride : 0, todo.p, audit_c.p);
+        k_band<<<grid_for(n_all), 256, 0, s>>>(bnd.p, pass == 0 ? d_audit : nullptr, mask_known.p, n_all, todo.p,
+                                               audit_c.p);
         k_count<<<n_var, 256, 0, s>>>(todo.p, per, dcounts.p);
         TRI_CUDA(cudaGetLastError());
         TRI_CUDA(cudaMemcpyAsync(counts.data(), dcounts.p, n_var * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -439,11 +493,17 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
         TRI_CUDA(cudaGetLastError());
         const double p1 = now_ms();
         t_band += p1 - p0;
-        // Few cells: the pass is latency-bound (one warp per SM sub-partition
-        // issues one FP64 instruction per several tens of cycles whatever its
-        // lane count), so one particle per thread halves the chain per warp.
-        trk_schedule sch = {128, n_todo <= 2 * 152 * 128 ? 1 : 2, 1, 2};
-        r = trk_da_survival(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, &sch, tsurv.p, stream);
+        // Few cells: the pass is bound by one particle's latency over all turns,
+        // so the lane-parallel scan (8 lanes per particle) takes it where the
+        // lattices allow; otherwise one particle per thread keeps one chain per
+        // thread and spreads the warps over the SMs.
+        r = TRK_EUNSUPPORTED;
+        if (n_todo <= kLaneCells)
+            r = trk_da_survival_lanes(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, tsurv.p, stream);
+        if (r == TRK_EUNSUPPORTED) {
+            trk_schedule sch = {128, n_todo <= 2 * 152 * 128 ? 1 : 2, 1, 2};
+            r = trk_da_survival(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, &sch, tsurv.p, stream);
+        }
         if (r != TRK_OK) return r;
         TRI_CUDA(cudaMemsetAsync(flip.p, 0, n_all, s));
         k_merge<<<grid_for(n_todo), 256, 0, s>>>(tcell.p, tsurv.p, n_todo, o->n_turns, audit_c.p, d_mask,

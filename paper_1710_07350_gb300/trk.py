@@ -56,7 +56,8 @@ class trk_triage_stats(ctypes.Structure):
     _fields_ = [("n_cells", c_int64), ("n_coarse", c_int64), ("n_band", c_int64), ("n_audit", c_int64),
                 ("n_tracked", c_int64), ("n_audit_wrong", c_int64), ("ms_coarse", c_double),
                 ("ms_train", c_double), ("ms_infer", c_double), ("ms_band", c_double), ("ms_retrack", c_double),
-                ("n_passes", c_int64), ("pass_cells", c_int64 * 16), ("pass_ms", c_double * 16)]
+                ("n_passes", c_int64), ("pass_cells", c_int64 * 16), ("pass_ms", c_double * 16),
+                ("n_sentinel", c_int64)]
 
 
 class trk_schedule(ctypes.Structure):
@@ -110,6 +111,7 @@ def lib():
             "trk_bunch_stats": [P, P, c_int32],
             "trk_wake_static": [P, c_int64, c_int64, c_int32, c_double, c_double, c_double, c_double, P, P, P],
             "trk_probe_fp64": [P, P],
+            "trk_da_survival_lanes": [P, c_int32, P, P, P, c_int32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -362,6 +364,19 @@ def trk_da_survival(lattices, x0, y0, offsets, n_turns, schedule=None, stream=No
                                       schedule.get("chunk_turns", 0), schedule.get("growth", 0)))
     _check(lib().trk_da_survival(_handles(lattices), len(lattices), offs.ctypes.data_as(c_void_p), _dptr(x0),
                                  _dptr(y0), n_turns, s, _dptr(surv), c_void_p(stream.cuda_stream)))
+    return surv
+
+
+def trk_da_survival_lanes(lattices, x0, y0, offsets, n_turns, stream=None):
+    """As trk_da_survival, 8 lanes per particle (few points; MAP, EDRIFT and
+    THINSEXT lattices)."""
+    import torch
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    surv = torch.empty(int(offs[-1]), dtype=torch.int32, device=x0.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(x0.device)
+    _check(lib().trk_da_survival_lanes(_handles(lattices), len(lattices), offs.ctypes.data_as(c_void_p), _dptr(x0),
+                                       _dptr(y0), n_turns, _dptr(surv), c_void_p(stream.cuda_stream)))
     return surv
 
 

@@ -110,3 +110,38 @@ def test_nonlearned_triage_matches_triage_oracle():
     if strict:
         assert st["n_tracked"] == n_tracked
         assert st["n_passes"] == passes
+
+
+def test_lane_scan_bit_identical_to_batched_scan():
+    """8 lanes per particle give the batched tracker's survival turns exactly,
+    on maps, thin sextupoles and exact drifts, rectangle and ellipse apertures."""
+    n, turns = 40, 300
+    x0, y0, _ = grid_points(n)
+    lats = [syn.lattice_c5(v) for v in (0, 1, 2)]
+    lats[1]["elements"] = lats[1]["elements"][:5] + [{"type": "EDRIFT", "L": 0.05}] + lats[1]["elements"][5:]
+    lats[2]["aperture"] = ("ellipse", 0.02, 0.015)
+    L = [trk.trk_create_lattice(l, moments=False) for l in lats]
+    offs = [k * n * n for k in range(4)]
+    ax, ay = torch.cat([x0] * 3), torch.cat([y0] * 3)
+    batched = trk.trk_da_survival(L, ax, ay, offs, turns, schedule={"block": 128, "per_thread": 1,
+                                                                     "chunk_turns": 7}).cpu().numpy()
+    lanes = trk.trk_da_survival_lanes(L, ax, ay, offs, turns).cpu().numpy()
+    assert np.array_equal(batched, lanes)
+    assert 0 < np.sum(lanes == turns + 1) < lanes.size
+    # ragged variant sizes, an empty variant, a single point
+    offs2 = [0, 7, 7, 8]
+    sub_x = torch.cat([x0[:7], x0[100:101]])
+    sub_y = torch.cat([y0[:7], y0[100:101]])
+    a = trk.trk_da_survival(L, sub_x, sub_y, offs2, turns, schedule={"block": 64, "per_thread": 1}).cpu().numpy()
+    b = trk.trk_da_survival_lanes(L, sub_x, sub_y, offs2, turns).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_lane_scan_rejects_kick_drift_lattice():
+    L = [trk.trk_create_lattice(syn.lattice_c2(cells=1), moments=False)]
+    x0, y0, _ = grid_points(4)
+    with pytest.raises(RuntimeError, match="MAP, EDRIFT and THINSEXT"):
+        trk.trk_da_survival_lanes(L, x0, y0, [0, 16], 5)
+    # the general entry point falls back to the batched tracker
+    s = trk.trk_da_survival(L, x0, y0, [0, 16], 5).cpu().numpy()
+    assert np.all((s >= 1) & (s <= 6))

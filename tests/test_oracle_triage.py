@@ -83,9 +83,11 @@ def test_sentinels_make_the_one_cell_criterion_hold(seed, predict):
     assert passes >= 1
     # every tracked or coarse cell carries its exact survival turn; the rest the merged label
     ci = tri.coarse_index(n, 8)
-    coarse = np.zeros((n, n), bool)
-    coarse[np.ix_(ci, ci)] = True
-    known = tracked | coarse
+    sa = tri.sentinel_axis(n, 5)
+    pre = np.zeros((n, n), bool)
+    pre[np.ix_(ci, ci)] = True
+    pre[np.ix_(sa, sa)] = True
+    known = tracked | pre
     assert np.array_equal(out[known], surv[known])
     assert np.array_equal(out[~known], np.where(mask[~known], turns + 1, 0))
     assert np.array_equal(mask[known], exact[known])
@@ -118,6 +120,31 @@ def test_island_between_coarse_cells_is_missed_without_sentinels():
     mask, _, tracked, _ = tri.triage_variant(surv, turns, stride=8, r=2, sentinel=5)
     assert dm.boundary_difference(mask, exact)[0]
     assert np.array_equal(mask, exact)
+
+
+def test_nearest_known_prediction_brute_force():
+    """Nearest known cell by brute force over coarse and sentinel cells:
+    squared index distance, coarse cells win ties, and among sentinels the
+    lower position per axis."""
+    g = np.random.Generator(np.random.Philox(key=22))
+    n, s, t = 37, 8, 5
+    exact = g.uniform(size=(n, n)) < 0.5
+    pred = tri.nearest_known_prediction(exact, n, s, t)
+    ci, sa = tri.coarse_index(n, s), tri.sentinel_axis(n, t)
+    for iy in range(n):
+        for ix in range(n):
+            dc = min((cy - iy) ** 2 + (cx - ix) ** 2 for cy in ci for cx in ci)
+            ds = min((sy - iy) ** 2 + (sx - ix) ** 2 for sy in sa for sx in sa)
+            if ds < dc:
+                best = min(((sy - iy) ** 2 + (sx - ix) ** 2, sy, sx) for sy in sa for sx in sa)
+                want = exact[best[1], best[2]]
+            else:
+                # the coarse rule: per-axis nearest, the upper one on a tie
+                jy = tri.nearest_coarse_index(n, s)[iy]
+                jx = tri.nearest_coarse_index(n, s)[ix]
+                assert (ci[jy] - iy) ** 2 + (ci[jx] - ix) ** 2 == dc
+                want = exact[ci[jy], ci[jx]]
+            assert pred[iy, ix] == want, (iy, ix)
 
 
 def test_nearest_coarse_prediction_indices():
