@@ -421,7 +421,8 @@ def run_da(n_var, trk, syn, torch):
     return out
 
 
-TRACK_SOURCES = ("paper_1710_07350_gb300/csrc/trk_track.cu", "paper_1710_07350_gb300/csrc/trk_internal.cuh")
+TRACK_SOURCES = ("paper_1710_07350_gb300/csrc/trk_track.cu", "paper_1710_07350_gb300/csrc/trk_device.cuh",
+                 "paper_1710_07350_gb300/csrc/trk_internal.cuh")
 
 
 def track_source_digest():
