@@ -62,10 +62,12 @@ def parse():
     p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
-                   help="c2 (default, the headline line); c3 wake linac and c4 batched variants print "
-                        "their own measurement lines")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train"],
+                   help="c2 (default, the headline line); c3 wake linac, c4 batched variants and the "
+                        "surrogate's inference (mlp) and training (mlp-train) print their own lines")
     p.add_argument("--da-variants", type=int, default=64)
+    p.add_argument("--rows", type=int, default=64 * 512 * 512, help="mlp: rows per inference call")
+    p.add_argument("--epochs", type=int, default=24, help="mlp-train: epochs")
     return p.parse_args()
 
 
@@ -549,6 +551,63 @@ def run_c4(args):
     return 0
 
 
+def run_mlp(args):
+    """Surrogate inference: one call over `rows` feature rows (the DA grid's
+    16.8 M cells by default), tcgen05 layers; BF16 tensor FLOP/s counted on
+    the unpadded network (8 -> 256 -> 256 -> 256 -> 256 -> 1)."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import trk
+    net = trk.trk_mlp_create(syn.mlp_init(7))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.rand((args.rows, 8), device="cuda", dtype=torch.float32, generator=g) * 2 - 1
+    for _ in range(args.warmup):
+        trk.trk_mlp_forward(net, X)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        trk.trk_mlp_forward(net, X)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flops = args.rows * 2.0 * (8 * 256 + 3 * 256 * 256 + 256)
+    print(json.dumps({"workload": "surrogate inference, %d rows" % args.rows, "ms_per_call": ms,
+                      "rows_per_s": args.rows / (ms / 1e3), "tflops_bf16": flops / (ms / 1e3) / 1e12,
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
+def run_mlp_train(args):
+    """Surrogate training as the triaged scan runs it: 262 144 samples (64
+    variants x 64 x 64 coarse cells), batch 4096, Adam lr 2e-3, `epochs` epochs."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import trk
+    n = 64 * 64 * 64
+    g = torch.Generator(device="cuda").manual_seed(6)
+    X = torch.rand((n, 8), device="cuda", dtype=torch.float32, generator=g) * 2 - 1
+    y = (X[:, 0] ** 2 + X[:, 1] ** 2 < 0.5).float()
+    perm = torch.stack([torch.randperm(n, device="cuda", generator=g) for _ in range(args.epochs)]).int()
+    times = []
+    for k in range(args.warmup + args.steps):
+        net = trk.trk_mlp_create(syn.mlp_init(7))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        trk.trk_mlp_train(net, X, y, batch=4096, epochs=args.epochs, perm=perm, lr=2e-3)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    steps = args.epochs * ((n + 4095) // 4096)
+    s = sum(times) / len(times)
+    print(json.dumps({"workload": "surrogate training, %d samples, batch 4096, %d epochs" % (n, args.epochs),
+                      "seconds": s, "adam_steps": steps, "us_per_step": 1e6 * s / steps,
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -557,6 +616,10 @@ def main():
         return run_c3(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
+    if args.workload == "mlp-train":
+        return run_mlp_train(args)
     return run_ours(args)
 
 

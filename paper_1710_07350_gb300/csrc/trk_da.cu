@@ -4,11 +4,10 @@
 //
 // For few particles the scan is bound by one particle's chain of dependent
 // FP64 operations over all turns, not by throughput.  k_da_lanes then gives a
-// particle 8 lanes, lane r holding coordinate r: the six rows of a map are
-// evaluated on six lanes at once (coordinates exchanged by warp shuffles),
-// thin sextupoles and drifts update their lanes, and every lane takes the same
-// aperture decision.  Each row sums its terms in the order, and with the
-// operations, of the tracking kernel, so the survival turns are bit-identical.
+// particle 8 lanes: the six rows of a map are evaluated on six lanes at once
+// and exchanged by warp shuffles; everything else runs replicated on every
+// lane.  Each row sums its terms in the order, and with the operations, of the
+// tracking kernel, so the survival turns are bit-identical.
 #include "trk_device.cuh"
 #include "trk_internal.cuh"
 
@@ -37,9 +36,23 @@ __global__ void k_da_survival(const int32_t *__restrict__ ids, const int32_t *__
     }
 }
 
+// q[j] for a runtime j by selects, so that q stays in registers.
+__device__ __forceinline__ double sel6(const double (&q)[6], int j) {
+    double v = q[0];
+    v = j == 1 ? q[1] : v;
+    v = j == 2 ? q[2] : v;
+    v = j == 3 ? q[3] : v;
+    v = j == 4 ? q[4] : v;
+    v = j == 5 ? q[5] : v;
+    return v;
+}
+
 // Particle i of the point list takes threads 8 i .. 8 i + 7; its variant is the
-// v with offsets[v] <= i < offsets[v + 1].  Lattices hold MAP, EDRIFT and
-// THINSEXT elements only (checked on the host).
+// v with offsets[v] <= i < offsets[v + 1].  Every lane of the group holds all
+// six coordinates; lane r < 6 sums row r of a map, and six independent
+// shuffles hand the new coordinates to the group.  Thin sextupoles, drifts and
+// the aperture test run on every lane with the same operations (no exchange).
+// Lattices hold MAP, EDRIFT and THINSEXT elements only (checked on the host).
 __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict__ views, int n_var,
                                                   const int64_t *__restrict__ offsets,
                                                   const double *__restrict__ x0, const double *__restrict__ y0,
@@ -56,7 +69,7 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
         else hi = mid;
     }
     const LatticeView L = views[lo];
-    double c = r == 0 ? x0[i] : (r == 2 ? y0[i] : 0.0);
+    double q[6] = {x0[i], 0.0, y0[i], 0.0, 0.0, 0.0};
     int32_t surv = n_turns + 1;
     bool alive = true;
     for (int turn = 0; alive && turn < n_turns; ++turn) {
@@ -68,40 +81,35 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                 const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
                 const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
                 const double2 *t = reinterpret_cast<const double2 *>(L.terms + __ldg(&E->term0));
-                int nmax = 0;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) nmax = rb[q + 1] - rb[q] > nmax ? rb[q + 1] - rb[q] : nmax;
-                const int kb = r < 6 ? rb[r] : 0, len = r < 6 ? rb[r + 1] - rb[r] : 0;
-                double acc = (r < 6 && ((flags >> r) & 1u)) ? c : 0.0;
-                for (int k = 0; k < nmax; ++k) {
-                    const bool on = k < len;
-                    const double2 tv = on ? __ldg(t + kb + k) : make_double2(0.0, 0.0);
+                const int rr = r < 6 ? r : 0;
+                const int kb = rb[rr], len = r < 6 ? rb[rr + 1] - rb[rr] : 0;
+                double acc = (r < 6 && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
+                for (int k = 0; k < len; ++k) {
+                    const double2 tv = __ldg(t + kb + k);
                     const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
                     const int deg = code & 3, j = (code >> 2) & 7, jk = (code >> 5) & 7, jl = (code >> 8) & 7;
-                    const double v1 = __shfl_sync(gm, c, g0 + j);
-                    const double v2 = __shfl_sync(gm, c, g0 + jk);
-                    const double v3 = __shfl_sync(gm, c, g0 + jl);
                     double m = 1.0;
-                    if (deg >= 1) m = v1;
-                    if (deg >= 2) m *= v2;
-                    if (deg >= 3) m *= v3;
-                    if (on) acc = fma(tv.x, m, acc);
+                    if (deg >= 1) m = sel6(q, j);
+                    if (deg >= 2) m *= sel6(q, jk);
+                    if (deg >= 3) m *= sel6(q, jl);
+                    acc = fma(tv.x, m, acc);
                 }
-                if (r < 6) c = acc;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
             } else if (type == TRK_THINSEXT) {
-                const double x = __shfl_sync(gm, c, g0), y = __shfl_sync(gm, c, g0 + 2);
                 const double k2 = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
-                if (r == 1) c = fma(-hk, (x - y) * (x + y), c);
-                if (r == 3) c = fma(k2, x * y, c);
+                const double x = q[0], y = q[2];
+                q[1] = fma(-hk, (x - y) * (x + y), q[1]);
+                q[3] = fma(k2, x * y, q[3]);
             } else if (type == TRK_EDRIFT) {
-                const double xp = __shfl_sync(gm, c, g0 + 1), yp = __shfl_sync(gm, c, g0 + 3);
                 const double Ld = __ldg(&E->p[0]);
-                if (r == 0) c = fma(Ld, xp, c);
-                if (r == 2) c = fma(Ld, yp, c);
-                if (r == 4) c = fma(Ld, edrift_g(fma(xp, xp, yp * yp)), c);
+                const double xp = q[1], yp = q[3];
+                const double g = edrift_g(fma(xp, xp, yp * yp));
+                q[0] = fma(Ld, xp, q[0]);
+                q[2] = fma(Ld, yp, q[2]);
+                q[4] = fma(Ld, g, q[4]);
             }
-            const double x = __shfl_sync(gm, c, g0), y = __shfl_sync(gm, c, g0 + 2);
-            if (!inside(x, y, L)) {
+            if (!inside(q[0], q[2], L)) {
                 surv = turn + 1;
                 alive = false;
                 break;

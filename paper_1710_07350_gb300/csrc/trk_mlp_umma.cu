@@ -20,7 +20,7 @@
 //   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M 128, N 256, K 16), commits
 //              to free each A stage and to publish each finished accumulator;
-//   warps 2-9  epilogue: tcgen05.ld of their TMEM lane quadrant and column half,
+//   warps 2-17 epilogue: tcgen05.ld of their TMEM lane quadrant and column quarter,
 //              bias + GELU + BF16, 16-byte stores in the tiled layout; the
 //              accumulator is released to the MMA thread for the tile after next.
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
@@ -36,7 +36,7 @@ namespace {
 
 constexpr int UM = 128, UN = 256, KCH = 64;
 constexpr int kStages = 4;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;                       // 4 per TMEM lane quadrant
 constexpr int kUmmaThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kABlockBytes = UM * KCH * 2;  // 16 KB
 constexpr uint32_t kWBlockBytes = UN * KCH * 2;  // 32 KB
@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
             mbar_wait(&S.drain, 0, abort);
         }
     } else {
-        const int q = warp & 3, half = (warp - 2) >> 2;
+        constexpr int kCols = UN / (kEpiWarps / 4);   // columns per epilogue warp
+        const int q = warp & 3, part = (warp - 2) >> 2;
         const int row = q * 32 + lane;   // TMEM lane = row of the tile
         uint32_t j = 0;
         for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             __nv_bfloat16 *orow = Out + ((size_t)t * 4 * 16 * 8 * 64) + (size_t)(row >> 3) * 8 * 64 + (row & 7) * 8;
 #pragma unroll 1
-            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+            for (int c0 = part * kCols; c0 < part * kCols + kCols; c0 += 32) {
                 uint32_t r[32];
                 const uint32_t ta = tmem + b * UN + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
                 asm volatile(
