@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
+    p.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi samples (default: temp dir)")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train"],
                    help="c2 (default, the headline line); c3 wake linac, c4 batched variants and the "
                         "surrogate's inference (mlp) and training (mlp-train) print their own lines")
@@ -85,11 +86,11 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, directory=None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/trk_clocks_%d.csv" % os.getpid()
+        self.path = os.path.join(directory or tempfile.gettempdir(), "trk_clocks_rank%d.csv" % index)
 
     def start(self):
         try:
@@ -251,7 +252,7 @@ def run_ours(args):
     trk.trk_bunch_set_schedule(b, **sched)
     trk.trk_bunch_enable_timing(b, True)
     trk.trk_bunch_stats(b, reset=True)
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_dir)
     barrier()
     clocks.start()
     step_ms, passes, flop = [], 0.0, 0.0

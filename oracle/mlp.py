@@ -4,7 +4,7 @@ round, so gradients can be compared tightly.
 
 Oracle / test infrastructure only.
 
-Network (the DA surrogate of the benchmark spec; the paper has no learned part):
+Network (the dynamic-aperture triage surrogate; the paper has no learned part):
   input 8 (x/25 mm, y/25 mm, 6 normalised lattice parameters)
   4 hidden layers Linear(-> 256) + GELU (erf form), then Linear(256 -> 1) logit.
 Weights are BF16 copies of FP32 master weights; activations entering every

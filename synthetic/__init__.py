@@ -33,7 +33,7 @@ def p0c_from_energy(e_total_ev):
 
 P0C_1GEV = p0c_from_energy(1.0e9)
 
-# Ring and linac constants (readings of the paper's silent points, listed in the design doc).
+# Ring and linac constants (readings of the points the paper leaves open).
 L_QUAD, K1_QUAD, L_DRIFT = 0.2, 1.2, 1.0
 L_SEXT, K2_SEXT, L_DRIFT_C2, N_KICKS = 0.1, 20.0, 0.9, 4
 C2_CELLS, C2_HARMONIC, C2_VOLT, C2_PHASE = 40, 400, 1.0e6, -90.0

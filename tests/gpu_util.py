@@ -4,7 +4,7 @@ import numpy as np
 
 from paper_1710_07350_gb300 import trk
 
-# Tolerances (BASELINE the benchmark spec): max coordinate error 1e-12 after one pass
+# Tolerances of the tracking path: max coordinate error 1e-12 after one pass
 # and 1e-9 after 100 turns on regular orbits; moments 1e-12 relative to the
 # beam sizes; lost-id sets exact except particles that came within 1e-9 m of
 # the aperture edge.
