@@ -141,6 +141,16 @@ trk_status trk_bunch_free(trk_bunch *b);
 trk_status trk_bunch_set_p0c(trk_bunch *b, double p0c_ev);
 trk_status trk_bunch_p0c(trk_bunch *b, double *p0c_ev);
 
+/* Absolute turn counter of the bunch (turns tracked so far; loss records carry
+ * it).  Checkpoint and restart: copy the alive slots [0, n_alive) of the
+ * coordinates and ids, trk_bunch_p0c and trk_bunch_turn to the host; later wrap
+ * copies of them as a new bunch and set its p0c and turn: tracking continues
+ * bit-identically (the loss records before the checkpoint stay with the old
+ * bunch).  trk_bunch_set_turn takes 0 .. 2^31 - 1; neither call touches the
+ * device. */
+trk_status trk_bunch_set_turn(trk_bunch *b, int64_t turn);
+trk_status trk_bunch_turn(const trk_bunch *b, int64_t *turn);
+
 /* Launch schedule: threads per block (64..256, multiple of 32), particles per
  * thread (1, 2 or 4, advanced in lock-step), turns per fused launch between
  * compactions (>= 1).  Zero

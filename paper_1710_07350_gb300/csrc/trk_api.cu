@@ -383,6 +383,18 @@ extern "C" trk_status trk_bunch_p0c(trk_bunch *b, double *p0c) {
     return TRK_OK;
 }
 
+extern "C" trk_status trk_bunch_set_turn(trk_bunch *b, int64_t turn) {
+    if (!b || turn < 0 || turn > 0x7fffffffll) return fail(TRK_EINVAL, "trk_bunch_set_turn: bad argument");
+    b->turn = turn;
+    return TRK_OK;
+}
+
+extern "C" trk_status trk_bunch_turn(const trk_bunch *b, int64_t *turn) {
+    if (!b || !turn) return fail(TRK_EINVAL, "trk_bunch_turn: bad argument");
+    *turn = b->turn;
+    return TRK_OK;
+}
+
 extern "C" trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s) {
     if (!b || !s) return fail(TRK_EINVAL, "trk_bunch_set_schedule: NULL argument");
     if (s->block && (s->block < 64 || s->block > 256 || s->block % 32))

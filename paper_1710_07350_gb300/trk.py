@@ -110,6 +110,8 @@ def lib():
             "trk_da_triage": [P, c_int32, P, P, P, P, P, P, P, P, P],
             "trk_bunch_stats": [P, P, c_int32],
             "trk_wake_static": [P, c_int64, c_int64, c_int32, c_double, c_double, c_double, c_double, P, P, P],
+            "trk_bunch_set_turn": [P, c_int64],
+            "trk_bunch_turn": [P, P],
             "trk_probe_fp64": [P, P],
             "trk_da_survival_lanes": [P, c_int32, P, P, P, c_int32, P, P],
         }
@@ -511,6 +513,16 @@ def trk_probe_fp64(stream=None):
     out = (c_double * 3)()
     _check(lib().trk_probe_fp64(out, c_void_p(stream.cuda_stream)))
     return tuple(out)
+
+
+def trk_bunch_set_turn(b, turn):
+    _check(lib().trk_bunch_set_turn(b.handle, int(turn)))
+
+
+def trk_bunch_turn(b):
+    t = c_int64()
+    _check(lib().trk_bunch_turn(b.handle, ctypes.byref(t)))
+    return t.value
 
 
 def download(b):

@@ -188,3 +188,59 @@ def test_fp64_probe_rates_are_plausible():
     assert 2e11 < fma_rate < 7e11
     assert 0.3 * fma_rate < mul_rate <= 1.05 * fma_rate
     assert 0.3 * fma_rate < add_rate <= 1.05 * fma_rate
+
+
+def test_checkpoint_restart_bit_identical():
+    """Checkpoint after 4 turns (alive slots, ids, p0c, turn counter copied to the
+    host), restart in a new bunch for 5 more: the coordinates and loss records
+    equal one straight 9-turn run; the moments agree to reduction order."""
+    lat = syn.lattice_c2(cells=3)
+    lat["aperture"] = ("ellipse", 1.5e-3, 8e-4)
+    z = syn.bunch("c2", n=1500, seed=4)
+    a = gpu_track(lat, z, 9)
+    za, al_a, lt_a, le_a = by_id(a, 1500)
+    L = trk.trk_create_lattice(lat)
+    coords, ids = trk.upload(z)
+    b = trk.trk_bunch_wrap(coords, ids)
+    trk.trk_track(b, L, 4)
+    m1 = trk.trk_moments(b)
+    na = trk.trk_n_alive(b)
+    zz, ii = trk.download(b)
+    p0, turn, lost1 = trk.trk_bunch_p0c(b), trk.trk_bunch_turn(b), trk.trk_lost(b)
+    assert turn == 4 and 0 < na < 1500
+    c2, _ = trk.upload(zz[:na])
+    ids2 = torch.from_numpy(np.ascontiguousarray(ii[:na]).astype(np.int32)).cuda()
+    b2 = trk.trk_bunch_wrap(c2, ids2)
+    trk.trk_bunch_set_p0c(b2, p0)
+    trk.trk_bunch_set_turn(b2, turn)
+    trk.trk_track(b2, L, 5)
+    m2 = trk.trk_moments(b2)
+    assert trk.trk_bunch_turn(b2) == 9 and trk.trk_bunch_p0c(b2) == a["p0c"]
+    zb = np.full((1500, 6), np.nan)
+    z2, i2 = trk.download(b2)
+    zb[i2] = z2
+    zb[ii[na:]] = zz[na:]          # lost before the checkpoint: slots [n_alive, n) of the first bunch
+    lt_b = np.full(1500, -1)
+    le_b = np.full(1500, -1)
+    for lid, lt, le in (lost1, trk.trk_lost(b2)):
+        lt_b[lid] = lt
+        le_b[lid] = le
+    al_b = np.zeros(1500, bool)
+    al_b[i2[:trk.trk_n_alive(b2)]] = True
+    assert np.array_equal(al_a, al_b)
+    assert np.array_equal(lt_a, lt_b) and np.array_equal(le_a, le_b)
+    assert np.array_equal(za, zb)
+    assert np.allclose(a["moments"], np.concatenate([m1, m2]), rtol=1e-13, atol=0)
+    assert np.array_equal(a["moments"][:, 0], np.concatenate([m1, m2])[:, 0])
+
+
+def test_repeated_runs_bit_identical():
+    """Run-to-run reproducibility of the reductions (moments) and of the
+    coordinates: no order depends on scheduling or atomics."""
+    lat = syn.lattice_c2(cells=4)
+    lat["aperture"] = ("ellipse", 1.5e-3, 8e-4)
+    z = syn.bunch("c2", n=30_000, seed=8)
+    r1 = gpu_track(lat, z, 6)
+    r2 = gpu_track(lat, z, 6)
+    assert np.array_equal(r1["moments"], r2["moments"])
+    assert np.array_equal(r1["z"], r2["z"]) and np.array_equal(r1["ids"], r2["ids"])
