@@ -53,6 +53,12 @@ def lib():
         L.o_wake.restype = None
         L.o_wake.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                              ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
+        L.o_wake2.restype = None
+        L.o_wake2.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]
+        L.o_wake_dipole.restype = None
+        L.o_wake_dipole.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -91,6 +97,7 @@ def lattice_arrays(lat):
         elif t == "WAKE":
             ei[e, 3] = el["nbins"]
             ed[e, 6], ed[e, 7], ed[e, 8] = el["W0"], el["sc"], el["charge"]
+            ed[e, 10] = el.get("W0T", 0.0)
         else:
             raise ValueError(t)
     return ei, ed, em
@@ -164,6 +171,31 @@ def wake(z, nbins, w0, sc, charge, p0c, alive=None, n_total=None):
     lib().o_wake(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, w0, sc, charge, p0c,
                  _p(h), _p(V))
     return z, h, V
+
+
+def wake2(z, nbins, w0, w0t, sc, charge, p0c, alive=None, n_total=None):
+    """Longitudinal and transverse wake on a copy of z; returns (z, hist, V, Vx, Vy)."""
+    z = np.array(z, dtype=np.float64, order="C", copy=True)
+    n = z.shape[0]
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    V, Vx, Vy = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
+    lib().o_wake2(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, w0, w0t, sc, charge, p0c,
+                  _p(h), _p(V), _p(Vx), _p(Vy))
+    return z, h, V, Vx, Vy
+
+
+def wake_dipole(z, nbins, coord, alive=None):
+    """Per-bin sums of coordinate `coord` (0 = x, 2 = y) on the bins of wake_hist."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    n = z.shape[0]
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    lmin, dl = ctypes.c_double(), ctypes.c_double()
+    lib().o_wake_hist(_p(z), _p(alive), n, nbins, ctypes.byref(lmin), ctypes.byref(dl), _p(h))
+    D = np.zeros(nbins)
+    lib().o_wake_dipole(_p(z), _p(alive), n, nbins, lmin.value, dl.value, coord, _p(D))
+    return D
 
 
 def survival_turns(lat, z0, n_turns):

@@ -25,7 +25,10 @@
  *     the paper's USE_KAHAN option): n, 6 means, 21 central second moments;
  *   - longitudinal wake (Sec. 2.2-2.3, Table 1 WAKE): min/max of l, histogram,
  *     direct O(N^2) causal convolution with W(s) = W0/sqrt(max(s, s_c)),
- *     linearly interpolated energy kick.
+ *     linearly interpolated energy kick;
+ *   - transverse dipole wake on the same bins (Table 1 TRWAKE, the transverse
+ *     half of RFCW): per-bin sums of x and y, convolution with
+ *     W_T(s) = W0T/sqrt(max(s, s_c)), interpolated kicks on x' and y'.
  *
  * Coordinates: (x, x', y, y', l, delta), l the path-length deviation [m].
  * Lattice description: one row per element in three flat arrays
@@ -41,7 +44,7 @@
 enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7 };
 enum { O_AP_NONE = 0, O_AP_RECT = 1, O_AP_ELLIPSE = 2 };
 enum { ED_LENGTH = 0, ED_K1 = 1, ED_K2 = 2, ED_VOLT = 3, ED_PHASE = 4, ED_FREQ = 5,
-       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_N = 16 };
+       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_N = 16 };
 #define EM_N 504
 #define C_LIGHT 299792458.0
 #define O_PI 3.14159265358979323846
@@ -306,25 +309,94 @@ void o_wake_kick(double *x, const uint8_t *alive, int64_t n, const double *V, in
     }
 }
 
+/* Transverse dipole sums on the bins of o_wake_hist: D[k] = sum of coordinate
+ * c (0 = x, 2 = y) over the alive particles of bin k, compensated sums in
+ * particle order. */
+void o_wake_dipole(const double *x, const uint8_t *alive, int64_t n, int nb, double lmin, double dl, int c,
+                   double *D)
+{
+    nsum *acc = (nsum *)calloc((size_t)nb, sizeof(nsum));
+    for (int64_t i = 0; i < n; ++i) {
+        if (!alive[i]) continue;
+        int64_t b = 0;
+        if (dl > 0.0) {
+            b = (int64_t)floor((x[6 * i + 4] - lmin) / dl);
+            if (b < 0) b = 0;
+            if (b > nb - 1) b = nb - 1;
+        }
+        nsum_add(&acc[b], x[6 * i + c]);
+    }
+    for (int k = 0; k < nb; ++k) D[k] = nsum_get(&acc[k]);
+    free(acc);
+}
+
+/* Transverse voltage: V_k = +q_m sum_{j<=k} D_j W_T((k-j) dl),
+ * W_T(s) = W0T/sqrt(max(s, s_c)): a leading offset deflects the particles
+ * behind it towards the same side.  Direct O(nb^2), compensated sums. */
+void o_wake_conv_t(const double *D, int nb, double dl, double w0t, double sc, double qm, double *V)
+{
+    for (int k = 0; k < nb; ++k) {
+        nsum acc = {0.0, 0.0};
+        for (int j = 0; j <= k; ++j) {
+            if (D[j] == 0.0) continue;
+            double s = (double)(k - j) * dl;
+            double w = w0t / sqrt(s > sc ? s : sc);
+            nsum_add(&acc, D[j] * w);
+        }
+        V[k] = qm * nsum_get(&acc);
+    }
+}
+
 /* Whole wake element; n_total sets the macro-particle charge q_m = Q/n_total.
- * hist_out / V_out (nb entries each) may be NULL. */
-void o_wake(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb,
-            double w0, double sc, double charge, double p0c, int64_t *hist_out, double *V_out)
+ * With w0t != 0 the transverse kicks x' += Vx(l)/(p0c (1 + delta)),
+ * y' += Vy(l)/(p0c (1 + delta)) come first (delta before the energy kick); all
+ * voltages are computed from the particles entering the element.
+ * hist_out / V_out / Vx_out / Vy_out (nb entries each) may be NULL. */
+void o_wake2(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb, double w0, double w0t,
+             double sc, double charge, double p0c, int64_t *hist_out, double *V_out, double *Vx_out,
+             double *Vy_out)
 {
     int64_t *h = (int64_t *)malloc((size_t)nb * sizeof(int64_t));
-    double *V = (double *)malloc((size_t)nb * sizeof(double));
+    double *V = (double *)calloc((size_t)nb, sizeof(double));
+    double *Vx = (double *)calloc((size_t)nb, sizeof(double));
+    double *Vy = (double *)calloc((size_t)nb, sizeof(double));
+    double *D = (double *)malloc((size_t)nb * sizeof(double));
     double lmin, dl;
     int64_t na = o_wake_hist(x, alive, n, nb, &lmin, &dl, h);
     if (na > 0) {
-        o_wake_conv(h, nb, dl, w0, sc, charge / (double)n_total, V);
+        const double qm = charge / (double)n_total;
+        o_wake_conv(h, nb, dl, w0, sc, qm, V);
+        if (w0t != 0.0) {
+            o_wake_dipole(x, alive, n, nb, lmin, dl, 0, D);
+            o_wake_conv_t(D, nb, dl, w0t, sc, qm, Vx);
+            o_wake_dipole(x, alive, n, nb, lmin, dl, 2, D);
+            o_wake_conv_t(D, nb, dl, w0t, sc, qm, Vy);
+            for (int64_t i = 0; i < n; ++i) {
+                if (!alive[i]) continue;
+                double *z = x + 6 * i;
+                const double P = p0c * (1.0 + z[5]);
+                z[1] += o_wake_interp(Vx, nb, lmin, dl, z[4]) / P;
+                z[3] += o_wake_interp(Vy, nb, lmin, dl, z[4]) / P;
+            }
+        }
         o_wake_kick(x, alive, n, V, nb, lmin, dl, p0c);
-    } else {
-        memset(V, 0, (size_t)nb * sizeof(double));
     }
     if (hist_out) memcpy(hist_out, h, (size_t)nb * sizeof(int64_t));
     if (V_out) memcpy(V_out, V, (size_t)nb * sizeof(double));
+    if (Vx_out) memcpy(Vx_out, Vx, (size_t)nb * sizeof(double));
+    if (Vy_out) memcpy(Vy_out, Vy, (size_t)nb * sizeof(double));
     free(h);
     free(V);
+    free(Vx);
+    free(Vy);
+    free(D);
+}
+
+/* The longitudinal wake alone (w0t = 0). */
+void o_wake(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb,
+            double w0, double sc, double charge, double p0c, int64_t *hist_out, double *V_out)
+{
+    o_wake2(x, alive, n, n_total, nb, w0, 0.0, sc, charge, p0c, hist_out, V_out, NULL, NULL);
 }
 
 /* ------------------------------------------------------------ tracking ---- */
@@ -353,7 +425,8 @@ int64_t o_track(int ne, const int32_t *ei, const double *ed, const double *em,
             const double *dv = ed + ED_N * e;
             int type = iv[0];
             if (type == O_WAKE) {
-                o_wake(x, alive, n, n_total, iv[3], dv[ED_W0], dv[ED_SC], dv[ED_CHARGE], *p0c, NULL, NULL);
+                o_wake2(x, alive, n, n_total, iv[3], dv[ED_W0], dv[ED_W0T], dv[ED_SC], dv[ED_CHARGE], *p0c, NULL,
+                        NULL, NULL, NULL);
             } else if (type == O_RFCA) {
                 double phi = dv[ED_PHASE] * O_PI / 180.0;
                 double k = 2.0 * O_PI * dv[ED_FREQ] / C_LIGHT;
