@@ -310,8 +310,9 @@ void o_wake_kick(double *x, const uint8_t *alive, int64_t n, const double *V, in
 }
 
 /* Transverse dipole sums on the bins of o_wake_hist: D[k] = sum of coordinate
- * c (0 = x, 2 = y) over the alive particles of bin k, compensated sums in
- * particle order. */
+ * c (0 = x, 2 = y) over the alive particles of bin k whose coordinate is finite
+ * (a non-finite offset carries no dipole moment), compensated sums in particle
+ * order. */
 void o_wake_dipole(const double *x, const uint8_t *alive, int64_t n, int nb, double lmin, double dl, int c,
                    double *D)
 {
@@ -324,7 +325,7 @@ void o_wake_dipole(const double *x, const uint8_t *alive, int64_t n, int nb, dou
             if (b < 0) b = 0;
             if (b > nb - 1) b = nb - 1;
         }
-        nsum_add(&acc[b], x[6 * i + c]);
+        if (isfinite(x[6 * i + c])) nsum_add(&acc[b], x[6 * i + c]);
     }
     for (int k = 0; k < nb; ++k) D[k] = nsum_get(&acc[k]);
     free(acc);
