@@ -63,9 +63,10 @@ def parse():
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
     p.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi samples (default: temp dir)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train"],
-                   help="c2 (default, the headline line); c3 wake linac, c4 batched variants and the "
-                        "surrogate's inference (mlp) and training (mlp-train) print their own lines")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train", "sweep"],
+                   help="c2 (default, the headline line); c3 wake linac, c4 batched variants, the "
+                        "surrogate's inference (mlp) and training (mlp-train), and the particle-count "
+                        "sweep of the map ring (sweep) print their own lines")
     p.add_argument("--da-variants", type=int, default=64)
     p.add_argument("--rows", type=int, default=64 * 512 * 512, help="mlp: rows per inference call")
     p.add_argument("--epochs", type=int, default=24, help="mlp-train: epochs")
@@ -609,6 +610,50 @@ def run_mlp_train(args):
     return 0
 
 
+def run_sweep(args):
+    """Particle-count sweep of the c1 map ring (10 FODO cells, 40 order-2 or
+    order-3 maps, rectangle 20 mm): passes/s for N = 1e4 .. 1e8 particles, each
+    point about 1e8 particle-turns (turns = 1e8 / N, 1 to 1000) in one launch
+    configuration (block 128, 2 particles per thread, 100-turn chunks)."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import flops, trk
+    out = []
+    for order in (2, 3):
+        lat = syn.lattice_c1(order=order)
+        L = trk.trk_create_lattice(lat, moments=False)
+        f_pass = float(np.mean(flops.lattice_pass_flops(lat)))
+        for n in (10_000, 100_000, 1_000_000, 10_000_000, 100_000_000):
+            turns = int(min(1000, max(1, round(1e8 / n))))
+            g = torch.Generator(device="cuda").manual_seed(9)
+            coords = torch.zeros((6, n), dtype=torch.float64, device="cuda")
+            coords[0].normal_(0.0, 2e-4, generator=g)
+            coords[2].normal_(0.0, 1e-4, generator=g)
+            coords[5].normal_(0.0, 1e-3, generator=g)
+            ids = torch.arange(n, dtype=torch.int32, device="cuda")
+            b = trk.trk_bunch_wrap(coords, ids)
+            trk.trk_bunch_set_schedule(b, block=128, per_thread=2, chunk_turns=100)
+            trk.trk_track(b, L, 1)                      # warm-up (first launch, scratch allocation)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            trk.trk_track(b, L, turns)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            alive = trk.trk_n_alive(b)
+            passes = float(n) * turns * len(lat["elements"])   # counted as if all survive
+            out.append({"order": order, "particles": n, "turns": turns, "ms": ms,
+                        "passes_per_s": passes / (ms / 1e3),
+                        "tflops": passes * f_pass / (ms / 1e3) / 1e12, "alive_end": alive})
+            del b, coords, ids
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": "c1 map ring particle-count sweep (order 2 and 3 maps)", "metric": UNIT,
+                      "points": out}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -621,6 +666,8 @@ def main():
         return run_mlp(args)
     if args.workload == "mlp-train":
         return run_mlp_train(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
