@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--da-variants", type=int, default=64)
     p.add_argument("--rows", type=int, default=64 * 512 * 512, help="mlp: rows per inference call")
     p.add_argument("--epochs", type=int, default=24, help="mlp-train: epochs")
+    p.add_argument("--transverse", action="store_true", help="c3: add the transverse dipole wake")
     return p.parse_args()
 
 
@@ -471,9 +472,12 @@ def run_c3(args):
 
     import synthetic as syn
     from paper_1710_07350_gb300 import flops, trk
-    lat = syn.lattice_c3()
+    lat = syn.lattice_c3(transverse=args.transverse)
     L = trk.trk_create_lattice(lat)
     z0 = syn.bunch("c3")
+    if args.transverse:                       # an offset bunch, so that the dipole moments act
+        z0[:, 0] += 1.0e-4
+        z0[:, 2] -= 5.0e-5
     coords0, ids0 = trk.upload(z0)
     n = z0.shape[0]
     times = []
@@ -497,7 +501,10 @@ def run_c3(args):
     passes = n * len(lat["elements"])
     _, f = flops.step_work(lat, n, 1)
     f += n * 200 * flops.WAKE_FLOPS_PER_PARTICLE + 200 * flops.wake_conv_flops(syn.C3_NBINS)
-    print(json.dumps({"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins, drift, quad], 1e7 particles",
+    if args.transverse:
+        f += n * 200 * flops.TRWAKE_FLOPS_PER_PARTICLE + 200 * 2 * flops.wake_conv_flops(syn.C3_NBINS)
+    print(json.dumps({"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins%s, drift, quad], 1e7 particles"
+                                  % (" + transverse dipole wake, offset bunch" if args.transverse else ""),
                       "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
                       "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
                       "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, "launches": times[0][1]["launches"],

@@ -77,7 +77,14 @@ typedef enum {
                           counts h_j, V_k = -q_m sum_{j<=k} h_j W((k-j) dl) with
                           W(s) = w0 / sqrt(max(s, s_c)), q_m = charge / n,
                           delta += V(l) / p0c, V linearly interpolated between
-                          bin centres and clamped at the end bins */
+                          bin centres and clamped at the end bins.  With
+                          wake_w0t != 0 also the transverse dipole wake (Table 1
+                          TRWAKE, the transverse half of RFCW): per-bin sums
+                          D_j of x (and y) over alive particles with finite
+                          offsets, V_x,k = +q_m sum_{j<=k} D_j W_T((k-j) dl),
+                          x' += V_x(l) / (p0c (1 + delta)) (y likewise), applied
+                          before the energy kick; voltages from the particles
+                          entering the element */
 } trk_elem_type;
 
 typedef enum { TRK_APERTURE_NONE = 0, TRK_APERTURE_RECT = 1, TRK_APERTURE_ELLIPSE = 2 } trk_aperture;
@@ -99,6 +106,8 @@ typedef struct {
     double wake_w0;     /* V m^1/2 / C (TRK_WAKE) */
     double wake_sc;     /* m, saturation length s_c (TRK_WAKE) */
     double charge;      /* C, bunch charge (TRK_WAKE) */
+    double wake_w0t;    /* V m^-1/2 / C: transverse dipole wake
+                           W_T(s) = wake_w0t / sqrt(max(s, s_c)) (TRK_WAKE; 0 = none) */
     const double *C;    /* TRK_MAP: [6] or NULL (zero) */
     const double *R;    /* TRK_MAP: [6*6] row-major */
     const double *T;    /* TRK_MAP: [6*21], (j,k) j<=k lexicographic, or NULL */

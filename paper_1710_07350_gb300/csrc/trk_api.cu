@@ -51,6 +51,7 @@ struct trk_lattice {
     double p0c = 0.0;
     std::vector<int> wakes;  // element indices of TRK_WAKE
     int max_bins = 0;
+    bool transverse = false; // a wake with a transverse part
 };
 
 struct trk_bunch {
@@ -73,6 +74,8 @@ struct trk_bunch {
     int moments_cap = 0, moments_turns = 0;
     uint32_t *hist = nullptr;
     double *wfun = nullptr, *V = nullptr;
+    unsigned long long *dip = nullptr;            // transverse dipole sums [2][bins], fixed point
+    double *wfun_t = nullptr, *Vt = nullptr;      // transverse wake samples, voltages [2][bins]
     int wake_cap = 0;
     int64_t turn = 0;
     double p0c = 0.0;
@@ -235,9 +238,15 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             }
             E.n = d.nbins;
             E.term0 = (int32_t)L->wakes.size();
+            if (!std::isfinite(d.wake_w0) || !std::isfinite(d.wake_w0t) || !(d.wake_sc > 0.0)) {
+                s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": bad wake parameters");
+                break;
+            }
             E.p[0] = d.wake_w0;
             E.p[1] = d.wake_sc;
             E.p[2] = d.charge;
+            E.p[3] = d.wake_w0t;
+            if (d.wake_w0t != 0.0) L->transverse = true;
             L->wakes.push_back(i);
             if (d.nbins > L->max_bins) L->max_bins = d.nbins;
             break;
@@ -318,6 +327,9 @@ static void free_bunch_scratch(trk_bunch *b) {
     cudaFree(b->hist);
     cudaFree(b->wfun);
     cudaFree(b->V);
+    cudaFree(b->dip);
+    cudaFree(b->wfun_t);
+    cudaFree(b->Vt);
 }
 
 extern "C" trk_status trk_bunch_wrap(double *d_coords, int64_t pitch, int32_t *d_id, int64_t n, void *stream,
@@ -431,18 +443,26 @@ static trk_status ensure_moments(trk_bunch *b, int n_turns, int n_tiles, int chu
     return TRK_OK;
 }
 
-static trk_status ensure_wake(trk_bunch *b, int nbins) {
-    if (nbins <= b->wake_cap) return TRK_OK;
+static trk_status ensure_wake(trk_bunch *b, int nbins, bool transverse) {
+    if (nbins <= b->wake_cap && (!transverse || b->dip)) return TRK_OK;
+    const int cap = nbins > b->wake_cap ? nbins : b->wake_cap;
     cudaFree(b->hist);
     cudaFree(b->wfun);
     cudaFree(b->V);
+    cudaFree(b->dip);
+    cudaFree(b->wfun_t);
+    cudaFree(b->Vt);
     b->hist = nullptr;
-    b->wfun = b->V = nullptr;
+    b->wfun = b->V = b->wfun_t = b->Vt = nullptr;
+    b->dip = nullptr;
     b->wake_cap = 0;
-    if (dalloc(&b->hist, nbins) != cudaSuccess || dalloc(&b->wfun, nbins) != cudaSuccess ||
-        dalloc(&b->V, nbins) != cudaSuccess)
+    if (dalloc(&b->hist, cap) != cudaSuccess || dalloc(&b->wfun, cap) != cudaSuccess ||
+        dalloc(&b->V, cap) != cudaSuccess)
         return fail(TRK_ENOMEM, "wake scratch allocation failed");
-    b->wake_cap = nbins;
+    if (transverse && (dalloc(&b->dip, 2 * (size_t)cap) != cudaSuccess || dalloc(&b->wfun_t, cap) != cudaSuccess ||
+                       dalloc(&b->Vt, 2 * (size_t)cap) != cudaSuccess))
+        return fail(TRK_ENOMEM, "transverse wake scratch allocation failed");
+    b->wake_cap = cap;
     return TRK_OK;
 }
 
@@ -513,7 +533,7 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
         if (s != TRK_OK) return s;
     }
     if (wakes) {
-        trk_status s = ensure_wake(b, L->max_bins);
+        trk_status s = ensure_wake(b, L->max_bins, L->transverse);
         if (s != TRK_OK) return s;
     }
     const int ne = L->view.n_elem;
@@ -548,21 +568,30 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                     g.kick_wake = prev_wake;
                     g.kick_slot = prev_slot;
                     g.wake_nbins = prev_wake >= 0 ? L->elems[prev_wake].n : 0;
+                    g.wake_Vx = prev_wake >= 0 && L->elems[prev_wake].p[3] != 0.0 ? b->Vt : nullptr;
                     g.minmax_slot = s < nw ? slot : -1;
                     g.do_moments = L->moments && s == nw;
                     g.p0c = p0;
                     if (s < nw) {
-                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist, L->elems[e_end].n, b->stream));
+                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist,
+                                                   L->elems[e_end].p[3] != 0.0 ? b->dip : nullptr,
+                                                   L->elems[e_end].n, b->stream));
                         ++b->launches;
                     }
                     TRK_CUDA(track_launch(b, g, n_tiles));
                     p0 = advance_p0(L, e_start, e_end, p0);
                     if (s < nw) {
                         const DevElem &W = L->elems[e_end];
+                        const bool tr = W.p[3] != 0.0;
                         TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, W.p[0], W.p[1],
-                                                  b->hist, b->wfun, b->n, b->stream));
+                                                  b->hist, b->wfun, W.p[3], tr ? b->dip : nullptr, b->wfun_t, b->n,
+                                                  b->stream));
                         TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, b->V, b->stream));
                         b->launches += 2;
+                        if (tr) {
+                            TRK_CUDA(launch_wake_conv_t(b->dip, b->wfun_t, W.n, W.p[2] * qm_base, b->Vt, b->stream));
+                            ++b->launches;
+                        }
                     }
                     prev_wake = e_end;
                     prev_slot = slot;
@@ -628,12 +657,12 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     if (nbins < 1 || nbins > kMaxBins) return fail(TRK_EINVAL, "trk_wake: nbins must be 1..65536");
     if (!(p0c_ev > 0.0)) return fail(TRK_EINVAL, "trk_wake: p0c_ev must be > 0");
     if (b->n == 0) return TRK_OK;
-    trk_status s = ensure_wake(b, nbins);
+    trk_status s = ensure_wake(b, nbins, false);
     if (s != TRK_OK) return s;
-    TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nbins, b->stream));
+    TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nullptr, nbins, b->stream));
     TRK_CUDA(launch_wake_minmax(b->coords, b->pitch, b->lt, b->st, 0, b->n, b->stream));
-    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, 0, nbins, w0, sc, b->hist, b->wfun, b->n,
-                              b->stream));
+    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, 0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
+                              nullptr, b->n, b->stream));
     TRK_CUDA(launch_wake_conv(b->hist, b->wfun, nbins, charge / (double)b->n, b->V, b->stream));
     const int tile = b->block * b->per_thread;
     const int n_tiles = (int)((b->n + tile - 1) / tile);

@@ -23,7 +23,8 @@ constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
 //   EDRIFT       p[0] L, p[1] L / 2, p[2] 3 L / 8
 //   THINSEXT     p[0] K2L, p[1] K2L / 2
 //   RFCA         p[0] V, p[1] phi [rad], p[2] k_rf = 2 pi f / c, p[3] G = V cos(phi)
-//   WAKE         p[0] W0, p[1] s_c, p[2] charge; n = nbins; term0 = wake ordinal
+//   WAKE         p[0] W0, p[1] s_c, p[2] charge, p[3] W0T (transverse, 0 = none);
+//                n = nbins; term0 = wake ordinal
 //   MAP          term0 = first term; rb[r]..rb[r+1] = terms of output row r;
 //                flags bit r (r < 6) = row r starts from x_r (R_rr == 1 folded);
 //                flags bit 6 = row 5 (delta) changes
@@ -84,6 +85,7 @@ struct TrackArgs {
     double *partials;       // [turn][tile][28]
     int32_t *tile_alive;    // alive count per tile at the end (may be null)
     const double *wake_V;   // voltages of the kicking wake
+    const double *wake_Vx;  // its transverse voltages (x then y, 2 x nbins), or null
     int32_t wake_nbins;
     int32_t tile;           // particles per tile (block * per_thread)
     double *mom_out;        // finalised moments of this launch's first turn (batched path)
@@ -114,13 +116,21 @@ cudaError_t launch_batch_chunk(const TrackArgs *args, const CompactArgs *cargs, 
                                int n_var, int n_chunks, int chunk, int block, int per_thread, int tile,
                                int max_turns, bool moments, cudaStream_t s);
 cudaError_t launch_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n, cudaStream_t s);
-cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, int nbins, cudaStream_t s);
+// Transverse dipole sums are 64-bit fixed point, 2^-40 m per unit.
+constexpr double kDipoleScale = 1099511627776.0;   // 2^40 per metre
+cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins,
+                              cudaStream_t s);
 cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
                                int slot, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot, int nbins,
-                             double w0, double sc, uint32_t *hist, double *wfun, int64_t n_max, cudaStream_t s);
+                             double w0, double sc, uint32_t *hist, double *wfun, double w0t, unsigned long long *dip,
+                             double *wfun_t, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
                              cudaStream_t s);
+// Transverse voltages V_c[k] = q_m sum_{j<=k} D_c[j] W_T((k - j) dl) for c = x, y
+// (dip[c * nbins + j] fixed point, V[c * nbins + k]).
+cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
+                               cudaStream_t s);
 
 // Dynamic-aperture helpers (trk_da.cu).
 // tcgen05 surrogate inference layers (trk_mlp_umma.cu); BF16 passed as uint16_t.

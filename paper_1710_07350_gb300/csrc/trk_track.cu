@@ -346,7 +346,6 @@ __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, b
     return fma(f, v1 - v0, v0);
 }
 
-// Aperture: edge counts as inside, NaN as outside.
 // -------------------------------------------------------- block sums ----
 // Sum 28 per-thread values over the block; the totals land in tot[0..27].
 __device__ __forceinline__ void block_sum28(double (&v)[kMomentsN], double *sh, double *tot) {
@@ -547,6 +546,17 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             const bool flat = !(dl > 0.0);
             const double idl = flat ? 0.0 : 1.0 / dl;
             const double ip0 = 1.0 / p0;
+            if (a.wake_Vx) {
+                // transverse kicks first: slopes change by V_x / P, V_y / P with P = p0 (1 + delta)
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (!alive[p]) continue;
+                    const double iP = ip0 / (1.0 + q.d[p]);
+                    q.xp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_Vx, a.wake_nbins), iP, q.xp[p]);
+                    q.yp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_Vx + a.wake_nbins, a.wake_nbins), iP,
+                                  q.yp[p]);
+                }
+            }
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q.d[p]);

@@ -29,6 +29,13 @@ MOMENTS_FLOPS = 54
 WAKE_FLOPS_PER_PARTICLE = 14
 
 
+# Transverse part of a wake element per alive particle: the x and y dipole sums
+# (2 adds), 1 / (p0c (1 + delta)) (add, multiply, divide: 3), two interpolated
+# voltages (sub, 2 for the interpolation each, shared bin index: 5) and two
+# slope kicks (FMA each: 4) -> 14; plus two nbins^2/2 convolutions per wake.
+TRWAKE_FLOPS_PER_PARTICLE = 14
+
+
 def wake_conv_flops(nbins):
     return float(nbins) * (nbins + 1)
 

@@ -32,7 +32,7 @@ class trk_element_desc(ctypes.Structure):
     _fields_ = [("type", c_int32), ("order", c_int32), ("n_kicks", c_int32), ("nbins", c_int32),
                 ("length", c_double), ("k1", c_double), ("k2", c_double), ("k2l", c_double),
                 ("volt", c_double), ("phase_deg", c_double), ("freq_hz", c_double),
-                ("wake_w0", c_double), ("wake_sc", c_double), ("charge", c_double),
+                ("wake_w0", c_double), ("wake_sc", c_double), ("charge", c_double), ("wake_w0t", c_double),
                 ("C", PD), ("R", PD), ("T", PD), ("U", PD)]
 
 
@@ -179,6 +179,7 @@ def trk_create_lattice(lattice, moments=True):
             d.volt, d.phase_deg, d.freq_hz = el["volt"], el["phase_deg"], el["freq_hz"]
         elif t == "WAKE":
             d.nbins, d.wake_w0, d.wake_sc, d.charge = el["nbins"], el["W0"], el["sc"], el["charge"]
+            d.wake_w0t = el.get("W0T", 0.0)
         else:
             raise ValueError(t)
     o = trk_lattice_opts()

@@ -41,6 +41,10 @@ C3_PERIODS, C3_VOLT, C3_PHASE, C3_FREQ = 200, 20.0e6, -10.0, 2.856e9
 C3_NBINS, C3_W0, C3_CHARGE = 4096, 4.0e11, 250e-12
 C3_SIGMA_L = 100e-6
 C3_SC = 0.1 * C3_SIGMA_L
+# transverse dipole wake of the linac variant with transverse wakes: about
+# 1e-6 rad per cavity behind a bunch offset by 100 um (a readable kick, not a
+# physical structure)
+C3_W0T = 1.0e15
 K2L_THIN = K2_SEXT * L_SEXT
 # c5 names no sextupole strength; 10x the c4 value makes the DA sextupole-limited
 # inside the +-20 mm aperture (with K2L_THIN it is the aperture rectangle).
@@ -102,9 +106,10 @@ def lattice_c2(cells=C2_CELLS, rf=True):
     return {"name": "c2", "elements": els, "aperture": ("ellipse", 0.015, 0.008), "p0c": P0C_1GEV}
 
 
-def lattice_c3(periods=C3_PERIODS, nbins=C3_NBINS):
+def lattice_c3(periods=C3_PERIODS, nbins=C3_NBINS, transverse=False):
     rf = {"type": "RFCA", "volt": C3_VOLT, "phase_deg": C3_PHASE, "freq_hz": C3_FREQ}
-    wk = {"type": "WAKE", "nbins": nbins, "W0": C3_W0, "sc": C3_SC, "charge": C3_CHARGE}
+    wk = {"type": "WAKE", "nbins": nbins, "W0": C3_W0, "sc": C3_SC, "charge": C3_CHARGE,
+          "W0T": C3_W0T if transverse else 0.0}
     dr = _map_elem("D1.0.o2")
     qf, qd = _map_elem("QF.o2"), _map_elem("QD.o2")
     els = []

@@ -81,3 +81,39 @@ def test_wake_last_and_first_element():
     o = orc.track(lat, z, 2)
     err = compare_tracking(g, o, TOL_PASS * 10)
     compare_moments(g["moments"], o["moments"], coord_err=err)
+
+
+def offset_bunch(n, seed=3):
+    z = syn.bunch("c3", n=n, seed=seed)
+    z[:, 0] += 1.0e-4
+    z[:, 2] -= 5.0e-5
+    return z
+
+
+def test_transverse_wake_linac_reduced():
+    """Linac periods with longitudinal and transverse wakes on an offset bunch:
+    coordinates after one pass and the per-pass moments against the oracle."""
+    lat = syn.lattice_c3(periods=6, nbins=512, transverse=True)
+    z = offset_bunch(20_000)
+    g = gpu_track(lat, z, 1, schedule={"block": 128, "per_thread": 2})
+    o = orc.track(lat, z, 1)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
+    # the transverse wake acts: the mean slope differs from the run without it
+    o0 = orc.track(syn.lattice_c3(periods=6, nbins=512), z, 1)
+    assert abs(o["moments"][-1, 2] - o0["moments"][-1, 2]) > 1e-9
+
+
+@pytest.mark.parametrize("nbins", [4096, 6000])
+def test_transverse_wake_single_element(nbins):
+    """One wake element with a transverse part, shared-memory dipole sums
+    (4096 bins) and global ones (6000 bins), against the oracle."""
+    wk = {"type": "WAKE", "nbins": nbins, "W0": syn.C3_W0, "sc": syn.C3_SC, "charge": syn.C3_CHARGE,
+          "W0T": syn.C3_W0T}
+    lat = {"elements": [wk, {"type": "EDRIFT", "L": 0.5}], "aperture": None, "p0c": 2.0e9}
+    z = offset_bunch(50_000, seed=7)
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    compare_tracking(g, o, TOL_PASS)
+    oz, _, _, Vx, Vy = orc.wake2(z, nbins, syn.C3_W0, syn.C3_W0T, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
+    assert np.max(np.abs(Vx)) > 0 and np.max(np.abs(Vy)) > 0
