@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "trk_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
-TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7}
+TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8}
 APERTURES = {None: 0, "rect": 1, "ellipse": 2}
 ED_N, EM_N = 16, 504
 
@@ -56,6 +56,11 @@ def lib():
         L.o_wake2.restype = None
         L.o_wake2.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]
+        L.o_lsc.restype = None
+        L.o_lsc.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                            ctypes.c_double, ctypes.c_double, P, P]
+        L.o_lsc_field.restype = None
+        L.o_lsc_field.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         L.o_wake_dipole.restype = None
         L.o_wake_dipole.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, P]
@@ -98,6 +103,9 @@ def lattice_arrays(lat):
             ei[e, 3] = el["nbins"]
             ed[e, 6], ed[e, 7], ed[e, 8] = el["W0"], el["sc"], el["charge"]
             ed[e, 10] = el.get("W0T", 0.0)
+        elif t == "LSC":
+            ei[e, 3], ei[e, 1] = el["nbins"], el.get("passes", 0)
+            ed[e, 0], ed[e, 11], ed[e, 8] = el["L"], el["K"], el["charge"]
         else:
             raise ValueError(t)
     return ei, ed, em
@@ -183,6 +191,25 @@ def wake2(z, nbins, w0, w0t, sc, charge, p0c, alive=None, n_total=None):
     lib().o_wake2(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, w0, w0t, sc, charge, p0c,
                   _p(h), _p(V), _p(Vx), _p(Vy))
     return z, h, V, Vx, Vy
+
+
+def lsc(z, nbins, KL, passes, charge, p0c, alive=None, n_total=None):
+    """One space-charge kick on a copy of z; returns (z, hist, V)."""
+    z = np.array(z, dtype=np.float64, order="C", copy=True)
+    n = z.shape[0]
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    V = np.zeros(nbins)
+    lib().o_lsc(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, KL, passes, charge, p0c, _p(h),
+                _p(V))
+    return z, h, V
+
+
+def lsc_field(hist, dl, qm, KL, passes):
+    h = np.ascontiguousarray(hist, np.int64)
+    V = np.zeros(len(h))
+    lib().o_lsc_field(_p(h), len(h), dl, qm, KL, passes, _p(V))
+    return V
 
 
 def wake_dipole(z, nbins, coord, alive=None):

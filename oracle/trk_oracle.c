@@ -28,11 +28,16 @@
  *     linearly interpolated energy kick;
  *   - transverse dipole wake on the same bins (Table 1 TRWAKE, the transverse
  *     half of RFCW): per-bin sums of x and y, convolution with
- *     W_T(s) = W0T/sqrt(max(s, s_c)), interpolated kicks on x' and y'.
+ *     W_T(s) = W0T/sqrt(max(s, s_c)), interpolated kicks on x' and y';
+ *   - longitudinal space charge (Table 1 LSCDRIFT) in the long-wavelength limit
+ *     (impedance proportional to i k): the same histogram as a line density,
+ *     smoothed by repeated 1-2-1 passes, differentiated, energy kick
+ *     delta += K L (d lambda / d l)(l) / p0c.
  *
  * Coordinates: (x, x', y, y', l, delta), l the path-length deviation [m].
  * Lattice description: one row per element in three flat arrays
- *   ei[4*e + 0..3]  = type, order (MAP), n_kicks (KQUAD/KSEXT), nbins (WAKE)
+ *   ei[4*e + 0..3]  = type, order (MAP) or smoothing passes (LSC), n_kicks (KQUAD/KSEXT),
+ *                     nbins (WAKE, LSC)
  *   ed[16*e + ...]  = see ED_* below
  *   em[504*e + ...] = C[6], R[36] (row-major), T[6*21], U[6*56] (MAP only)
  */
@@ -41,10 +46,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7 };
+enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7, O_LSC = 8 };
 enum { O_AP_NONE = 0, O_AP_RECT = 1, O_AP_ELLIPSE = 2 };
 enum { ED_LENGTH = 0, ED_K1 = 1, ED_K2 = 2, ED_VOLT = 3, ED_PHASE = 4, ED_FREQ = 5,
-       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_N = 16 };
+       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_KLSC = 11, ED_N = 16 };
 #define EM_N 504
 #define C_LIGHT 299792458.0
 #define O_PI 3.14159265358979323846
@@ -400,6 +405,61 @@ void o_wake(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb,
     o_wake2(x, alive, n, n_total, nb, w0, 0.0, sc, charge, p0c, hist_out, V_out, NULL, NULL);
 }
 
+/* --------------------------------------------------- space charge ---- */
+
+/* Field of the long-wavelength space charge on the bins of o_wake_hist:
+ * lambda_k = q_m h_k / dl (C/m); `passes` times lambda_k <- (lambda_{k-1} +
+ * 2 lambda_k + lambda_{k+1}) / 4 with the end bins repeated outside; then
+ * d_k = (lambda_{k+1} - lambda_{k-1}) / (2 dl) inside, one-sided differences
+ * at the two ends; V_k = KL d_k (V).  dl == 0 or nb == 1: V = 0. */
+void o_lsc_field(const int64_t *hist, int nb, double dl, double qm, double KL, int passes, double *V)
+{
+    if (!(dl > 0.0) || nb < 2) {
+        memset(V, 0, (size_t)nb * sizeof(double));
+        return;
+    }
+    double *a = (double *)malloc((size_t)nb * sizeof(double));
+    double *b = (double *)malloc((size_t)nb * sizeof(double));
+    for (int k = 0; k < nb; ++k) a[k] = qm * (double)hist[k] / dl;
+    for (int p = 0; p < passes; ++p) {
+        for (int k = 0; k < nb; ++k) {
+            double lo = a[k > 0 ? k - 1 : 0], hi = a[k < nb - 1 ? k + 1 : nb - 1];
+            b[k] = (lo + 2.0 * a[k] + hi) / 4.0;
+        }
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    for (int k = 0; k < nb; ++k) {
+        double d;
+        if (k == 0) d = (a[1] - a[0]) / dl;
+        else if (k == nb - 1) d = (a[nb - 1] - a[nb - 2]) / dl;
+        else d = (a[k + 1] - a[k - 1]) / (2.0 * dl);
+        V[k] = KL * d;
+    }
+    free(a);
+    free(b);
+}
+
+/* Whole space-charge element (a thin kick of effective length L);
+ * hist_out / V_out may be NULL. */
+void o_lsc(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb, double KL, int passes,
+           double charge, double p0c, int64_t *hist_out, double *V_out)
+{
+    int64_t *h = (int64_t *)malloc((size_t)nb * sizeof(int64_t));
+    double *V = (double *)calloc((size_t)nb, sizeof(double));
+    double lmin, dl;
+    int64_t na = o_wake_hist(x, alive, n, nb, &lmin, &dl, h);
+    if (na > 0) {
+        o_lsc_field(h, nb, dl, charge / (double)n_total, KL, passes, V);
+        o_wake_kick(x, alive, n, V, nb, lmin, dl, p0c);
+    }
+    if (hist_out) memcpy(hist_out, h, (size_t)nb * sizeof(int64_t));
+    if (V_out) memcpy(V_out, V, (size_t)nb * sizeof(double));
+    free(h);
+    free(V);
+}
+
 /* ------------------------------------------------------------ tracking ---- */
 
 /*
@@ -428,6 +488,9 @@ int64_t o_track(int ne, const int32_t *ei, const double *ed, const double *em,
             if (type == O_WAKE) {
                 o_wake2(x, alive, n, n_total, iv[3], dv[ED_W0], dv[ED_W0T], dv[ED_SC], dv[ED_CHARGE], *p0c, NULL,
                         NULL, NULL, NULL);
+            } else if (type == O_LSC) {
+                o_lsc(x, alive, n, n_total, iv[3], dv[ED_KLSC] * dv[ED_LENGTH], iv[1], dv[ED_CHARGE], *p0c, NULL,
+                      NULL);
             } else if (type == O_RFCA) {
                 double phi = dv[ED_PHASE] * O_PI / 180.0;
                 double k = 2.0 * O_PI * dv[ED_FREQ] / C_LIGHT;
