@@ -72,7 +72,7 @@ typedef enum {
                           simple_rf_cavity): dE = V cos(phi + 2 pi f l / c),
                           P' = P + dE, p0' = p0 + V cos(phi),
                           delta' = P'/p0' - 1, x' and y' scaled by P/P' */
-    TRK_WAKE = 7       /* longitudinal wake (Table 1 WAKE; Sec. 2.2-2.3): l-window
+    TRK_WAKE = 7,      /* longitudinal wake (Table 1 WAKE; Sec. 2.2-2.3): l-window
                           [min, max] over alive particles, nbins equal bins,
                           counts h_j, V_k = -q_m sum_{j<=k} h_j W((k-j) dl) with
                           W(s) = w0 / sqrt(max(s, s_c)), q_m = charge / n,
@@ -85,6 +85,14 @@ typedef enum {
                           x' += V_x(l) / (p0c (1 + delta)) (y likewise), applied
                           before the energy kick; voltages from the particles
                           entering the element */
+    TRK_LSC = 8        /* longitudinal space charge (Table 1 LSCDRIFT) in the
+                          long-wavelength limit, a thin kick of effective length
+                          `length`: on the bins of TRK_WAKE, line density
+                          lambda_k = q_m h_k / dl, n_kicks passes of
+                          lambda_k <- (lambda_{k-1} + 2 lambda_k + lambda_{k+1}) / 4
+                          (end bins repeated), d_k = central difference (one-sided
+                          at the ends), delta += lsc_k length d(l) / p0c with d
+                          interpolated as the wake voltage */
 } trk_elem_type;
 
 typedef enum { TRK_APERTURE_NONE = 0, TRK_APERTURE_RECT = 1, TRK_APERTURE_ELLIPSE = 2 } trk_aperture;
@@ -94,8 +102,9 @@ typedef enum { TRK_APERTURE_NONE = 0, TRK_APERTURE_RECT = 1, TRK_APERTURE_ELLIPS
 typedef struct {
     int32_t type;       /* trk_elem_type */
     int32_t order;      /* TRK_MAP: 1, 2 or 3 (U ignored below 3, T below 2) */
-    int32_t n_kicks;    /* TRK_KQUAD / TRK_KSEXT: Yoshida-4 steps (>= 1) */
-    int32_t nbins;      /* TRK_WAKE: histogram bins (1 .. 65536) */
+    int32_t n_kicks;    /* TRK_KQUAD / TRK_KSEXT: Yoshida-4 steps (>= 1);
+                           TRK_LSC: smoothing passes (0 .. 1000) */
+    int32_t nbins;      /* TRK_WAKE, TRK_LSC: histogram bins (1 .. 65536) */
     double length;      /* m (TRK_EDRIFT, TRK_KQUAD, TRK_KSEXT) */
     double k1;          /* m^-2 (TRK_KQUAD, TRK_KSEXT) */
     double k2;          /* m^-3 (TRK_KSEXT) */
@@ -108,6 +117,8 @@ typedef struct {
     double charge;      /* C, bunch charge (TRK_WAKE) */
     double wake_w0t;    /* V m^-1/2 / C: transverse dipole wake
                            W_T(s) = wake_w0t / sqrt(max(s, s_c)) (TRK_WAKE; 0 = none) */
+    double lsc_k;       /* V m / C per m of length: space-charge factor g / (4 pi eps0 gamma^2)
+                           (TRK_LSC; uses length, nbins, charge, n_kicks) */
     const double *C;    /* TRK_MAP: [6] or NULL (zero) */
     const double *R;    /* TRK_MAP: [6*6] row-major */
     const double *T;    /* TRK_MAP: [6*21], (j,k) j<=k lexicographic, or NULL */

@@ -76,6 +76,7 @@ struct trk_bunch {
     double *wfun = nullptr, *V = nullptr;
     unsigned long long *dip = nullptr;            // transverse dipole sums [2][bins], fixed point
     double *wfun_t = nullptr, *Vt = nullptr;      // transverse wake samples, voltages [2][bins]
+    double *lsc = nullptr;                        // space-charge smoothing scratch [bins]
     int wake_cap = 0;
     int64_t turn = 0;
     double p0c = 0.0;
@@ -231,6 +232,20 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             E.p[3] = d.volt * std::cos(phi);
             break;
         }
+        case TRK_LSC:
+            if (d.nbins < 1 || d.nbins > kMaxBins || d.n_kicks < 0 || d.n_kicks > 1000 ||
+                !std::isfinite(d.lsc_k) || !std::isfinite(d.length) || !std::isfinite(d.charge)) {
+                s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": bad space-charge parameters");
+                break;
+            }
+            E.n = d.nbins;
+            E.flags = (uint32_t)d.n_kicks;
+            E.term0 = (int32_t)L->wakes.size();
+            E.p[2] = d.charge;
+            E.p[4] = d.lsc_k * d.length;
+            L->wakes.push_back(i);
+            if (d.nbins > L->max_bins) L->max_bins = d.nbins;
+            break;
         case TRK_WAKE:
             if (d.nbins < 1 || d.nbins > kMaxBins) {
                 s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": nbins must be 1..65536");
@@ -330,6 +345,7 @@ static void free_bunch_scratch(trk_bunch *b) {
     cudaFree(b->dip);
     cudaFree(b->wfun_t);
     cudaFree(b->Vt);
+    cudaFree(b->lsc);
 }
 
 extern "C" trk_status trk_bunch_wrap(double *d_coords, int64_t pitch, int32_t *d_id, int64_t n, void *stream,
@@ -452,12 +468,13 @@ static trk_status ensure_wake(trk_bunch *b, int nbins, bool transverse) {
     cudaFree(b->dip);
     cudaFree(b->wfun_t);
     cudaFree(b->Vt);
+    cudaFree(b->lsc);
     b->hist = nullptr;
-    b->wfun = b->V = b->wfun_t = b->Vt = nullptr;
+    b->wfun = b->V = b->wfun_t = b->Vt = b->lsc = nullptr;
     b->dip = nullptr;
     b->wake_cap = 0;
     if (dalloc(&b->hist, cap) != cudaSuccess || dalloc(&b->wfun, cap) != cudaSuccess ||
-        dalloc(&b->V, cap) != cudaSuccess)
+        dalloc(&b->V, cap) != cudaSuccess || dalloc(&b->lsc, cap) != cudaSuccess)
         return fail(TRK_ENOMEM, "wake scratch allocation failed");
     if (transverse && (dalloc(&b->dip, 2 * (size_t)cap) != cudaSuccess || dalloc(&b->wfun_t, cap) != cudaSuccess ||
                        dalloc(&b->Vt, 2 * (size_t)cap) != cudaSuccess))
@@ -568,13 +585,18 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                     g.kick_wake = prev_wake;
                     g.kick_slot = prev_slot;
                     g.wake_nbins = prev_wake >= 0 ? L->elems[prev_wake].n : 0;
-                    g.wake_Vx = prev_wake >= 0 && L->elems[prev_wake].p[3] != 0.0 ? b->Vt : nullptr;
+                    g.wake_Vx = prev_wake >= 0 && L->elems[prev_wake].type == TRK_WAKE &&
+                                        L->elems[prev_wake].p[3] != 0.0
+                                    ? b->Vt
+                                    : nullptr;
                     g.minmax_slot = s < nw ? slot : -1;
                     g.do_moments = L->moments && s == nw;
                     g.p0c = p0;
                     if (s < nw) {
                         TRK_CUDA(launch_wake_reset(b->st, slot, b->hist,
-                                                   L->elems[e_end].p[3] != 0.0 ? b->dip : nullptr,
+                                                   L->elems[e_end].type == TRK_WAKE && L->elems[e_end].p[3] != 0.0
+                                                       ? b->dip
+                                                       : nullptr,
                                                    L->elems[e_end].n, b->stream));
                         ++b->launches;
                     }
@@ -582,11 +604,16 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                     p0 = advance_p0(L, e_start, e_end, p0);
                     if (s < nw) {
                         const DevElem &W = L->elems[e_end];
-                        const bool tr = W.p[3] != 0.0;
-                        TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, W.p[0], W.p[1],
-                                                  b->hist, b->wfun, W.p[3], tr ? b->dip : nullptr, b->wfun_t, b->n,
-                                                  b->stream));
-                        TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, b->V, b->stream));
+                        const bool lsc = W.type == TRK_LSC;
+                        const bool tr = !lsc && W.p[3] != 0.0;
+                        TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, lsc ? 0.0 : W.p[0],
+                                                  lsc ? 1.0 : W.p[1], b->hist, b->wfun, lsc ? 0.0 : W.p[3],
+                                                  tr ? b->dip : nullptr, b->wfun_t, b->n, b->stream));
+                        if (lsc)
+                            TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
+                                                      (int)W.flags, b->wfun, b->lsc, b->V, b->stream));
+                        else
+                            TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, b->V, b->stream));
                         b->launches += 2;
                         if (tr) {
                             TRK_CUDA(launch_wake_conv_t(b->dip, b->wfun_t, W.n, W.p[2] * qm_base, b->Vt, b->stream));

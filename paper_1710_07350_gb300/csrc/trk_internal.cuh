@@ -25,6 +25,8 @@ constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
 //   RFCA         p[0] V, p[1] phi [rad], p[2] k_rf = 2 pi f / c, p[3] G = V cos(phi)
 //   WAKE         p[0] W0, p[1] s_c, p[2] charge, p[3] W0T (transverse, 0 = none);
 //                n = nbins; term0 = wake ordinal
+//   LSC          p[2] charge, p[4] K L; n = nbins; flags = smoothing passes;
+//                term0 = wake ordinal (kicked like a wake)
 //   MAP          term0 = first term; rb[r]..rb[r+1] = terms of output row r;
 //                flags bit r (r < 6) = row r starts from x_r (R_rr == 1 folded);
 //                flags bit 6 = row 5 (delta) changes
@@ -129,6 +131,10 @@ cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins
                              cudaStream_t s);
 // Transverse voltages V_c[k] = q_m sum_{j<=k} D_c[j] W_T((k - j) dl) for c = x, y
 // (dip[c * nbins + j] fixed point, V[c * nbins + k]).
+// Long-wavelength space-charge field on the bins of slot `slot`:
+// V_k = KL d_k (see TRK_LSC); a, b scratch of nbins doubles.
+cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double KL,
+                             int passes, double *a, double *b, double *V, cudaStream_t s);
 cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
                                cudaStream_t s);
 

@@ -221,6 +221,42 @@ __global__ void __launch_bounds__(kConvThreads) k_wake_conv_t(const unsigned lon
     }
 }
 
+// One block: line density, `passes` 1-2-1 smoothing passes, central
+// difference; every operation rounded as written (no contraction), so the field
+// is the oracle's on identical counts.
+__global__ void __launch_bounds__(1024) k_lsc_field(const uint32_t *__restrict__ hist, const BunchState *st, int slot,
+                                                    int nbins, double qm, double KL, int passes, double *a, double *b,
+                                                    double *__restrict__ V) {
+    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const bool any = kmin <= kmax;
+    const double lmin = any ? dkey_inv(kmin) : 0.0;
+    const double lmax = any ? dkey_inv(kmax) : 0.0;
+    const double dl = (lmax - lmin) / nbins;
+    if (!any || !(dl > 0.0) || nbins < 2) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = 0.0;
+        return;
+    }
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) a[k] = __ddiv_rn(__dmul_rn(qm, (double)hist[k]), dl);
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) {
+            const double lo = a[k > 0 ? k - 1 : 0], hi = a[k < nbins - 1 ? k + 1 : nbins - 1];
+            b[k] = __dmul_rn(__dadd_rn(__dadd_rn(lo, __dmul_rn(2.0, a[k])), hi), 0.25);
+        }
+        __syncthreads();
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) {
+        double d;
+        if (k == 0) d = __ddiv_rn(__dsub_rn(a[1], a[0]), dl);
+        else if (k == nbins - 1) d = __ddiv_rn(__dsub_rn(a[nbins - 1], a[nbins - 2]), dl);
+        else d = __ddiv_rn(__dsub_rn(a[k + 1], a[k - 1]), __dmul_rn(2.0, dl));
+        V[k] = __dmul_rn(KL, d);
+    }
+}
+
 int grid_for(int64_t n, int threads, int cap) {
     int64_t g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
@@ -266,6 +302,12 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
     if (g < gw) g = gw;
     k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, slot, nbins, w0, sc, hist, wfun, w0t, dip,
                                               wfun_t, smem_ok ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double KL,
+                             int passes, double *a, double *b, double *V, cudaStream_t s) {
+    k_lsc_field<<<1, 1024, 0, s>>>(hist, st, slot, nbins, qm, KL, passes, a, b, V);
     return cudaGetLastError();
 }
 

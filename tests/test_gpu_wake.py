@@ -117,3 +117,20 @@ def test_transverse_wake_single_element(nbins):
     compare_tracking(g, o, TOL_PASS)
     oz, _, _, Vx, Vy = orc.wake2(z, nbins, syn.C3_W0, syn.C3_W0T, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
     assert np.max(np.abs(Vx)) > 0 and np.max(np.abs(Vy)) > 0
+
+
+@pytest.mark.parametrize("nbins,passes", [(256, 4), (4096, 0), (1, 3)])
+def test_space_charge_against_oracle(nbins, passes):
+    """Long-wavelength space charge between drifts, twice per turn, two turns;
+    the field is computed from bit-exact counts with the oracle's rounding."""
+    sc = {"type": "LSC", "nbins": nbins, "L": 2.0, "K": 4.0e4, "charge": syn.C3_CHARGE, "passes": passes}
+    lat = {"elements": [sc, {"type": "EDRIFT", "L": 1.0}, sc, {"type": "EDRIFT", "L": 0.5}], "aperture": None,
+           "p0c": 1.0e8}
+    z = syn.bunch("c3", n=30_000, seed=11)
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
+    if nbins > 1:
+        o0 = orc.track({**lat, "elements": [e for e in lat["elements"] if e["type"] != "LSC"]}, z, 2)
+        assert np.max(np.abs(o["z"][:, 5] - o0["z"][:, 5])) > 1e-9
