@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "trk_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
-TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8}
+TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8,
+         "SBEND": 9}
 APERTURES = {None: 0, "rect": 1, "ellipse": 2}
 ED_N, EM_N = 16, 504
 
@@ -61,6 +62,8 @@ def lib():
                             ctypes.c_double, ctypes.c_double, P, P]
         L.o_lsc_field.restype = None
         L.o_lsc_field.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
+        L.o_sbend.restype = None
+        L.o_sbend.argtypes = [P, ctypes.c_double, ctypes.c_double]
         L.o_wake_dipole.restype = None
         L.o_wake_dipole.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, P]
@@ -103,6 +106,8 @@ def lattice_arrays(lat):
             ei[e, 3] = el["nbins"]
             ed[e, 6], ed[e, 7], ed[e, 8] = el["W0"], el["sc"], el["charge"]
             ed[e, 10] = el.get("W0T", 0.0)
+        elif t == "SBEND":
+            ed[e, 0], ed[e, 12] = el["L"], el["angle"]
         elif t == "LSC":
             ei[e, 3], ei[e, 1] = el["nbins"], el.get("passes", 0)
             ed[e, 0], ed[e, 11], ed[e, 8] = el["L"], el["K"], el["charge"]
@@ -210,6 +215,13 @@ def lsc_field(hist, dl, qm, KL, passes):
     V = np.zeros(len(h))
     lib().o_lsc_field(_p(h), len(h), dl, qm, KL, passes, _p(V))
     return V
+
+
+def sbend(z, L, angle):
+    """The exact sector bend on a copy of one particle's 6 coordinates."""
+    zz = np.array(z, dtype=np.float64, copy=True)
+    lib().o_sbend(_p(zz), L, angle)
+    return zz
 
 
 def wake_dipole(z, nbins, coord, alive=None):

@@ -29,6 +29,10 @@
  *   - transverse dipole wake on the same bins (Table 1 TRWAKE, the transverse
  *     half of RFCW): per-bin sums of x and y, convolution with
  *     W_T(s) = W0T/sqrt(max(s, s_c)), interpolated kicks on x' and y';
+ *   - sector dipole (Table 1 CSBEND without gradient, fringe fields or
+ *     radiation): the exact motion in a uniform vertical field, a circle of
+ *     radius rho p_h in the horizontal plane (p_h = sqrt((1+delta)^2 - py^2)),
+ *     followed to the exit face at angle theta;
  *   - longitudinal space charge (Table 1 LSCDRIFT) in the long-wavelength limit
  *     (impedance proportional to i k): the same histogram as a line density,
  *     smoothed by repeated 1-2-1 passes, differentiated, energy kick
@@ -46,10 +50,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7, O_LSC = 8 };
+enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA = 6, O_WAKE = 7, O_LSC = 8,
+       O_SBEND = 9 };
 enum { O_AP_NONE = 0, O_AP_RECT = 1, O_AP_ELLIPSE = 2 };
 enum { ED_LENGTH = 0, ED_K1 = 1, ED_K2 = 2, ED_VOLT = 3, ED_PHASE = 4, ED_FREQ = 5,
-       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_KLSC = 11, ED_N = 16 };
+       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_KLSC = 11, ED_ANGLE = 12, ED_N = 16 };
 #define EM_N 504
 #define C_LIGHT 299792458.0
 #define O_PI 3.14159265358979323846
@@ -238,6 +243,49 @@ void o_moments(const double *x, const uint8_t *alive, int64_t n, double *out)
     for (int j = 0; j < 6; ++j) out[1 + j] = m[j];
     for (int q = 0; q < 21; ++q) out[7 + q] = nsum_get(&s2[q]) / (double)na;
 }
+
+/* ---------------------------------------------------------- sector bend ---- */
+
+/* Sector dipole of length L (along the reference arc) and angle theta, hard
+ * edge: rho = L/theta, the reference circle centred at the origin, the
+ * particle entering at radius rho + x with radial momentum px and tangential
+ * momentum pz (canonical, in units of the reference momentum).  Its orbit is a
+ * circle of radius rho p_h centred at C = (rho + x - rho pz, rho px); it leaves
+ * through the ray at angle theta after turning by alpha = theta + beta with
+ *   pz sin(beta) - px cos(beta) = (1 + x/rho - pz) sin(theta) - px cos(theta)
+ * (the branch through beta = 0 for the reference particle).  Then
+ *   x_f = |P_exit| - rho,  px_f = px cos(beta) - pz sin(beta),
+ *   y_f = y + py rho alpha,  l += rho (1 + delta) alpha - L,
+ * and slopes are restored with pz_f = sqrt((1+delta)^2 - px_f^2 - py^2).
+ * theta == 0 is the exact drift. */
+static void sbend(double *z, double L, double theta)
+{
+    if (theta == 0.0) {
+        exact_drift(z, L);
+        return;
+    }
+    const double rho = L / theta;
+    const double d1 = 1.0 + z[5];
+    const double r = sqrt(1.0 + z[1] * z[1] + z[3] * z[3]);
+    const double px = z[1] * d1 / r, py = z[3] * d1 / r, pz = d1 / r;
+    const double ph = sqrt(d1 * d1 - py * py);
+    const double S = (1.0 + z[0] / rho - pz) * sin(theta) - px * cos(theta);
+    const double beta = atan2(px, pz) + asin(S / ph);
+    const double alpha = theta + beta;
+    const double Cx = rho + z[0] - rho * pz, Cy = rho * px;
+    const double Px = Cx + rho * (pz * cos(alpha) + px * sin(alpha));
+    const double Py = Cy + rho * (pz * sin(alpha) - px * cos(alpha));
+    const double pxf = px * cos(beta) - pz * sin(beta);
+    const double pzf = sqrt(d1 * d1 - pxf * pxf - py * py);
+    z[0] = sqrt(Px * Px + Py * Py) - rho;
+    z[1] = pxf / pzf;
+    z[2] = z[2] + py * rho * alpha;
+    z[3] = py / pzf;
+    z[4] = z[4] + (rho * d1 * alpha - L);
+}
+
+/* The sector bend alone on one particle (for the tests). */
+void o_sbend(double *z, double L, double theta) { sbend(z, L, theta); }
 
 /* ---------------------------------------------------------------- wake ---- */
 
@@ -508,6 +556,7 @@ int64_t o_track(int ne, const int32_t *ei, const double *ed, const double *em,
                     case O_KQUAD:
                     case O_KSEXT: thick_multipole(z, dv[ED_LENGTH], dv[ED_K1], dv[ED_K2], iv[2]); break;
                     case O_THINSEXT: thin_sext(z, dv[ED_K2L]); break;
+                    case O_SBEND: sbend(z, dv[ED_LENGTH], dv[ED_ANGLE]); break;
                     default: break;
                     }
                 }
