@@ -85,7 +85,7 @@ typedef enum {
                           x' += V_x(l) / (p0c (1 + delta)) (y likewise), applied
                           before the energy kick; voltages from the particles
                           entering the element */
-    TRK_LSC = 8        /* longitudinal space charge (Table 1 LSCDRIFT) in the
+    TRK_LSC = 8,       /* longitudinal space charge (Table 1 LSCDRIFT) in the
                           long-wavelength limit, a thin kick of effective length
                           `length`: on the bins of TRK_WAKE, line density
                           lambda_k = q_m h_k / dl, n_kicks passes of
@@ -93,6 +93,12 @@ typedef enum {
                           (end bins repeated), d_k = central difference (one-sided
                           at the ends), delta += lsc_k length d(l) / p0c with d
                           interpolated as the wake voltage */
+    TRK_SBEND = 9      /* sector dipole, hard edge, no gradient (Table 1 CSBEND
+                          without fringe fields or radiation): the exact orbit in a
+                          uniform field, a circle of radius rho p_h
+                          (rho = length/angle, p_h = sqrt((1+delta)^2 - py^2)) from
+                          the entrance face to the exit face at `angle`; x is
+                          measured outward; angle 0 is the exact drift */
 } trk_elem_type;
 
 typedef enum { TRK_APERTURE_NONE = 0, TRK_APERTURE_RECT = 1, TRK_APERTURE_ELLIPSE = 2 } trk_aperture;
@@ -119,6 +125,7 @@ typedef struct {
                            W_T(s) = wake_w0t / sqrt(max(s, s_c)) (TRK_WAKE; 0 = none) */
     double lsc_k;       /* V m / C per m of length: space-charge factor g / (4 pi eps0 gamma^2)
                            (TRK_LSC; uses length, nbins, charge, n_kicks) */
+    double angle;       /* rad, bending angle (TRK_SBEND; |angle| < pi) */
     const double *C;    /* TRK_MAP: [6] or NULL (zero) */
     const double *R;    /* TRK_MAP: [6*6] row-major */
     const double *T;    /* TRK_MAP: [6*21], (j,k) j<=k lexicographic, or NULL */

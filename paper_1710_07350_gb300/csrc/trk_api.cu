@@ -232,6 +232,25 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             E.p[3] = d.volt * std::cos(phi);
             break;
         }
+        case TRK_SBEND:
+            if (!(d.length > 0.0) || !std::isfinite(d.length) || !(std::fabs(d.angle) < 3.14159265358979)) {
+                s = fail(TRK_EINVAL, "element " + std::to_string(i) + ": bad sector bend");
+                break;
+            }
+            if (d.angle == 0.0) {   // the exact drift
+                E.type = TRK_EDRIFT;
+                E.p[0] = d.length;
+                E.p[1] = 0.5 * d.length;
+                E.p[2] = 0.375 * d.length;
+                break;
+            }
+            E.p[0] = d.length;
+            E.p[1] = d.angle;
+            E.p[2] = d.length / d.angle;     // rho
+            E.p[3] = d.angle / d.length;     // 1 / rho
+            E.p[4] = std::sin(d.angle);
+            E.p[5] = std::cos(d.angle);
+            break;
         case TRK_LSC:
             if (d.nbins < 1 || d.nbins > kMaxBins || d.n_kicks < 0 || d.n_kicks > 1000 ||
                 !std::isfinite(d.lsc_k) || !std::isfinite(d.length) || !std::isfinite(d.charge)) {

@@ -25,6 +25,7 @@ constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
 //   RFCA         p[0] V, p[1] phi [rad], p[2] k_rf = 2 pi f / c, p[3] G = V cos(phi)
 //   WAKE         p[0] W0, p[1] s_c, p[2] charge, p[3] W0T (transverse, 0 = none);
 //                n = nbins; term0 = wake ordinal
+//   SBEND        p[0] L, p[1] theta, p[2] rho, p[3] 1/rho, p[4] sin theta, p[5] cos theta
 //   LSC          p[2] charge, p[4] K L; n = nbins; flags = smoothing passes;
 //                term0 = wake ordinal (kicked like a wake)
 //   MAP          term0 = first term; rb[r]..rb[r+1] = terms of output row r;

@@ -314,6 +314,41 @@ __device__ __forceinline__ void v_thin_sext(Tile<P> &q, const DevElem *__restric
     }
 }
 
+// Sector dipole, hard edge (Table 1 CSBEND without fringe fields or
+// radiation): the particle enters at radius rho + x with canonical radial and
+// tangential momenta px, pz and moves on a circle of radius rho p_h centred at
+// (rho + x - rho pz, rho px) until the exit face at angle theta, after turning
+// by alpha = theta + beta, beta = atan2(px, pz) + asin(S / p_h),
+// S = (1 + x/rho - pz) sin(theta) - px cos(theta).  Exit: x = |P| - rho,
+// px = px cos(beta) - pz sin(beta), y += py rho alpha, l += rho (1+delta) alpha - L.
+template <int P>
+__device__ __forceinline__ void v_sbend(Tile<P> &q, const DevElem *__restrict__ E) {
+    const double L = __ldg(&E->p[0]), th = __ldg(&E->p[1]), rho = __ldg(&E->p[2]), h = __ldg(&E->p[3]);
+    const double st = __ldg(&E->p[4]), ct = __ldg(&E->p[5]);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double d1 = 1.0 + q.d[p];
+        const double ir = rsqrt(fma(q.xp[p], q.xp[p], fma(q.yp[p], q.yp[p], 1.0)));
+        const double pz = d1 * ir, px = q.xp[p] * pz, py = q.yp[p] * pz;
+        const double ph = sqrt(fma(d1, d1, -py * py));
+        const double S = fma(fma(q.x[p], h, 1.0) - pz, st, -px * ct);
+        const double beta = atan2(px, pz) + asin(S / ph);
+        const double alpha = th + beta;
+        double sa, ca, sb, cb;
+        sincos(alpha, &sa, &ca);
+        sincos(beta, &sb, &cb);
+        const double Px = fma(rho, fma(pz, ca, px * sa), fma(-rho, pz, rho + q.x[p]));
+        const double Py = fma(rho, fma(pz, sa, -px * ca), rho * px);
+        const double pxf = fma(px, cb, -pz * sb);
+        const double ipzf = rsqrt(fma(d1, d1, -fma(pxf, pxf, py * py)));
+        q.x[p] = sqrt(fma(Px, Px, Py * Py)) - rho;
+        q.xp[p] = pxf * ipzf;
+        q.y[p] = fma(py * rho, alpha, q.y[p]);
+        q.yp[p] = py * ipzf;
+        q.l[p] = fma(rho * d1, alpha, q.l[p] - L);
+    }
+}
+
 // Thin RF: P = (1+delta) p0, P' = P + V cos(phi + k l), delta' = P'/p0' - 1,
 // slopes scaled by P/P'.
 template <int P>
@@ -585,6 +620,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             case TRK_KQUAD:
             case TRK_KSEXT: v_kick_drift<P>(q, iP, dirty, canon, E); break;
             case TRK_THINSEXT: v_thin_sext<P>(q, E); break;
+            case TRK_SBEND: v_sbend<P>(q, E); break;
             case TRK_RFCA: {
                 const double p01 = p0 + __ldg(&E->p[3]);
                 v_rfca<P>(q, E, p0, 1.0 / p01, dirty);

@@ -14,6 +14,9 @@ Per particle and pass (alive particle entering the element):
                 per sextupole kick (3 per step): (x^2 - y^2) (3), *c, -= (2); x y * c += (3) -> 8
                 exit: pz (6), x' = px/pz, y' = py/pz (2)                           -> 8
   THINSEXT      x' -= (K2L/2)(x^2 - y^2) (5), y' += K2L x y (3)                      -> 8
+  SBEND         slopes -> px, py, pz (9), p_h (4), S (6), beta: atan2, asin, divide,
+                add (4), alpha (1), sin and cos of alpha and beta (4), exit point
+                (14), px_f (3), 1/pz_f (6), x_f (5), slopes, y, l (9)               -> 64
   RFCA          P (2), phi + k l (2), cos (1), V * (1), + (1), P/P' (1), 2 *, delta (2) -> 12
   MAP           per nonzero term of degree d (the R_rr = 1 diagonal is free): d * (products) + 1 add
                 i.e. deg 0: 1, deg 1: 2, deg 2: 3, deg 3: 4
@@ -70,6 +73,8 @@ def element_flops(el):
         return 10 + (3 * n + 1) * 16 + 3 * n * kick + 8
     if t == "THINSEXT":
         return 8
+    if t == "SBEND":
+        return 64 if el["angle"] != 0.0 else 12
     if t == "RFCA":
         return 12
     if t == "MAP":

@@ -16,7 +16,8 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 PD = ctypes.POINTER(c_double)
 
 TRK_OK = 0
-TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8}
+TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8,
+         "SBEND": 9}
 APERTURES = {None: 0, "rect": 1, "ellipse": 2}
 STATUS = {0: "TRK_OK", 1: "TRK_EINVAL", 2: "TRK_ENOMEM", 3: "TRK_ECUDA", 4: "TRK_EKERNEL",
           5: "TRK_ETIMEOUT", 6: "TRK_EUNSUPPORTED"}
@@ -33,7 +34,7 @@ class trk_element_desc(ctypes.Structure):
                 ("length", c_double), ("k1", c_double), ("k2", c_double), ("k2l", c_double),
                 ("volt", c_double), ("phase_deg", c_double), ("freq_hz", c_double),
                 ("wake_w0", c_double), ("wake_sc", c_double), ("charge", c_double), ("wake_w0t", c_double),
-                ("lsc_k", c_double),
+                ("lsc_k", c_double), ("angle", c_double),
                 ("C", PD), ("R", PD), ("T", PD), ("U", PD)]
 
 
@@ -181,6 +182,8 @@ def trk_create_lattice(lattice, moments=True):
         elif t == "WAKE":
             d.nbins, d.wake_w0, d.wake_sc, d.charge = el["nbins"], el["W0"], el["sc"], el["charge"]
             d.wake_w0t = el.get("W0T", 0.0)
+        elif t == "SBEND":
+            d.length, d.angle = el["L"], el["angle"]
         elif t == "LSC":
             d.nbins, d.length, d.lsc_k, d.charge = el["nbins"], el["L"], el["K"], el["charge"]
             d.n_kicks = el.get("passes", 0)

@@ -136,6 +136,29 @@ def c4_variants(n_var=256, seed=4):
     return [(K2L_THIN * (1 + u[v, 0]), -K2L_THIN * (1 + u[v, 1]), int(n[v])) for v in range(n_var)]
 
 
+def lattice_bend_ring(cells=8, aperture=("ellipse", 0.02, 0.012)):
+    """A ring with sector dipoles: per cell [B, D0.4, QF, D0.4, B, D0.4, QD, D0.4],
+    B a 1.5 m sector bend of 2 pi / (2 cells), QF / QD kick-drift quadrupoles
+    (0.2 m, K1 = +-1.2, 4 steps); no cavity (the momentum deviation slips)."""
+    ang = 2.0 * math.pi / (2 * cells)
+    b = {"type": "SBEND", "L": 1.5, "angle": ang}
+    d = {"type": "EDRIFT", "L": 0.4}
+    qf = {"type": "KQUAD", "L": L_QUAD, "K1": K1_QUAD, "n_kicks": N_KICKS}
+    qd = {"type": "KQUAD", "L": L_QUAD, "K1": -K1_QUAD, "n_kicks": N_KICKS}
+    return {"name": "bend ring", "elements": [b, d, qf, d, b, d, qd, d] * cells, "aperture": aperture,
+            "p0c": P0C_1GEV}
+
+
+def bend_ring_bunch(n, seed=77):
+    """Gaussian bunch for the bend ring: 0.3 mm, 0.1 mrad, sigma_delta 1e-3."""
+    g = np.random.Generator(np.random.Philox(key=seed))
+    z = np.zeros((n, 6))
+    z[:, 0], z[:, 1] = g.normal(0, 3e-4, n), g.normal(0, 1e-4, n)
+    z[:, 2], z[:, 3] = g.normal(0, 3e-4, n), g.normal(0, 1e-4, n)
+    z[:, 5] = g.normal(0, 1e-3, n)
+    return z
+
+
 def lattice_c4(variant):
     k2f, k2d, _ = variant
     qf, qd = _map_elem("QF.o2"), _map_elem("QD.o2")

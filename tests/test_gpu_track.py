@@ -244,3 +244,27 @@ def test_repeated_runs_bit_identical():
     r2 = gpu_track(lat, z, 6)
     assert np.array_equal(r1["moments"], r2["moments"])
     assert np.array_equal(r1["z"], r2["z"]) and np.array_equal(r1["ids"], r2["ids"])
+
+
+def test_bend_ring_one_pass_and_50_turns():
+    """Sector dipoles (exact orbit in a uniform field) between kick-drift
+    quadrupoles, with the ellipse aperture: one pass and 50 turns."""
+    lat = syn.lattice_bend_ring()
+    z = syn.bend_ring_bunch(3000)
+    g1 = gpu_track(lat, z, 1)
+    o1 = orc.track(lat, z, 1)
+    compare_tracking(g1, o1, TOL_PASS)
+    compare_moments(g1["moments"], o1["moments"])
+    g = gpu_track(lat, z, 50, schedule={"block": 128, "per_thread": 2, "chunk_turns": 20})
+    o = orc.track(lat, z, 50)
+    err = compare_tracking(g, o, TOL_100)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
+
+
+def test_sbend_zero_angle_is_the_exact_drift():
+    lat = {"elements": [{"type": "SBEND", "L": 1.5, "angle": 0.0}, {"type": "SBEND", "L": 0.7, "angle": -0.05}],
+           "aperture": ("rect", 0.02, 0.02), "p0c": syn.P0C_1GEV}
+    z = syn.bend_ring_bunch(1000, seed=5)
+    g = gpu_track(lat, z, 3)
+    o = orc.track(lat, z, 3)
+    compare_tracking(g, o, TOL_PASS * 10)
