@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "_build", "liboracle.so")
 TYPES = {"MAP": 1, "EDRIFT": 2, "KQUAD": 3, "KSEXT": 4, "THINSEXT": 5, "RFCA": 6, "WAKE": 7, "LSC": 8,
          "SBEND": 9}
 APERTURES = {None: 0, "rect": 1, "ellipse": 2}
-ED_N, EM_N = 16, 504
+ED_N, EM_N = 20, 504
 
 
 def build(force=False):
@@ -62,6 +62,14 @@ def lib():
                             ctypes.c_double, ctypes.c_double, P, P]
         L.o_lsc_field.restype = None
         L.o_lsc_field.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
+        L.o_lsc_bracket.restype = ctypes.c_double
+        L.o_lsc_bracket.argtypes = [ctypes.c_double]
+        L.o_lsc_imp_apply.restype = None
+        L.o_lsc_imp_apply.argtypes = [P, ctypes.c_int] + [ctypes.c_double] * 6 + [P]
+        L.o_lsc_imp_field.restype = None
+        L.o_lsc_imp_field.argtypes = [P, ctypes.c_int] + [ctypes.c_double] * 7 + [P]
+        L.o_lsc_imp.restype = None
+        L.o_lsc_imp.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int] + [ctypes.c_double] * 7 + [P, P]
         L.o_sbend.restype = None
         L.o_sbend.argtypes = [P, ctypes.c_double, ctypes.c_double]
         L.o_wake_dipole.restype = None
@@ -110,7 +118,9 @@ def lattice_arrays(lat):
             ed[e, 0], ed[e, 12] = el["L"], el["angle"]
         elif t == "LSC":
             ei[e, 3], ei[e, 1] = el["nbins"], el.get("passes", 0)
-            ed[e, 0], ed[e, 11], ed[e, 8] = el["L"], el["K"], el["charge"]
+            ed[e, 0], ed[e, 11], ed[e, 8] = el["L"], el.get("K", 0.0), el["charge"]
+            ed[e, 13], ed[e, 14] = el.get("rb", 0.0), el.get("mc2", 0.0)
+            ed[e, 15], ed[e, 16] = el.get("f0", 0.0), el.get("f1", 0.0)
         else:
             raise ValueError(t)
     return ei, ed, em
@@ -215,6 +225,39 @@ def lsc_field(hist, dl, qm, KL, passes):
     V = np.zeros(len(h))
     lib().o_lsc_field(_p(h), len(h), dl, qm, KL, passes, _p(V))
     return V
+
+
+def lsc_bracket(x):
+    """1 - x K1(x), the bracket of the round-beam space-charge impedance."""
+    return lib().o_lsc_bracket(float(x))
+
+
+def lsc_imp_apply(lam, dl, L, rb, gamma, f0=0.0, f1=0.0):
+    """Impedance kick voltage on a periodic line density lam (C/m), all bins."""
+    lam = np.ascontiguousarray(lam, np.float64)
+    V = np.zeros(len(lam))
+    lib().o_lsc_imp_apply(_p(lam), len(lam), dl, L, rb, gamma, f0, f1, _p(V))
+    return V
+
+
+def lsc_imp_field(hist, dl, qm, L, rb, gamma, f0=0.0, f1=0.0):
+    """Impedance kick voltage on the bins of a histogram (zero-padded to 2 nb)."""
+    h = np.ascontiguousarray(hist, np.int64)
+    V = np.zeros(len(h))
+    lib().o_lsc_imp_field(_p(h), len(h), dl, qm, L, rb, gamma, f0, f1, _p(V))
+    return V
+
+
+def lsc_imp(z, nbins, L, rb, mc2, charge, p0c, f0=0.0, f1=0.0, alive=None, n_total=None):
+    """One impedance space-charge kick on a copy of z; returns (z, hist, V)."""
+    z = np.array(z, dtype=np.float64, order="C", copy=True)
+    n = z.shape[0]
+    alive = np.ones(n, np.uint8) if alive is None else np.ascontiguousarray(alive, np.uint8)
+    h = np.zeros(nbins, np.int64)
+    V = np.zeros(nbins)
+    lib().o_lsc_imp(_p(z), _p(alive), n, n if n_total is None else n_total, nbins, L, rb, mc2, f0, f1, charge,
+                    p0c, _p(h), _p(V))
+    return z, h, V
 
 
 def sbend(z, L, angle):

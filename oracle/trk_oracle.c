@@ -33,16 +33,19 @@
  *     radiation): the exact motion in a uniform vertical field, a circle of
  *     radius rho p_h in the horizontal plane (p_h = sqrt((1+delta)^2 - py^2)),
  *     followed to the exit face at angle theta;
- *   - longitudinal space charge (Table 1 LSCDRIFT) in the long-wavelength limit
- *     (impedance proportional to i k): the same histogram as a line density,
- *     smoothed by repeated 1-2-1 passes, differentiated, energy kick
- *     delta += K L (d lambda / d l)(l) / p0c.
+ *   - longitudinal space charge (Table 1 LSCDRIFT) on the same histogram as a
+ *     line density, either in the long-wavelength limit (impedance proportional
+ *     to i k: smoothed by repeated 1-2-1 passes, differentiated, energy kick
+ *     delta += K L (d lambda / d l)(l) / p0c) or with the impedance of a round,
+ *     transversely uniform beam of radius r_b,
+ *       Z(k) = i Z0 / (pi k r_b^2) (1 - xi K1(xi)),  xi = |k| r_b / gamma,
+ *     applied by discrete Fourier transforms of the zero-padded line density.
  *
  * Coordinates: (x, x', y, y', l, delta), l the path-length deviation [m].
  * Lattice description: one row per element in three flat arrays
  *   ei[4*e + 0..3]  = type, order (MAP) or smoothing passes (LSC), n_kicks (KQUAD/KSEXT),
  *                     nbins (WAKE, LSC)
- *   ed[16*e + ...]  = see ED_* below
+ *   ed[20*e + ...]  = see ED_* below
  *   em[504*e + ...] = C[6], R[36] (row-major), T[6*21], U[6*56] (MAP only)
  */
 #include <math.h>
@@ -54,10 +57,13 @@ enum { O_MAP = 1, O_EDRIFT = 2, O_KQUAD = 3, O_KSEXT = 4, O_THINSEXT = 5, O_RFCA
        O_SBEND = 9 };
 enum { O_AP_NONE = 0, O_AP_RECT = 1, O_AP_ELLIPSE = 2 };
 enum { ED_LENGTH = 0, ED_K1 = 1, ED_K2 = 2, ED_VOLT = 3, ED_PHASE = 4, ED_FREQ = 5,
-       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_KLSC = 11, ED_ANGLE = 12, ED_N = 16 };
+       ED_W0 = 6, ED_SC = 7, ED_CHARGE = 8, ED_K2L = 9, ED_W0T = 10, ED_KLSC = 11, ED_ANGLE = 12,
+       ED_RB = 13, ED_MC2 = 14, ED_F0 = 15, ED_F1 = 16, ED_N = 20 };
 #define EM_N 504
 #define C_LIGHT 299792458.0
 #define O_PI 3.14159265358979323846
+#define O_EULER 0.57721566490153286061   /* Euler's constant */
+#define O_Z0 376.730313412               /* impedance of free space mu0 c [Ohm], CODATA 2018 */
 
 /* ---------------------------------------------------------------- maps ---- */
 
@@ -508,6 +514,152 @@ void o_lsc(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb, 
     free(V);
 }
 
+/* Bracket of the round-beam space-charge impedance, B(x) = 1 - x K1(x), x >= 0.
+ * x <= 2: the power series of K1 (Abramowitz & Stegun 9.6.11, n = 1),
+ *   x K1(x) = 1 + x ln(x/2) I1(x) - (x^2/4) S,
+ *   I1(x) = (x/2) sum_k y^k / (k! (k+1)!),  S = sum_k (psi(k+1) + psi(k+2)) y^k / (k! (k+1)!),
+ *   y = x^2/4, psi(k+1) = -gamma_E + H_k (H_k the harmonic numbers),
+ * so B = -x ln(x/2) I1(x) + y S with no cancellation at small x.
+ * x > 2: the integral K1(x) = int_0^inf exp(-x cosh t) cosh t dt (A&S 9.6.24) by the
+ * trapezoidal rule with step 1/16, exp(-x) taken out (cosh t - 1 = 2 sinh^2(t/2));
+ * for this entire integrand the rule's error falls like exp(-pi^2 / h), far below
+ * double rounding.  Terms are added until one is below 1e-18 of the sum. */
+double o_lsc_bracket(double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    if (x <= 2.0) {
+        const double y = 0.25 * x * x;
+        double term = 1.0, H = 0.0, si = 0.0, ss = 0.0;
+        for (int k = 0; k < 40; ++k) {
+            if (k > 0) {
+                term = term * y / ((double)k * (double)(k + 1));
+                H += 1.0 / (double)k;
+            }
+            const double psi = (H - O_EULER) + (H + 1.0 / (double)(k + 1) - O_EULER);
+            si += term;
+            ss += psi * term;
+        }
+        const double I1 = 0.5 * x * si;
+        return -x * log(0.5 * x) * I1 + y * ss;
+    }
+    const double h = 1.0 / 16.0;
+    double sum = 0.5;   /* t = 0 at half weight: exp(0) cosh(0) / 2 */
+    for (int j = 1; j < 100000; ++j) {
+        const double t = (double)j * h;
+        const double sh = sinh(0.5 * t);
+        const double f = exp(-x * (2.0 * sh * sh)) * cosh(t);
+        sum += f;
+        if (f < 1e-18 * sum) break;
+    }
+    return 1.0 - x * exp(-x) * (h * sum);
+}
+
+/* Cosine taper of the space-charge filter at f = |m'| / (N/2), a fraction of the
+ * Nyquist frequency: 1 up to f0, (1 + cos(pi (f - f0) / (f1 - f0))) / 2 between,
+ * 0 from f1 on; f1 <= 0: no filter. */
+static double o_lsc_taper(double f, double f0, double f1)
+{
+    if (!(f1 > 0.0) || f <= f0) return 1.0;
+    if (f >= f1) return 0.0;
+    return 0.5 * (1.0 + cos(O_PI * (f - f0) / (f1 - f0)));
+}
+
+/* Impedance kick on a periodic line density lam[0..N) of bin width dl:
+ *   Lambda_m = sum_k lam_k exp(-2 pi i m k / N),
+ *   kappa_m = 2 pi m' / (N dl),  m' = m (m < N/2), m - N (m > N/2),
+ *   Z_m = i sgn(m') Z0 / (pi |kappa_m| r_b^2) B(|kappa_m| r_b / gamma) taper(|m'| / (N/2)),
+ *         Z_0 = 0 and, for even N, Z_{N/2} = 0 (no mean field; the Nyquist term has no sign),
+ *   V_k = L c Re[(1/N) sum_m Z_m Lambda_m exp(+2 pi i m k / N)]   (V), all k < N.
+ * With lambda in C/m, Z in Ohm/m and c in m/s, Z c lambda is a field in V/m.  Direct
+ * transforms, phases from a table of 2 pi j / N (the index m k reduced modulo N),
+ * compensated sums. */
+void o_lsc_imp_apply(const double *lam, int N, double dl, double L, double rb, double gamma, double f0,
+                     double f1, double *V)
+{
+    double *cs = (double *)malloc((size_t)N * sizeof(double));
+    double *sn = (double *)malloc((size_t)N * sizeof(double));
+    double *Zr = (double *)malloc((size_t)N * sizeof(double));
+    double *Zi = (double *)malloc((size_t)N * sizeof(double));
+    for (int j = 0; j < N; ++j) {
+        cs[j] = cos(2.0 * O_PI * (double)j / (double)N);
+        sn[j] = sin(2.0 * O_PI * (double)j / (double)N);
+    }
+    for (int m = 0; m < N; ++m) {
+        /* Lambda_m */
+        nsum re = {0.0, 0.0}, im = {0.0, 0.0};
+        for (int k = 0; k < N; ++k) {
+            const int j = (int)(((int64_t)m * k) % N);
+            nsum_add(&re, lam[k] * cs[j]);
+            nsum_add(&im, -lam[k] * sn[j]);
+        }
+        const double Lr = nsum_get(&re), Li = nsum_get(&im);
+        const int mp = 2 * m < N ? m : m - N;
+        if (mp == 0 || 2 * m == N) {
+            Zr[m] = Zi[m] = 0.0;
+            continue;
+        }
+        const double kap = 2.0 * O_PI * fabs((double)mp) / ((double)N * dl);
+        const double z = O_Z0 / (O_PI * kap * rb * rb) * o_lsc_bracket(kap * rb / gamma) *
+                         o_lsc_taper(fabs((double)mp) / (0.5 * (double)N), f0, f1);
+        const double zs = mp > 0 ? z : -z;   /* Z_m = i zs */
+        Zr[m] = -zs * Li;                     /* (Lr + i Li) (i zs) */
+        Zi[m] = zs * Lr;
+    }
+    for (int k = 0; k < N; ++k) {
+        nsum acc = {0.0, 0.0};
+        for (int m = 0; m < N; ++m) {
+            const int j = (int)(((int64_t)m * k) % N);
+            nsum_add(&acc, Zr[m] * cs[j]);    /* Re[(Zr + i Zi)(cos + i sin)] */
+            nsum_add(&acc, -Zi[m] * sn[j]);
+        }
+        V[k] = L * C_LIGHT * (nsum_get(&acc) / (double)N);
+    }
+    free(cs);
+    free(sn);
+    free(Zr);
+    free(Zi);
+}
+
+/* Impedance field on the bins of o_wake_hist: lambda_k = q_m h_k / dl, zero-padded
+ * to N = 2 nb so that the periodic transform adds no field from a wrapped image of
+ * the bunch; V_k for k < nb.  dl == 0 or nb == 1: V = 0. */
+void o_lsc_imp_field(const int64_t *hist, int nb, double dl, double qm, double L, double rb, double gamma,
+                     double f0, double f1, double *V)
+{
+    if (!(dl > 0.0) || nb < 2) {
+        memset(V, 0, (size_t)nb * sizeof(double));
+        return;
+    }
+    const int N = 2 * nb;
+    double *lam = (double *)calloc((size_t)N, sizeof(double));
+    double *W = (double *)malloc((size_t)N * sizeof(double));
+    for (int k = 0; k < nb; ++k) lam[k] = qm * (double)hist[k] / dl;
+    o_lsc_imp_apply(lam, N, dl, L, rb, gamma, f0, f1, W);
+    memcpy(V, W, (size_t)nb * sizeof(double));
+    free(lam);
+    free(W);
+}
+
+/* Whole impedance space-charge element (a thin kick of effective length L) for a
+ * particle of rest energy mc2 [eV]: gamma = sqrt(1 + (p0c / mc2)^2). */
+void o_lsc_imp(double *x, const uint8_t *alive, int64_t n, int64_t n_total, int nb, double L, double rb,
+               double mc2, double f0, double f1, double charge, double p0c, int64_t *hist_out, double *V_out)
+{
+    int64_t *h = (int64_t *)malloc((size_t)nb * sizeof(int64_t));
+    double *V = (double *)calloc((size_t)nb, sizeof(double));
+    double lmin, dl;
+    int64_t na = o_wake_hist(x, alive, n, nb, &lmin, &dl, h);
+    if (na > 0) {
+        const double r = p0c / mc2;
+        o_lsc_imp_field(h, nb, dl, charge / (double)n_total, L, rb, sqrt(1.0 + r * r), f0, f1, V);
+        o_wake_kick(x, alive, n, V, nb, lmin, dl, p0c);
+    }
+    if (hist_out) memcpy(hist_out, h, (size_t)nb * sizeof(int64_t));
+    if (V_out) memcpy(V_out, V, (size_t)nb * sizeof(double));
+    free(h);
+    free(V);
+}
+
 /* ------------------------------------------------------------ tracking ---- */
 
 /*
@@ -536,6 +688,9 @@ int64_t o_track(int ne, const int32_t *ei, const double *ed, const double *em,
             if (type == O_WAKE) {
                 o_wake2(x, alive, n, n_total, iv[3], dv[ED_W0], dv[ED_W0T], dv[ED_SC], dv[ED_CHARGE], *p0c, NULL,
                         NULL, NULL, NULL);
+            } else if (type == O_LSC && dv[ED_RB] > 0.0) {
+                o_lsc_imp(x, alive, n, n_total, iv[3], dv[ED_LENGTH], dv[ED_RB], dv[ED_MC2], dv[ED_F0],
+                          dv[ED_F1], dv[ED_CHARGE], *p0c, NULL, NULL);
             } else if (type == O_LSC) {
                 o_lsc(x, alive, n, n_total, iv[3], dv[ED_KLSC] * dv[ED_LENGTH], iv[1], dv[ED_CHARGE], *p0c, NULL,
                       NULL);
