@@ -63,14 +63,16 @@ def parse():
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
     p.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi samples (default: temp dir)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train", "sweep"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train", "sweep", "bend"],
                    help="c2 (default, the headline line); c3 wake linac, c4 batched variants, the "
-                        "surrogate's inference (mlp) and training (mlp-train), and the particle-count "
-                        "sweep of the map ring (sweep) print their own lines")
+                        "surrogate's inference (mlp) and training (mlp-train), the particle-count "
+                        "sweep of the map ring (sweep) and the sector-bend ring (bend) print their own "
+                        "lines")
     p.add_argument("--da-variants", type=int, default=64)
     p.add_argument("--rows", type=int, default=64 * 512 * 512, help="mlp: rows per inference call")
     p.add_argument("--epochs", type=int, default=24, help="mlp-train: epochs")
     p.add_argument("--transverse", action="store_true", help="c3: add the transverse dipole wake")
+    p.add_argument("--lsc", action="store_true", help="c3: add impedance space charge after every wake")
     return p.parse_args()
 
 
@@ -472,7 +474,7 @@ def run_c3(args):
 
     import synthetic as syn
     from paper_1710_07350_gb300 import flops, trk
-    lat = syn.lattice_c3(transverse=args.transverse)
+    lat = syn.lattice_c3(transverse=args.transverse, lsc=args.lsc)
     L = trk.trk_create_lattice(lat)
     z0 = syn.bunch("c3")
     if args.transverse:                       # an offset bunch, so that the dipole moments act
@@ -503,12 +505,57 @@ def run_c3(args):
     f += n * 200 * flops.WAKE_FLOPS_PER_PARTICLE + 200 * flops.wake_conv_flops(syn.C3_NBINS)
     if args.transverse:
         f += n * 200 * flops.TRWAKE_FLOPS_PER_PARTICLE + 200 * 2 * flops.wake_conv_flops(syn.C3_NBINS)
+    if args.lsc:
+        f += n * 200 * flops.LSC_FLOPS_PER_PARTICLE + 200 * flops.lsc_imp_flops(syn.C3_NBINS)
+    extra = (" + transverse dipole wake, offset bunch" if args.transverse else "") + \
+            (" + impedance space charge (4096 bins, r_b 1 mm, L 3 m)" if args.lsc else "")
     print(json.dumps({"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins%s, drift, quad], 1e7 particles"
-                                  % (" + transverse dipole wake, offset bunch" if args.transverse else ""),
+                                  % extra,
                       "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
                       "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
                       "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, "launches": times[0][1]["launches"],
                       "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
+def run_bend(args):
+    """Sector-bend ring: 1e6 particles, 16 exact sector dipoles between
+    kick-drift quadrupoles and drifts per turn, 100 turns per step."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import flops, trk
+    lat = syn.lattice_bend_ring()
+    L = trk.trk_create_lattice(lat)
+    n, turns = args.particles, args.turns_per_step
+    coords0, ids0 = trk.upload(syn.bend_ring_bunch(n))
+    times, work = [], []
+    for k in range(args.warmup + args.steps):
+        b = trk.trk_bunch_wrap(coords0.clone(), ids0.clone())
+        trk.trk_bunch_set_schedule(b, block=args.block, per_thread=args.per_thread)
+        trk.trk_bunch_enable_timing(b, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        trk.trk_track(b, L, turns)
+        e1.record()
+        e1.synchronize()
+        st = trk.trk_bunch_stats(b)
+        if k >= args.warmup:
+            _, lt, le = trk.trk_lost(b)
+            times.append((e0.elapsed_time(e1), st))
+            work.append(flops.step_work(lat, n, turns, lt, le))
+        del b
+    ms = sum(t for t, _ in times) / len(times)
+    kms = sum(st["track_kernel_ms"] for _, st in times) / len(times)
+    passes = sum(p for p, _ in work) / len(work)
+    f = sum(w for _, w in work) / len(work)
+    print(json.dumps({"workload": "bend ring: 8 x [SBEND 1.5 m pi/8, D0.4, QF, D0.4, SBEND, D0.4, QD, D0.4], "
+                                  "%d particles, %d turns per step" % (n, turns),
+                      "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_step": ms,
+                      "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
+                      "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS,
+                      "launches": times[0][1]["launches"], "steps": args.steps, "warmup": args.warmup}))
     return 0
 
 
@@ -675,6 +722,8 @@ def main():
         return run_mlp_train(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "bend":
+        return run_bend(args)
     return run_ours(args)
 
 

@@ -85,14 +85,23 @@ typedef enum {
                           x' += V_x(l) / (p0c (1 + delta)) (y likewise), applied
                           before the energy kick; voltages from the particles
                           entering the element */
-    TRK_LSC = 8,       /* longitudinal space charge (Table 1 LSCDRIFT) in the
-                          long-wavelength limit, a thin kick of effective length
-                          `length`: on the bins of TRK_WAKE, line density
-                          lambda_k = q_m h_k / dl, n_kicks passes of
-                          lambda_k <- (lambda_{k-1} + 2 lambda_k + lambda_{k+1}) / 4
+    TRK_LSC = 8,       /* longitudinal space charge (Table 1 LSCDRIFT), a thin
+                          kick of effective length `length` on the bins of
+                          TRK_WAKE, line density lambda_k = q_m h_k / dl.
+                          lsc_rb == 0, the long-wavelength limit: n_kicks passes
+                          of lambda_k <- (lambda_{k-1} + 2 lambda_k + lambda_{k+1}) / 4
                           (end bins repeated), d_k = central difference (one-sided
                           at the ends), delta += lsc_k length d(l) / p0c with d
-                          interpolated as the wake voltage */
+                          interpolated as the wake voltage.
+                          lsc_rb > 0, the impedance of a round, transversely
+                          uniform beam of radius r_b:
+                          Z(k) = i sgn(k) Z0 / (pi |k| r_b^2) (1 - xi K1(xi)),
+                          xi = |k| r_b / gamma, gamma = sqrt(1 + (p0c/lsc_mc2)^2),
+                          times a cosine taper from lsc_f0 to lsc_f1 (fractions
+                          of the Nyquist frequency); lambda zero-padded to
+                          2 nbins, transformed, multiplied by Z, transformed
+                          back: V(l) = length c (Z lambda)(l), delta += V / p0c.
+                          nbins a power of two, 1 .. 4096, in this mode */
     TRK_SBEND = 9      /* sector dipole, hard edge, no gradient (Table 1 CSBEND
                           without fringe fields or radiation): the exact orbit in a
                           uniform field, a circle of radius rho p_h
@@ -126,6 +135,11 @@ typedef struct {
     double lsc_k;       /* V m / C per m of length: space-charge factor g / (4 pi eps0 gamma^2)
                            (TRK_LSC; uses length, nbins, charge, n_kicks) */
     double angle;       /* rad, bending angle (TRK_SBEND; |angle| < pi) */
+    double lsc_rb;      /* m, beam radius of the space-charge impedance (TRK_LSC;
+                           0 = the long-wavelength limit with lsc_k) */
+    double lsc_mc2;     /* eV, rest energy of the particle (TRK_LSC with lsc_rb > 0) */
+    double lsc_f0;      /* filter: start of the cosine taper, fraction of Nyquist (TRK_LSC, lsc_rb > 0) */
+    double lsc_f1;      /* filter: end of the taper (0 from here on), f0 < f1 <= 1; <= 0 = no filter */
     const double *C;    /* TRK_MAP: [6] or NULL (zero) */
     const double *R;    /* TRK_MAP: [6*6] row-major */
     const double *T;    /* TRK_MAP: [6*21], (j,k) j<=k lexicographic, or NULL */

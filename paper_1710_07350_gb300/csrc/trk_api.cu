@@ -260,6 +260,23 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             E.n = d.nbins;
             E.flags = (uint32_t)d.n_kicks;
             E.term0 = (int32_t)L->wakes.size();
+            if (d.lsc_rb != 0.0) {   // the impedance of a round beam
+                const bool pow2 = (d.nbins & (d.nbins - 1)) == 0;
+                const bool filt = !(d.lsc_f1 > 0.0) || (d.lsc_f0 >= 0.0 && d.lsc_f0 < d.lsc_f1 && d.lsc_f1 <= 1.0);
+                if (!(d.lsc_rb > 0.0) || !std::isfinite(d.lsc_rb) || !(d.lsc_mc2 > 0.0) ||
+                    !std::isfinite(d.lsc_mc2) || !pow2 || d.nbins > kLscImpMaxBins || !filt ||
+                    !std::isfinite(d.lsc_f0) || !std::isfinite(d.lsc_f1)) {
+                    s = fail(TRK_EINVAL, "element " + std::to_string(i) +
+                                             ": bad space-charge impedance (r_b > 0, rest energy > 0, nbins a "
+                                             "power of two up to 4096, 0 <= f0 < f1 <= 1 or f1 <= 0)");
+                    break;
+                }
+                E.p[5] = d.lsc_rb;
+                E.p[6] = d.lsc_mc2;
+                E.p[7] = d.lsc_f0;
+                E.p[8] = d.lsc_f1;
+                E.p[9] = d.length;
+            }
             E.p[2] = d.charge;
             E.p[4] = d.lsc_k * d.length;
             L->wakes.push_back(i);
@@ -628,7 +645,12 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                         TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, lsc ? 0.0 : W.p[0],
                                                   lsc ? 1.0 : W.p[1], b->hist, b->wfun, lsc ? 0.0 : W.p[3],
                                                   tr ? b->dip : nullptr, b->wfun_t, b->n, b->stream));
-                        if (lsc)
+                        if (lsc && W.p[5] > 0.0) {
+                            const double r = p0 / W.p[6];
+                            TRK_CUDA(launch_lsc_imp(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[9],
+                                                    W.p[5], std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->V,
+                                                    b->stream));
+                        } else if (lsc)
                             TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
                                                       (int)W.flags, b->wfun, b->lsc, b->V, b->stream));
                         else

@@ -27,7 +27,8 @@ constexpr int kMomentsN = 28;   // n, 6 means, 21 second moments
 //                n = nbins; term0 = wake ordinal
 //   SBEND        p[0] L, p[1] theta, p[2] rho, p[3] 1/rho, p[4] sin theta, p[5] cos theta
 //   LSC          p[2] charge, p[4] K L; n = nbins; flags = smoothing passes;
-//                term0 = wake ordinal (kicked like a wake)
+//                term0 = wake ordinal (kicked like a wake); impedance mode:
+//                p[5] r_b (> 0), p[6] rest energy mc^2 [eV], p[7] f0, p[8] f1, p[9] L
 //   MAP          term0 = first term; rb[r]..rb[r+1] = terms of output row r;
 //                flags bit r (r < 6) = row r starts from x_r (R_rr == 1 folded);
 //                flags bit 6 = row 5 (delta) changes
@@ -136,6 +137,12 @@ cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins
 // V_k = KL d_k (see TRK_LSC); a, b scratch of nbins doubles.
 cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double KL,
                              int passes, double *a, double *b, double *V, cudaStream_t s);
+// Space-charge field of the round-beam impedance on the bins of slot `slot`
+// (see TRK_LSC): one block, the line density zero-padded to N = 2 nbins
+// (nbins a power of two, <= kLscImpMaxBins) in shared memory.
+constexpr int kLscImpMaxBins = 4096;
+cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double L,
+                           double rb, double gamma, double f0, double f1, double *V, cudaStream_t s);
 cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
                                cudaStream_t s);
 

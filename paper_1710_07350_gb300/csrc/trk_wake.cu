@@ -5,6 +5,9 @@
 // strength the same pass sums x and y per bin (the dipole moments), in 64-bit
 // fixed point so that the sums do not depend on the order of the atomics, and
 // two more convolutions give the transverse voltages for the slope kicks.
+// Longitudinal space charge (Table 1 LSCDRIFT) uses the same window and counts:
+// either a smoothed derivative of the line density (long-wavelength limit) or
+// the round-beam impedance applied with radix-2 transforms in shared memory.
 #include <cmath>
 
 #include "trk_internal.cuh"
@@ -257,6 +260,134 @@ __global__ void __launch_bounds__(1024) k_lsc_field(const uint32_t *__restrict__
     }
 }
 
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kZ0 = 376.730313412;          // mu0 c [Ohm], CODATA 2018
+constexpr double kEulerGamma = 0.57721566490153286061;
+constexpr double kClight = 299792458.0;
+
+// 1 - x K1(x), x >= 0.  Up to x = 2 from the ascending series of K1 and I1
+// (Abramowitz & Stegun 9.6.11 and 9.6.10, order 1), written so that nothing
+// cancels at small x:  1 - x K1 = -x ln(x/2) I1(x) + (x^2/4) sum_k c_k t_k with
+// t_k = (x^2/4)^k / (k! (k+1)!) and c_k = psi(k+1) + psi(k+2) = 2 H_k + 1/(k+1)
+// - 2 gamma_E; I1 = (x/2) sum_k t_k.  Above 2 from K1(x) = int_0^inf exp(-x cosh t)
+// cosh t dt (A&S 9.6.24) by the trapezoidal rule, step 1/16 (exponentially
+// accurate for this entire integrand), with exp(-x) factored out.
+__device__ double lsc_bracket(double x) {
+    if (!(x > 0.0)) return 0.0;
+    if (x <= 2.0) {
+        const double q = 0.25 * x * x;
+        double t = 1.0, harm = 0.0, sum_t = 1.0, sum_ct = 1.0 - 2.0 * kEulerGamma;
+        for (int k = 1; k < 40; ++k) {
+            t *= q / ((double)k * (double)(k + 1));
+            harm += 1.0 / (double)k;
+            sum_t += t;
+            sum_ct += (2.0 * harm + 1.0 / (double)(k + 1) - 2.0 * kEulerGamma) * t;
+        }
+        return q * sum_ct - x * log(0.5 * x) * (0.5 * x * sum_t);
+    }
+    const double h = 0.0625;
+    double acc = 0.5;
+    for (int j = 1; j < 100000; ++j) {   // cosh t - 1 = 2 sinh^2(t/2), t = j h
+        const double sh = sinh(0.5 * (double)j * h);
+        const double f = exp(-2.0 * x * sh * sh) * cosh((double)j * h);
+        acc += f;
+        if (f < 1e-18 * acc) break;
+    }
+    return 1.0 - x * exp(-x) * (h * acc);
+}
+
+// Cosine taper at f (fraction of Nyquist): 1 to f0, 0 from f1, f1 <= 0: none.
+__device__ double lsc_taper(double f, double f0, double f1) {
+    if (!(f1 > 0.0) || f <= f0) return 1.0;
+    if (f >= f1) return 0.0;
+    return 0.5 * (1.0 + cospi((f - f0) / (f1 - f0)));
+}
+
+// In-place radix-2 decimation-in-time transform of N = 2^logn complex values in
+// shared memory: input in bit-reversed order, output in natural order,
+// X_m = sum_k x_k exp(sign 2 pi i m k / N).  Twiddles from sincospi of exact
+// dyadic arguments.  All threads of the block call it.
+__device__ void fft_radix2(double *re, double *im, int logn, double sign) {
+    const int N = 1 << logn;
+    for (int st = 0; st < logn; ++st) {
+        const int half = 1 << st;
+        for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+            const int pos = i & (half - 1);
+            const int a = ((i >> st) << (st + 1)) | pos;
+            const int b = a + half;
+            double sn, cs;
+            sincospi(sign * (double)pos / (double)half, &sn, &cs);
+            const double br = re[b], bi = im[b];
+            const double tr = cs * br - sn * bi, ti = cs * bi + sn * br;
+            const double ar = re[a], ai = im[a];
+            re[a] = ar + tr;
+            im[a] = ai + ti;
+            re[b] = ar - tr;
+            im[b] = ai - ti;
+        }
+        __syncthreads();
+    }
+}
+
+// Impedance space-charge field (TRK_LSC with r_b > 0): lambda_k = q_m h_k / dl on
+// the nbins bins, zero-padded to N = 2 nbins, forward transform, times
+// Z_m = i sgn(m') Z0 / (pi kappa r_b^2) (1 - xi K1(xi)) taper (kappa = 2 pi |m'| / (N dl),
+// xi = kappa r_b / gamma, m' the signed frequency index, 0 at m = 0 and at Nyquist),
+// inverse transform, V_k = L c Re(.) / N for k < nbins.  One block; 16 N bytes of
+// dynamic shared memory.
+__global__ void __launch_bounds__(1024) k_lsc_imp(const uint32_t *__restrict__ hist, const BunchState *st, int slot,
+                                                  int nbins, int logn, double qm, double L, double rb, double gamma,
+                                                  double f0, double f1, double *__restrict__ V) {
+    extern __shared__ double sm[];
+    const int N = 1 << logn;
+    double *re = sm, *im = sm + N;
+    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const bool any = kmin <= kmax;
+    const double lmin = any ? dkey_inv(kmin) : 0.0;
+    const double lmax = any ? dkey_inv(kmax) : 0.0;
+    const double dl = (lmax - lmin) / nbins;
+    if (!any || !(dl > 0.0) || nbins < 2) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = 0.0;
+        return;
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int j = (int)(__brev((unsigned)k) >> (32 - logn));
+        re[j] = k < nbins ? __ddiv_rn(__dmul_rn(qm, (double)hist[k]), dl) : 0.0;
+        im[j] = 0.0;
+    }
+    __syncthreads();
+    fft_radix2(re, im, logn, -1.0);
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        const int mp = 2 * m < N ? m : m - N;
+        double zs = 0.0;
+        if (mp != 0 && 2 * m != N) {
+            const double am = (double)(mp > 0 ? mp : -mp);
+            const double kap = 2.0 * kPi * am / ((double)N * dl);
+            const double z = kZ0 / (kPi * kap * rb * rb) * lsc_bracket(kap * rb / gamma) *
+                             lsc_taper(am / (0.5 * (double)N), f0, f1);
+            zs = mp > 0 ? z : -z;
+        }
+        const double a = re[m], b = im[m];
+        re[m] = -zs * b;   // (a + i b)(i zs)
+        im[m] = zs * a;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {   // back to bit-reversed order
+        const int j = (int)(__brev((unsigned)k) >> (32 - logn));
+        if (k < j) {
+            const double tr = re[k], ti = im[k];
+            re[k] = re[j];
+            im[k] = im[j];
+            re[j] = tr;
+            im[j] = ti;
+        }
+    }
+    __syncthreads();
+    fft_radix2(re, im, logn, 1.0);
+    const double scale = L * kClight;
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = scale * (re[k] / (double)N);
+}
+
 int grid_for(int64_t n, int threads, int cap) {
     int64_t g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
@@ -308,6 +439,23 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
 cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double KL,
                              int passes, double *a, double *b, double *V, cudaStream_t s) {
     k_lsc_field<<<1, 1024, 0, s>>>(hist, st, slot, nbins, qm, KL, passes, a, b, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double L,
+                           double rb, double gamma, double f0, double f1, double *V, cudaStream_t s) {
+    if (nbins < 1 || nbins > kLscImpMaxBins || (nbins & (nbins - 1)) != 0) return cudaErrorInvalidValue;
+    int logn = 1;
+    while ((1 << logn) < 2 * nbins) ++logn;
+    const size_t smem = (size_t)2 * (size_t)(1 << logn) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_lsc_imp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(2 * 2 * kLscImpMaxBins * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_lsc_imp<<<1, 1024, smem, s>>>(hist, st, slot, nbins, logn, qm, L, rb, gamma, f0, f1, V);
     return cudaGetLastError();
 }
 

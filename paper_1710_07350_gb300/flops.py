@@ -43,6 +43,22 @@ def wake_conv_flops(nbins):
     return float(nbins) * (nbins + 1)
 
 
+# Space-charge element per alive particle: the same window, bin index and
+# interpolated energy kick as the wake -> 14.
+LSC_FLOPS_PER_PARTICLE = 14
+# One value of the impedance bracket 1 - xi K1(xi): 39 series terms of about
+# 8 flops (or as many quadrature points above xi = 2), plus kappa, Z and the taper.
+LSC_BRACKET_FLOPS = 320
+
+
+def lsc_imp_flops(nbins):
+    """Impedance field of one element pass: two complex transforms of
+    N = 2 nbins points (5 N log2 N each), N impedance values and the complex
+    products (6 each)."""
+    n = 2 * int(nbins)
+    return 2 * 5.0 * n * np.log2(n) + n * (LSC_BRACKET_FLOPS + 6)
+
+
 APERTURE_FLOPS = {None: 0, "rect": 4, "ellipse": 6}
 
 
@@ -79,8 +95,8 @@ def element_flops(el):
         return 12
     if t == "MAP":
         return map_flops(el["map"])
-    if t == "WAKE":
-        return 0  # counted separately (histogram, convolution, kick)
+    if t in ("WAKE", "LSC"):
+        return 0  # counted separately (histogram, field, kick)
     raise ValueError(t)
 
 

@@ -34,7 +34,8 @@ class trk_element_desc(ctypes.Structure):
                 ("length", c_double), ("k1", c_double), ("k2", c_double), ("k2l", c_double),
                 ("volt", c_double), ("phase_deg", c_double), ("freq_hz", c_double),
                 ("wake_w0", c_double), ("wake_sc", c_double), ("charge", c_double), ("wake_w0t", c_double),
-                ("lsc_k", c_double), ("angle", c_double),
+                ("lsc_k", c_double), ("angle", c_double), ("lsc_rb", c_double), ("lsc_mc2", c_double),
+                ("lsc_f0", c_double), ("lsc_f1", c_double),
                 ("C", PD), ("R", PD), ("T", PD), ("U", PD)]
 
 
@@ -185,8 +186,10 @@ def trk_create_lattice(lattice, moments=True):
         elif t == "SBEND":
             d.length, d.angle = el["L"], el["angle"]
         elif t == "LSC":
-            d.nbins, d.length, d.lsc_k, d.charge = el["nbins"], el["L"], el["K"], el["charge"]
+            d.nbins, d.length, d.lsc_k, d.charge = el["nbins"], el["L"], el.get("K", 0.0), el["charge"]
             d.n_kicks = el.get("passes", 0)
+            d.lsc_rb, d.lsc_mc2 = el.get("rb", 0.0), el.get("mc2", 0.0)
+            d.lsc_f0, d.lsc_f1 = el.get("f0", 0.0), el.get("f1", 0.0)
         else:
             raise ValueError(t)
     o = trk_lattice_opts()

@@ -45,6 +45,9 @@ C3_SC = 0.1 * C3_SIGMA_L
 # 1e-6 rad per cavity behind a bunch offset by 100 um (a readable kick, not a
 # physical structure)
 C3_W0T = 1.0e15
+# impedance space charge of the linac variant with space charge: a 3 m
+# structure, 1 mm round beam, low-pass taper from 1/4 to 1/2 of Nyquist
+C3_LSC_L, C3_LSC_RB, C3_LSC_F0, C3_LSC_F1 = 3.0, 1.0e-3, 0.25, 0.5
 K2L_THIN = K2_SEXT * L_SEXT
 # c5 names no sextupole strength; 10x the c4 value makes the DA sextupole-limited
 # inside the +-20 mm aperture (with K2L_THIN it is the aperture rectangle).
@@ -106,15 +109,20 @@ def lattice_c2(cells=C2_CELLS, rf=True):
     return {"name": "c2", "elements": els, "aperture": ("ellipse", 0.015, 0.008), "p0c": P0C_1GEV}
 
 
-def lattice_c3(periods=C3_PERIODS, nbins=C3_NBINS, transverse=False):
+def lattice_c3(periods=C3_PERIODS, nbins=C3_NBINS, transverse=False, lsc=False):
+    """Per period [RFCA, WAKE, (LSC,) drift, quad]; with `transverse` the wake has
+    its dipole part and with `lsc` an impedance space-charge kick follows it, so
+    that a period holds the parts of an RFCW cavity (Table 1)."""
     rf = {"type": "RFCA", "volt": C3_VOLT, "phase_deg": C3_PHASE, "freq_hz": C3_FREQ}
     wk = {"type": "WAKE", "nbins": nbins, "W0": C3_W0, "sc": C3_SC, "charge": C3_CHARGE,
           "W0T": C3_W0T if transverse else 0.0}
+    sc = {"type": "LSC", "nbins": nbins, "L": C3_LSC_L, "charge": C3_CHARGE, "rb": C3_LSC_RB,
+          "mc2": ELECTRON_MASS_EV, "f0": C3_LSC_F0, "f1": C3_LSC_F1}
     dr = _map_elem("D1.0.o2")
     qf, qd = _map_elem("QF.o2"), _map_elem("QD.o2")
     els = []
     for p in range(periods):
-        els += [rf, wk, dr, qf if p % 2 == 0 else qd]
+        els += [rf, wk] + ([sc] if lsc else []) + [dr, qf if p % 2 == 0 else qd]
     return {"name": "c3", "elements": els, "aperture": None, "p0c": P0C_1GEV}
 
 

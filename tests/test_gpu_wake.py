@@ -134,3 +134,47 @@ def test_space_charge_against_oracle(nbins, passes):
     if nbins > 1:
         o0 = orc.track({**lat, "elements": [e for e in lat["elements"] if e["type"] != "LSC"]}, z, 2)
         assert np.max(np.abs(o["z"][:, 5] - o0["z"][:, 5])) > 1e-9
+
+
+MC2_E = 0.51099895e6   # electron rest energy [eV]
+
+
+@pytest.mark.parametrize("nbins,f0,f1,p0c", [(256, 0.0, 0.0, 1.0e8), (4096, 0.2, 0.6, 1.0e8), (1024, 0.0, 0.5, 5e6),
+                                             (1, 0.0, 0.0, 1.0e8)])
+def test_space_charge_impedance_against_oracle(nbins, f0, f1, p0c):
+    """Round-beam impedance space charge (radix-2 transforms on the GPU, direct
+    transforms in the oracle) between drifts, twice per turn, two turns; the
+    counts are bit-exact, the fields agree to the transforms' rounding."""
+    sc = {"type": "LSC", "nbins": nbins, "L": 2.0, "charge": syn.C3_CHARGE, "rb": 1e-3, "mc2": MC2_E,
+          "f0": f0, "f1": f1}
+    lat = {"elements": [sc, {"type": "EDRIFT", "L": 1.0}, sc, {"type": "EDRIFT", "L": 0.5}], "aperture": None,
+           "p0c": p0c}
+    z = syn.bunch("c3", n=30_000, seed=13)
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
+    if nbins > 1:
+        o0 = orc.track({**lat, "elements": [e for e in lat["elements"] if e["type"] != "LSC"]}, z, 2)
+        assert np.max(np.abs(o["z"][:, 5] - o0["z"][:, 5])) > 1e-9
+
+
+def test_space_charge_impedance_in_accelerating_lattice():
+    """gamma follows the reference momentum through an RF cavity between two
+    impedance kicks."""
+    sc = {"type": "LSC", "nbins": 512, "L": 1.0, "charge": syn.C3_CHARGE, "rb": 5e-4, "mc2": MC2_E}
+    rf = {"type": "RFCA", "volt": 2.0e7, "phase_deg": 80.0, "freq_hz": 2.856e9}
+    lat = {"elements": [sc, rf, {"type": "EDRIFT", "L": 1.0}, sc], "aperture": None, "p0c": 2.0e7}
+    z = syn.bunch("c3", n=20_000, seed=17)
+    g = gpu_track(lat, z, 3)
+    o = orc.track(lat, z, 3)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
+
+
+@pytest.mark.parametrize("bad", [{"nbins": 1000}, {"nbins": 8192}, {"rb": -1e-3}, {"mc2": 0.0},
+                                 {"f0": 0.6, "f1": 0.5}, {"f1": 1.5}, {"rb": float("nan")}])
+def test_space_charge_impedance_rejects_bad_parameters(bad):
+    sc = {"type": "LSC", "nbins": 256, "L": 1.0, "charge": 1e-9, "rb": 1e-3, "mc2": MC2_E, **bad}
+    with pytest.raises(trk.TrkError):
+        trk.trk_create_lattice({"elements": [sc], "aperture": None, "p0c": 1e8})
