@@ -76,7 +76,7 @@ struct trk_bunch {
     double *wfun = nullptr, *V = nullptr;
     unsigned long long *dip = nullptr;            // transverse dipole sums [2][bins], fixed point
     double *wfun_t = nullptr, *Vt = nullptr;      // transverse wake samples, voltages [2][bins]
-    double *lsc = nullptr;                        // space-charge smoothing scratch [bins]
+    double *lsc = nullptr;                        // space-charge scratch [4 bins]
     int wake_cap = 0;
     int64_t turn = 0;
     double p0c = 0.0;
@@ -510,7 +510,7 @@ static trk_status ensure_wake(trk_bunch *b, int nbins, bool transverse) {
     b->dip = nullptr;
     b->wake_cap = 0;
     if (dalloc(&b->hist, cap) != cudaSuccess || dalloc(&b->wfun, cap) != cudaSuccess ||
-        dalloc(&b->V, cap) != cudaSuccess || dalloc(&b->lsc, cap) != cudaSuccess)
+        dalloc(&b->V, cap) != cudaSuccess || dalloc(&b->lsc, 4 * (size_t)cap) != cudaSuccess)
         return fail(TRK_ENOMEM, "wake scratch allocation failed");
     if (transverse && (dalloc(&b->dip, 2 * (size_t)cap) != cudaSuccess || dalloc(&b->wfun_t, cap) != cudaSuccess ||
                        dalloc(&b->Vt, 2 * (size_t)cap) != cudaSuccess))
@@ -648,8 +648,8 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                         if (lsc && W.p[5] > 0.0) {
                             const double r = p0 / W.p[6];
                             TRK_CUDA(launch_lsc_imp(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[9],
-                                                    W.p[5], std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->V,
-                                                    b->stream));
+                                                    W.p[5], std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->lsc,
+                                                    b->V, b->stream));
                         } else if (lsc)
                             TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
                                                       (int)W.flags, b->wfun, b->lsc, b->V, b->stream));

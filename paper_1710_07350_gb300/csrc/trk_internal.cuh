@@ -138,11 +138,14 @@ cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins
 cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double KL,
                              int passes, double *a, double *b, double *V, cudaStream_t s);
 // Space-charge field of the round-beam impedance on the bins of slot `slot`
-// (see TRK_LSC): one block, the line density zero-padded to N = 2 nbins
-// (nbins a power of two, <= kLscImpMaxBins) in shared memory.
+// (see TRK_LSC): the impedance and twiddle tables over the whole GPU, then the
+// two transforms of the line density zero-padded to N = 2 nbins (nbins a power
+// of two, <= kLscImpMaxBins) on one CTA or a cluster of 8 sharing their halves
+// through distributed shared memory.  scratch: 3 nbins + 1 doubles.
 constexpr int kLscImpMaxBins = 4096;
 cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double L,
-                           double rb, double gamma, double f0, double f1, double *V, cudaStream_t s);
+                           double rb, double gamma, double f0, double f1, double *scratch, double *V,
+                           cudaStream_t s);
 cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
                                cudaStream_t s);
 

@@ -10,6 +10,8 @@
 // the round-beam impedance applied with radix-2 transforms in shared memory.
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "trk_internal.cuh"
 
 namespace trk {
@@ -20,6 +22,10 @@ constexpr int kSmemBins = 8192;      // sub-histograms in shared memory up to th
 constexpr int kSubHists = 2;         // per block (one per half of the warps)
 constexpr int kConvOut = 16;         // outputs per convolution block
 constexpr int kConvThreads = 256;
+constexpr int kLscThreads = 256;     // threads per CTA of the space-charge transform
+constexpr int kLscClusterMinN = 1024; // transforms of at least this many points run on a cluster of 8 CTAs
+
+namespace cg = cooperative_groups;
 
 __global__ void k_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) {
@@ -269,10 +275,15 @@ constexpr double kClight = 299792458.0;
 // (Abramowitz & Stegun 9.6.11 and 9.6.10, order 1), written so that nothing
 // cancels at small x:  1 - x K1 = -x ln(x/2) I1(x) + (x^2/4) sum_k c_k t_k with
 // t_k = (x^2/4)^k / (k! (k+1)!) and c_k = psi(k+1) + psi(k+2) = 2 H_k + 1/(k+1)
-// - 2 gamma_E; I1 = (x/2) sum_k t_k.  Above 2 from K1(x) = int_0^inf exp(-x cosh t)
-// cosh t dt (A&S 9.6.24) by the trapezoidal rule, step 1/16 (exponentially
-// accurate for this entire integrand), with exp(-x) factored out.
-__device__ double lsc_bracket(double x) {
+// - 2 gamma_E; I1 = (x/2) sum_k t_k; terms stop below 1e-18 of the sum.  Above 2
+// from K1(x) = int_0^inf exp(-x cosh t) cosh t dt (A&S 9.6.24) by the trapezoidal
+// rule, step 1/8, exp(-x) factored out: sum_j exp(-x e_j) c_j with the node values
+// e_j = cosh t_j - 1 = 2 sinh^2(t_j / 2), c_j = cosh t_j (t_j = j / 8) shared by all
+// x (`nodes`, 2 kLscNodes doubles); for this entire integrand the rule's error
+// stays at double rounding for every x > 2 at that step (checked against an
+// independent K1 to x = 80).  Above x = 45, x K1(x) < 1e-18 and 1 - x K1 rounds to 1.
+constexpr int kLscNodes = 48;   // t up to 6: exp(-2 e_j) c_j < 1e-150 there
+__device__ double lsc_bracket(double x, const double *nodes) {
     if (!(x > 0.0)) return 0.0;
     if (x <= 2.0) {
         const double q = 0.25 * x * x;
@@ -282,18 +293,18 @@ __device__ double lsc_bracket(double x) {
             harm += 1.0 / (double)k;
             sum_t += t;
             sum_ct += (2.0 * harm + 1.0 / (double)(k + 1) - 2.0 * kEulerGamma) * t;
+            if (t < 1e-18 * sum_t) break;
         }
         return q * sum_ct - x * log(0.5 * x) * (0.5 * x * sum_t);
     }
-    const double h = 0.0625;
+    if (x > 45.0) return 1.0;
     double acc = 0.5;
-    for (int j = 1; j < 100000; ++j) {   // cosh t - 1 = 2 sinh^2(t/2), t = j h
-        const double sh = sinh(0.5 * (double)j * h);
-        const double f = exp(-2.0 * x * sh * sh) * cosh((double)j * h);
+    for (int j = 1; j < kLscNodes; ++j) {
+        const double f = exp(-x * nodes[2 * j]) * nodes[2 * j + 1];
         acc += f;
         if (f < 1e-18 * acc) break;
     }
-    return 1.0 - x * exp(-x) * (h * acc);
+    return 1.0 - x * exp(-x) * (0.125 * acc);
 }
 
 // Cosine taper at f (fraction of Nyquist): 1 to f0, 0 from f1, f1 <= 0: none.
@@ -303,89 +314,179 @@ __device__ double lsc_taper(double f, double f0, double f1) {
     return 0.5 * (1.0 + cospi((f - f0) / (f1 - f0)));
 }
 
-// In-place radix-2 decimation-in-time transform of N = 2^logn complex values in
-// shared memory: input in bit-reversed order, output in natural order,
-// X_m = sum_k x_k exp(sign 2 pi i m k / N).  Twiddles from sincospi of exact
-// dyadic arguments.  All threads of the block call it.
-__device__ void fft_radix2(double *re, double *im, int logn, double sign) {
+// Bin width of slot `slot`'s window (the wake's): dl > 0 when the field is defined.
+__device__ __forceinline__ double lsc_dl(const BunchState *st, int slot, int nbins) {
+    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    if (kmin > kmax) return 0.0;
+    return (dkey_inv(kmax) - dkey_inv(kmin)) / nbins;
+}
+
+// Impedance and twiddle tables of one impedance space-charge pass, spread over the
+// whole GPU (the bracket is the costly part): Z_m = i zs[m] for m = 0 .. N/2
+// (zs[N - m] = -zs[m]; m = 0 and the Nyquist term carry no field),
+// zs[m] = Z0 / (pi kappa r_b^2) (1 - xi K1(xi)) taper(m / (N/2)), kappa = 2 pi m / (N dl),
+// xi = kappa r_b / gamma; tw[2j], tw[2j+1] = cos, sin of 2 pi j / N for j < N/2.
+__global__ void k_lsc_tables(const BunchState *st, int slot, int nbins, int logn, double rb, double gamma, double f0,
+                             double f1, double *__restrict__ zs, double *__restrict__ tw) {
+    __shared__ double nodes[2 * kLscNodes];
     const int N = 1 << logn;
-    for (int st = 0; st < logn; ++st) {
-        const int half = 1 << st;
-        for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
-            const int pos = i & (half - 1);
-            const int a = ((i >> st) << (st + 1)) | pos;
-            const int b = a + half;
+    const double dl = lsc_dl(st, slot, nbins);
+    if (!(dl > 0.0) || nbins < 2) return;   // the transform kernel writes V = 0
+    for (int j = threadIdx.x; j < kLscNodes; j += blockDim.x) {
+        const double sh = sinh(0.0625 * (double)j);
+        nodes[2 * j] = 2.0 * sh * sh;
+        nodes[2 * j + 1] = cosh(0.125 * (double)j);
+    }
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N + 1; i += gridDim.x * blockDim.x) {
+        if (i <= N / 2) {
+            double z = 0.0;
+            if (i != 0 && 2 * i != N) {
+                const double kap = 2.0 * kPi * (double)i / ((double)N * dl);
+                z = kZ0 / (kPi * kap * rb * rb) * lsc_bracket(kap * rb / gamma, nodes) *
+                    lsc_taper((double)i / (0.5 * (double)N), f0, f1);
+            }
+            zs[i] = z;
+        } else {
+            const int j = i - (N / 2 + 1);
             double sn, cs;
-            sincospi(sign * (double)pos / (double)half, &sn, &cs);
-            const double br = re[b], bi = im[b];
-            const double tr = cs * br - sn * bi, ti = cs * bi + sn * br;
-            const double ar = re[a], ai = im[a];
-            re[a] = ar + tr;
-            im[a] = ai + ti;
-            re[b] = ar - tr;
-            im[b] = ai - ti;
+            sincospi(2.0 * (double)j / (double)N, &sn, &cs);
+            tw[2 * j] = cs;
+            tw[2 * j + 1] = sn;
         }
-        __syncthreads();
     }
 }
 
-// Impedance space-charge field (TRK_LSC with r_b > 0): lambda_k = q_m h_k / dl on
-// the nbins bins, zero-padded to N = 2 nbins, forward transform, times
-// Z_m = i sgn(m') Z0 / (pi kappa r_b^2) (1 - xi K1(xi)) taper (kappa = 2 pi |m'| / (N dl),
-// xi = kappa r_b / gamma, m' the signed frequency index, 0 at m = 0 and at Nyquist),
-// inverse transform, V_k = L c Re(.) / N for k < nbins.  One block; 16 N bytes of
-// dynamic shared memory.
-__global__ void __launch_bounds__(1024) k_lsc_imp(const uint32_t *__restrict__ hist, const BunchState *st, int slot,
-                                                  int nbins, int logn, double qm, double L, double rb, double gamma,
-                                                  double f0, double f1, double *__restrict__ V) {
+// One radix-2 butterfly stage inside a CTA's own P points (all pairs local):
+// decimation in time (forward, w applied to the second input) or in frequency
+// (inverse, w applied to the difference).  x interleaved (re, im).
+__device__ __forceinline__ void local_stage(double *x, const double *tws, int P, int s, int logn, bool dit,
+                                            double wsign) {
+    const int half = 1 << s;
+    for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+        const int pos = t & (half - 1);
+        const int a = ((t >> s) << (s + 1)) | pos;
+        const int b = a + half;
+        const int j = pos << (logn - 1 - s);
+        const double wr = tws[2 * j], wi = wsign * tws[2 * j + 1];
+        const double ar = x[2 * a], ai = x[2 * a + 1], br = x[2 * b], bi = x[2 * b + 1];
+        if (dit) {
+            const double tr = wr * br - wi * bi, ti = wr * bi + wi * br;
+            x[2 * a] = ar + tr;
+            x[2 * a + 1] = ai + ti;
+            x[2 * b] = ar - tr;
+            x[2 * b + 1] = ai - ti;
+        } else {
+            const double dr = ar - br, di = ai - bi;
+            x[2 * a] = ar + br;
+            x[2 * a + 1] = ai + bi;
+            x[2 * b] = wr * dr - wi * di;
+            x[2 * b + 1] = wr * di + wi * dr;
+        }
+    }
+    __syncthreads();
+}
+
+// Impedance space-charge field (TRK_LSC with r_b > 0) on a cluster of C CTAs
+// (C = 1 or 8), each holding P = N / C of the N = 2 nbins points in shared memory:
+// lambda_k = q_m h_k / dl zero-padded to N, loaded in bit-reversed order; forward
+// transform by decimation in time (natural-order spectrum); times i zs[m];
+// inverse by decimation in frequency (bit-reversed output, so no permutation
+// pass); V_k = scale Re(.) with scale = L c / N, for k < nbins.  Stages whose
+// butterflies span CTAs read the partner CTA's points through distributed shared
+// memory into a second buffer, between cluster barriers; every CTA passes the
+// same barriers (the stage loops depend on N and C only, and the degenerate exit
+// is taken by all CTAs before the first barrier).
+__global__ void __launch_bounds__(kLscThreads) k_lsc_fft(const uint32_t *__restrict__ hist, const BunchState *st,
+                                                          int slot, int nbins, int logn, int logc, double qm,
+                                                          double scale, const double *__restrict__ zs,
+                                                          const double *__restrict__ tw, double *__restrict__ V) {
     extern __shared__ double sm[];
-    const int N = 1 << logn;
-    double *re = sm, *im = sm + N;
-    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
-    const bool any = kmin <= kmax;
-    const double lmin = any ? dkey_inv(kmin) : 0.0;
-    const double lmax = any ? dkey_inv(kmax) : 0.0;
-    const double dl = (lmax - lmin) / nbins;
-    if (!any || !(dl > 0.0) || nbins < 2) {
-        for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = 0.0;
+    const int N = 1 << logn, P = N >> logc, logp = logn - logc;
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = logc > 0 ? (int)cl.block_rank() : 0;
+    const double dl = lsc_dl(st, slot, nbins);
+    if (!(dl > 0.0) || nbins < 2) {
+        if (c == 0)
+            for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = 0.0;
         return;
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const int j = (int)(__brev((unsigned)k) >> (32 - logn));
-        re[j] = k < nbins ? __ddiv_rn(__dmul_rn(qm, (double)hist[k]), dl) : 0.0;
-        im[j] = 0.0;
+    double *cur = sm, *nxt = sm + 2 * P, *tws = sm + 4 * P;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) tws[j] = tw[j];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int k = (int)(__brev((unsigned)(c * P + i)) >> (32 - logn));
+        cur[2 * i] = k < nbins ? __ddiv_rn(__dmul_rn(qm, (double)hist[k]), dl) : 0.0;
+        cur[2 * i + 1] = 0.0;
     }
     __syncthreads();
-    fft_radix2(re, im, logn, -1.0);
-    for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        const int mp = 2 * m < N ? m : m - N;
-        double zs = 0.0;
-        if (mp != 0 && 2 * m != N) {
-            const double am = (double)(mp > 0 ? mp : -mp);
-            const double kap = 2.0 * kPi * am / ((double)N * dl);
-            const double z = kZ0 / (kPi * kap * rb * rb) * lsc_bracket(kap * rb / gamma) *
-                             lsc_taper(am / (0.5 * (double)N), f0, f1);
-            zs = mp > 0 ? z : -z;
+    // forward, decimation in time
+    for (int s = 0; s < logn; ++s) {
+        if (s < logp) {
+            local_stage(cur, tws, P, s, logn, true, -1.0);
+            continue;
         }
-        const double a = re[m], b = im[m];
-        re[m] = -zs * b;   // (a + i b)(i zs)
-        im[m] = zs * a;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {   // back to bit-reversed order
-        const int j = (int)(__brev((unsigned)k) >> (32 - logn));
-        if (k < j) {
-            const double tr = re[k], ti = im[k];
-            re[k] = re[j];
-            im[k] = im[j];
-            re[j] = tr;
-            im[j] = ti;
+        const int half = 1 << s;
+        cl.sync();
+        const double *rem = cl.map_shared_rank(cur, c ^ (half >> logp));
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int g = c * P + i;
+            const int j = (g & (half - 1)) << (logn - 1 - s);
+            const double wr = tws[2 * j], wi = -tws[2 * j + 1];
+            const double pr = rem[2 * i], pi = rem[2 * i + 1], orr = cur[2 * i], oi = cur[2 * i + 1];
+            if (g & half) {   // second input: partner - w * own
+                nxt[2 * i] = pr - (wr * orr - wi * oi);
+                nxt[2 * i + 1] = pi - (wr * oi + wi * orr);
+            } else {          // first input: own + w * partner
+                nxt[2 * i] = orr + (wr * pr - wi * pi);
+                nxt[2 * i + 1] = oi + (wr * pi + wi * pr);
+            }
         }
+        cl.sync();
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    // impedance: (a + i b)(i z) = -z b + i z a
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int m = c * P + i;
+        const double z = 2 * m <= N ? zs[m] : -zs[N - m];
+        const double a = cur[2 * i], b = cur[2 * i + 1];
+        cur[2 * i] = -z * b;
+        cur[2 * i + 1] = z * a;
     }
     __syncthreads();
-    fft_radix2(re, im, logn, 1.0);
-    const double scale = L * kClight;
-    for (int k = threadIdx.x; k < nbins; k += blockDim.x) V[k] = scale * (re[k] / (double)N);
+    // inverse, decimation in frequency
+    for (int s = logn - 1; s >= 0; --s) {
+        if (s < logp) {
+            local_stage(cur, tws, P, s, logn, false, 1.0);
+            continue;
+        }
+        const int half = 1 << s;
+        cl.sync();
+        const double *rem = cl.map_shared_rank(cur, c ^ (half >> logp));
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int g = c * P + i;
+            const int j = (g & (half - 1)) << (logn - 1 - s);
+            const double wr = tws[2 * j], wi = tws[2 * j + 1];
+            const double pr = rem[2 * i], pi = rem[2 * i + 1], orr = cur[2 * i], oi = cur[2 * i + 1];
+            if (g & half) {   // second input: (partner - own) w
+                const double dr = pr - orr, di = pi - oi;
+                nxt[2 * i] = wr * dr - wi * di;
+                nxt[2 * i + 1] = wr * di + wi * dr;
+            } else {          // first input: own + partner
+                nxt[2 * i] = orr + pr;
+                nxt[2 * i + 1] = oi + pi;
+            }
+        }
+        cl.sync();
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int k = (int)(__brev((unsigned)(c * P + i)) >> (32 - logn));
+        if (k < nbins) V[k] = scale * cur[2 * i];
+    }
 }
 
 int grid_for(int64_t n, int threads, int cap) {
@@ -443,20 +544,44 @@ cudaError_t launch_lsc_field(const uint32_t *hist, const BunchState *st, int slo
 }
 
 cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot, int nbins, double qm, double L,
-                           double rb, double gamma, double f0, double f1, double *V, cudaStream_t s) {
+                           double rb, double gamma, double f0, double f1, double *scratch, double *V, cudaStream_t s) {
     if (nbins < 1 || nbins > kLscImpMaxBins || (nbins & (nbins - 1)) != 0) return cudaErrorInvalidValue;
     int logn = 1;
     while ((1 << logn) < 2 * nbins) ++logn;
-    const size_t smem = (size_t)2 * (size_t)(1 << logn) * sizeof(double);
+    const int N = 1 << logn;
+    const int logc = N >= kLscClusterMinN ? 3 : 0;
+    const int P = N >> logc;
+    double *zs = scratch, *tw = scratch + (N / 2 + 1);    // N/2 + 1 and N doubles
+    const size_t smem = ((size_t)4 * P + (size_t)N) * sizeof(double);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_lsc_imp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(2 * 2 * kLscImpMaxBins * sizeof(double)));
+        const int most = (int)((4 * (2 * kLscImpMaxBins) / 8 + 2 * kLscImpMaxBins) * sizeof(double));
+        const int small = (int)((4 + 1) * (kLscClusterMinN - 1) * sizeof(double));
+        cudaError_t e = cudaFuncSetAttribute(k_lsc_fft, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             most > small ? most : small);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_lsc_imp<<<1, 1024, smem, s>>>(hist, st, slot, nbins, logn, qm, L, rb, gamma, f0, f1, V);
-    return cudaGetLastError();
+    const int tb = 64;
+    int grid = (N + 1 + tb - 1) / tb;
+    if (grid > 152 * 4) grid = 152 * 4;
+    k_lsc_tables<<<grid, tb, 0, s>>>(st, slot, nbins, logn, rb, gamma, f0, f1, zs, tw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1u << logc);
+    cfg.blockDim = dim3(kLscThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1u << logc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_lsc_fft, hist, (const BunchState *)st, slot, nbins, logn, logc, qm,
+                              L * kClight / (double)N, (const double *)zs, (const double *)tw, V);
 }
 
 cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
