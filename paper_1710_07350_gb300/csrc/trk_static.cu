@@ -20,6 +20,7 @@
 #include <mutex>
 #include <string>
 
+#include "trk_bins.cuh"
 #include "trk_internal.cuh"
 
 namespace trk {
@@ -109,12 +110,11 @@ __global__ void __launch_bounds__(kThreads) k_static_hist(const double *__restri
         for (int i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0u;
         __syncthreads();
     }
+    double rdl_s;
+    long long bin_m;
+    bin_consts(dl, nbins, rdl_s, bin_m);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int b = 0;
-        if (dl > 0.0) {
-            const double u = floor(__ddiv_rn(__dsub_rn(coords[4 * pitch + i], lmin), dl));
-            b = !(u >= 0.0) ? 0 : (u > (double)(nbins - 1) ? nbins - 1 : (int)u);
-        }
+        const int b = bin_of(coords[4 * pitch + i], lmin, dl, rdl_s, bin_m, nbins);
         if (smem)
             atomicAdd(sh + b, 1u);
         else

@@ -12,6 +12,7 @@
 
 #include <cooperative_groups.h>
 
+#include "trk_bins.cuh"
 #include "trk_internal.cuh"
 
 namespace trk {
@@ -73,14 +74,6 @@ __global__ void k_wake_minmax(const double *__restrict__ coords, int64_t pitch, 
 }
 
 // Bin index exactly as floor((l - lmin) / dl) in IEEE double, clamped.
-__device__ __forceinline__ int bin_of(double l, double lmin, double dl, int nbins) {
-    if (!(dl > 0.0)) return 0;
-    const double u = floor(__ddiv_rn(__dsub_rn(l, lmin), dl));
-    if (!(u >= 0.0)) return 0;
-    if (u > (double)(nbins - 1)) return nbins - 1;
-    return (int)u;
-}
-
 // A finite offset in fixed point (round to nearest); a non-finite one carries no
 // dipole moment.
 __device__ __forceinline__ unsigned long long dipole_units(double x) {
@@ -101,6 +94,9 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     const double lmin = any ? dkey_inv(kmin) : 0.0;
     const double lmax = any ? dkey_inv(kmax) : 0.0;
     const double dl = (lmax - lmin) / nbins;
+    double rdl_s;
+    long long bin_m;
+    bin_consts(dl, nbins, rdl_s, bin_m);
     // wake function samples W(m dl) = w0 / sqrt(max(m dl, s_c))
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nbins; m += gridDim.x * blockDim.x) {
         const double s = (double)m * dl;
@@ -122,7 +118,7 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     uint32_t *mine = sh + ((threadIdx.x >> 5) % kSubHists) * nbins;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (lt[i] >= 0) continue;
-        const int b = bin_of(coords[4 * pitch + i], lmin, dl, nbins);
+        const int b = bin_of(coords[4 * pitch + i], lmin, dl, rdl_s, bin_m, nbins);
         if (smem)
             atomicAdd(mine + b, 1u);
         else
