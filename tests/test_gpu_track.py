@@ -268,3 +268,28 @@ def test_sbend_zero_angle_is_the_exact_drift():
     g = gpu_track(lat, z, 3)
     o = orc.track(lat, z, 3)
     compare_tracking(g, o, TOL_PASS * 10)
+
+
+def test_sbend_particles_that_cannot_reach_the_exit_face_are_lost_alike():
+    """Far off-axis and steep particles (asin argument outside [-1, 1], |y'| beyond
+    the momentum, momentum down to 0.1 of the reference): their coordinates turn
+    NaN and both sides lose them at the bend; the steep survivors agree to
+    rounding amplified by the near-tangent exits (relative 1e-11)."""
+    lat = {"elements": [{"type": "SBEND", "L": 1.0, "angle": 0.5}, {"type": "EDRIFT", "L": 0.1}],
+           "aperture": ("rect", 5.0, 5.0), "p0c": syn.P0C_1GEV}
+    g = np.random.Generator(np.random.Philox(key=23))
+    n = 4000
+    z = np.zeros((n, 6))
+    z[:, 0] = g.uniform(-3.0, 3.0, n)
+    z[:, 1] = g.uniform(-2.0, 2.0, n)
+    z[:, 2] = g.uniform(-0.01, 0.01, n)
+    z[:, 3] = g.uniform(-1.5, 1.5, n)
+    z[:, 5] = g.uniform(-0.9, 0.5, n)
+    gp = gpu_track(lat, z, 1)
+    o = orc.track(lat, z, 1)
+    gz, alive, lt, le = by_id(gp, n)
+    oa = o["alive"].astype(bool)
+    assert np.array_equal(alive, oa) and 1000 < np.sum(~oa) < n - 1000
+    assert np.all(le[~oa] == 0) and np.all(o["loss_elem"][~oa] == 0)
+    rel = np.abs(gz[oa] - o["z"][oa]) / np.maximum(1.0, np.abs(o["z"][oa]))
+    assert np.max(rel) <= 1e-11

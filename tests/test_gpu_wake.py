@@ -178,3 +178,19 @@ def test_space_charge_impedance_rejects_bad_parameters(bad):
     sc = {"type": "LSC", "nbins": 256, "L": 1.0, "charge": 1e-9, "rb": 1e-3, "mc2": MC2_E, **bad}
     with pytest.raises(trk.TrkError):
         trk.trk_create_lattice({"elements": [sc], "aperture": None, "p0c": 1e8})
+
+
+def test_wake_histogram_on_and_next_to_bin_edges():
+    """Particles placed on the bin edges and one ulp either side (where the
+    division-free bin index defers to the division): counts bit-exact."""
+    nb = 1000
+    lmin, lmax = -1.234e-4, 3.21e-4
+    dl = (lmax - lmin) / nb
+    edges = lmin + np.arange(nb + 1) * dl
+    l = np.concatenate([edges, np.nextafter(edges, np.inf), np.nextafter(edges, -np.inf), [lmin, lmax]])
+    z = np.zeros((l.size, 6))
+    z[:, 4] = np.clip(l, lmin, lmax)
+    g, gh, gV = gpu_wake(z, nb, syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
+    o, oh, oV = orc.wake(z, nb, syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
+    assert np.array_equal(gh, oh)
+    assert np.allclose(gV, oV, rtol=1e-13, atol=0)
