@@ -334,11 +334,16 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.ap_type = opts->aperture;
     v.ap_a = opts->a;
     v.ap_b = opts->b;
-    std::memcpy(&v.ap_a_bits, &opts->a, 8);
-    std::memcpy(&v.ap_b_bits, &opts->b, 8);
-    const double ia = 0.7 * opts->a, ib = 0.7 * opts->b;
-    std::memcpy(&v.ap_ia_bits, &ia, 8);
-    std::memcpy(&v.ap_ib_bits, &ib, 8);
+    // |x| <= a as integers: bit patterns of the positive bounds shifted left by one
+    const auto key = [](double v) {
+        uint64_t u;
+        std::memcpy(&u, &v, 8);
+        return (unsigned long long)(u << 1);
+    };
+    v.ap_a_key = key(opts->a);
+    v.ap_b_key = key(opts->b);
+    v.ap_ia_key = key(0.7 * opts->a);
+    v.ap_ib_key = key(0.7 * opts->b);
     *out = L;
     return TRK_OK;
 }

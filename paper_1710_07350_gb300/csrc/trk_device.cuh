@@ -32,21 +32,24 @@ __device__ __noinline__ bool ellipse_exact(double x, double y, double a, double 
     return __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) <= 1.0;
 }
 
+// |x| as an unsigned integer: the bit pattern shifted left by one, so the sign
+// bit drops out and every NaN, whatever its sign, compares above every finite
+// value.  (A sign mask would not do: the compiler may turn it into a
+// floating-point absolute value, which keeps the sign of a NaN on this GPU, so a
+// NaN produced with its sign bit set compared as negative and stayed inside.)
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) << 1;
+}
+
 // Aperture test (Sec. 2.5 limit_amplitudes, RCOL, ECOL).  The rectangle is an
-// integer compare of |x|, |y| bit patterns (NaN has the largest pattern and is
-// outside); the ellipse accepts the inner box |x| <= 0.7 a, |y| <= 0.7 b the same
-// way ((0.7)^2 + (0.7)^2 < 1) and otherwise takes the exact test, rounded as
+// integer compare of the abs_key of x, y with those of a, b (NaN is outside); the
+// ellipse accepts the inner box |x| <= 0.7 a, |y| <= 0.7 b the same way
+// ((0.7)^2 + (0.7)^2 < 1) and otherwise takes the exact test, rounded as
 // (x/a)^2 + (y/b)^2 <= 1 in IEEE double.
 __device__ __forceinline__ bool inside(double x, double y, const LatticeView &L) {
-    if (L.ap_type == TRK_APERTURE_RECT) {
-        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
-        return (ax <= L.ap_a_bits) & (ay <= L.ap_b_bits);
-    }
+    if (L.ap_type == TRK_APERTURE_RECT) return (abs_key(x) <= L.ap_a_key) & (abs_key(y) <= L.ap_b_key);
     if (L.ap_type == TRK_APERTURE_ELLIPSE) {
-        const long long ax = __double_as_longlong(x) & 0x7fffffffffffffffll;
-        const long long ay = __double_as_longlong(y) & 0x7fffffffffffffffll;
-        if ((ax <= L.ap_ia_bits) & (ay <= L.ap_ib_bits)) return true;
+        if ((abs_key(x) <= L.ap_ia_key) & (abs_key(y) <= L.ap_ib_key)) return true;
         return ellipse_exact(x, y, L.ap_a, L.ap_b);
     }
     return true;

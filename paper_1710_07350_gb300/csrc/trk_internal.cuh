@@ -55,8 +55,8 @@ struct LatticeView {
     int32_t n_elem;
     int32_t ap_type;
     double ap_a, ap_b;
-    long long ap_a_bits, ap_b_bits;   // bit patterns of a, b (> 0): |x| <= a as integers
-    long long ap_ia_bits, ap_ib_bits; // bit patterns of 0.7 a, 0.7 b: inner box of the ellipse
+    unsigned long long ap_a_key, ap_b_key;   // bit patterns of a, b (> 0) shifted left by one
+    unsigned long long ap_ia_key, ap_ib_key; // the same of 0.7 a, 0.7 b: inner box of the ellipse
 };
 
 // Device-resident bunch state.

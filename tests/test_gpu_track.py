@@ -293,3 +293,21 @@ def test_sbend_particles_that_cannot_reach_the_exit_face_are_lost_alike():
     assert np.all(le[~oa] == 0) and np.all(o["loss_elem"][~oa] == 0)
     rel = np.abs(gz[oa] - o["z"][oa]) / np.maximum(1.0, np.abs(o["z"][oa]))
     assert np.max(rel) <= 1e-11
+
+
+@pytest.mark.parametrize("ap", [("rect", 0.01, 0.01), ("ellipse", 0.01, 0.01)])
+def test_nan_of_either_sign_is_lost(ap):
+    """NaN coordinates with the sign bit set or clear are outside every aperture."""
+    n = 512
+    z = np.zeros((n, 6))
+    z[:, 0] = 1e-3
+    neg = np.copysign(np.nan, -1.0)
+    z[0::4, 0] = neg
+    z[1::4, 2] = neg
+    z[2::4, 0] = np.nan
+    lat = {"elements": [{"type": "EDRIFT", "L": 0.1}], "aperture": ap, "p0c": syn.P0C_1GEV}
+    g = gpu_track(lat, z, 1)
+    o = orc.track(lat, z, 1)
+    _, alive, lt, le = by_id(g, n)
+    assert np.array_equal(alive, o["alive"].astype(bool)) and np.sum(~alive) == 3 * n // 4
+    assert np.all(le[~alive] == 0)
