@@ -49,7 +49,10 @@ struct trk_lattice {
     LatticeView view{};
     int moments = 1;
     double p0c = 0.0;
-    std::vector<int> wakes;  // element indices of TRK_WAKE
+    std::vector<int> wakes;  // element indices of TRK_WAKE and TRK_LSC
+    // collective groups: one collective element, or two adjacent ones (second >= 0),
+    // which share one l window and kick together in the next segment's prologue
+    std::vector<std::pair<int, int>> groups;
     int max_bins = 0;
     bool transverse = false; // a wake with a transverse part
 };
@@ -76,6 +79,7 @@ struct trk_bunch {
     double *wfun = nullptr, *V = nullptr;
     unsigned long long *dip = nullptr;            // transverse dipole sums [2][bins], fixed point
     double *wfun_t = nullptr, *Vt = nullptr;      // transverse wake samples, voltages [2][bins]
+    double *V2 = nullptr, *Vt2 = nullptr;         // voltages of the second element of a group
     double *lsc = nullptr;                        // space-charge scratch [4 bins]
     int wake_cap = 0;
     int64_t turn = 0;
@@ -309,6 +313,12 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
         }
         L->elems.push_back(E);
     }
+    for (int w : L->wakes) {
+        if (!L->groups.empty() && L->groups.back().second < 0 && L->groups.back().first + 1 == w)
+            L->groups.back().second = w;
+        else
+            L->groups.push_back({w, -1});
+    }
     cudaError_t e1 = dalloc(&L->d_elems, L->elems.size());
     cudaError_t e2 = dalloc(&L->d_terms, L->terms.size());
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -386,6 +396,8 @@ static void free_bunch_scratch(trk_bunch *b) {
     cudaFree(b->dip);
     cudaFree(b->wfun_t);
     cudaFree(b->Vt);
+    cudaFree(b->V2);
+    cudaFree(b->Vt2);
     cudaFree(b->lsc);
 }
 
@@ -509,16 +521,20 @@ static trk_status ensure_wake(trk_bunch *b, int nbins, bool transverse) {
     cudaFree(b->dip);
     cudaFree(b->wfun_t);
     cudaFree(b->Vt);
+    cudaFree(b->V2);
+    cudaFree(b->Vt2);
     cudaFree(b->lsc);
     b->hist = nullptr;
-    b->wfun = b->V = b->wfun_t = b->Vt = b->lsc = nullptr;
+    b->wfun = b->V = b->wfun_t = b->Vt = b->lsc = b->V2 = b->Vt2 = nullptr;
     b->dip = nullptr;
     b->wake_cap = 0;
     if (dalloc(&b->hist, cap) != cudaSuccess || dalloc(&b->wfun, cap) != cudaSuccess ||
-        dalloc(&b->V, cap) != cudaSuccess || dalloc(&b->lsc, 4 * (size_t)cap) != cudaSuccess)
+        dalloc(&b->V, cap) != cudaSuccess || dalloc(&b->V2, cap) != cudaSuccess ||
+        dalloc(&b->lsc, 4 * (size_t)cap) != cudaSuccess)
         return fail(TRK_ENOMEM, "wake scratch allocation failed");
     if (transverse && (dalloc(&b->dip, 2 * (size_t)cap) != cudaSuccess || dalloc(&b->wfun_t, cap) != cudaSuccess ||
-                       dalloc(&b->Vt, 2 * (size_t)cap) != cudaSuccess))
+                       dalloc(&b->Vt, 2 * (size_t)cap) != cudaSuccess ||
+                       dalloc(&b->Vt2, 2 * (size_t)cap) != cudaSuccess))
         return fail(TRK_ENOMEM, "transverse wake scratch allocation failed");
     b->wake_cap = cap;
     return TRK_OK;
@@ -563,8 +579,10 @@ static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     a.partials = b->partials;
     a.tile_alive = b->tile_alive;
     a.kick_wake = -1;
+    a.kick_wake2 = -1;
     a.minmax_slot = -1;
     a.wake_V = b->V;
+    a.wake_V2 = b->V2;
     a.tile = b->block * b->per_thread;
     return a;
 }
@@ -610,65 +628,84 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
             TRK_CUDA(track_launch(b, a, n_tiles));
             for (int t = 0; t < nt; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
         } else {
-            const int nw = (int)L->wakes.size();
+            const int ng = (int)L->groups.size();
+            const auto transverse = [&](int e) {
+                return e >= 0 && L->elems[e].type == TRK_WAKE && L->elems[e].p[3] != 0.0;
+            };
+            // histogram and field of collective element e on the window of `slot`,
+            // voltages into V (and the transverse ones into Vt)
+            const auto collective = [&](int e, int slot, double p0, double *V, double *Vt) -> trk_status {
+                const DevElem &W = L->elems[e];
+                const bool lsc = W.type == TRK_LSC;
+                const bool tr = transverse(e);
+                TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, lsc ? 0.0 : W.p[0],
+                                          lsc ? 1.0 : W.p[1], b->hist, b->wfun, lsc ? 0.0 : W.p[3],
+                                          tr ? b->dip : nullptr, b->wfun_t, b->n, b->stream));
+                if (lsc && W.p[5] > 0.0) {
+                    const double r = p0 / W.p[6];
+                    TRK_CUDA(launch_lsc_imp(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[9], W.p[5],
+                                            std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->lsc, V, b->stream));
+                    b->launches += 3;
+                } else {
+                    if (lsc)
+                        TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
+                                                  (int)W.flags, b->wfun, b->lsc, V, b->stream));
+                    else
+                        TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, V, b->stream));
+                    b->launches += 2;
+                }
+                if (tr) {
+                    TRK_CUDA(launch_wake_conv_t(b->dip, b->wfun_t, W.n, W.p[2] * qm_base, Vt, b->stream));
+                    ++b->launches;
+                }
+                return TRK_OK;
+            };
             for (int t = 0; t < nt; ++t) {
-                int e_start = 0, prev_wake = -1, prev_slot = 0;
+                int e_start = 0, prev = -1, prev2 = -1, prev_slot = 0;
                 double p0 = b->p0c;
-                for (int s = 0; s <= nw; ++s) {
-                    const int e_end = s < nw ? L->wakes[s] : ne;
+                for (int s = 0; s <= ng; ++s) {
+                    const int e_first = s < ng ? L->groups[s].first : ne;
+                    const int e_second = s < ng ? L->groups[s].second : -1;
                     const int slot = s & 1;
                     TrackArgs g = a;
                     g.e0 = e_start;
-                    g.e1 = e_end;
+                    g.e1 = e_first;
                     g.n_turns = 1;
                     g.turn_abs0 = (int32_t)(b->turn + t0 + t);
                     g.local_turn0 = t;
-                    g.kick_wake = prev_wake;
+                    g.kick_wake = prev;
+                    g.kick_wake2 = prev2;
                     g.kick_slot = prev_slot;
-                    g.wake_nbins = prev_wake >= 0 ? L->elems[prev_wake].n : 0;
-                    g.wake_Vx = prev_wake >= 0 && L->elems[prev_wake].type == TRK_WAKE &&
-                                        L->elems[prev_wake].p[3] != 0.0
-                                    ? b->Vt
-                                    : nullptr;
-                    g.minmax_slot = s < nw ? slot : -1;
-                    g.do_moments = L->moments && s == nw;
+                    g.wake_nbins = prev >= 0 ? L->elems[prev].n : 0;
+                    g.wake_Vx = transverse(prev) ? b->Vt : nullptr;
+                    g.wake_nbins2 = prev2 >= 0 ? L->elems[prev2].n : 0;
+                    g.wake_Vx2 = transverse(prev2) ? b->Vt2 : nullptr;
+                    g.minmax_slot = s < ng ? slot : -1;
+                    g.do_moments = L->moments && s == ng;
                     g.p0c = p0;
-                    if (s < nw) {
-                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist,
-                                                   L->elems[e_end].type == TRK_WAKE && L->elems[e_end].p[3] != 0.0
-                                                       ? b->dip
-                                                       : nullptr,
-                                                   L->elems[e_end].n, b->stream));
+                    if (s < ng) {
+                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist, transverse(e_first) ? b->dip : nullptr,
+                                                   L->elems[e_first].n, true, b->stream));
                         ++b->launches;
                     }
                     TRK_CUDA(track_launch(b, g, n_tiles));
-                    p0 = advance_p0(L, e_start, e_end, p0);
-                    if (s < nw) {
-                        const DevElem &W = L->elems[e_end];
-                        const bool lsc = W.type == TRK_LSC;
-                        const bool tr = !lsc && W.p[3] != 0.0;
-                        TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, lsc ? 0.0 : W.p[0],
-                                                  lsc ? 1.0 : W.p[1], b->hist, b->wfun, lsc ? 0.0 : W.p[3],
-                                                  tr ? b->dip : nullptr, b->wfun_t, b->n, b->stream));
-                        if (lsc && W.p[5] > 0.0) {
-                            const double r = p0 / W.p[6];
-                            TRK_CUDA(launch_lsc_imp(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[9],
-                                                    W.p[5], std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->lsc,
-                                                    b->V, b->stream));
-                        } else if (lsc)
-                            TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
-                                                      (int)W.flags, b->wfun, b->lsc, b->V, b->stream));
-                        else
-                            TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, b->V, b->stream));
-                        b->launches += 2;
-                        if (tr) {
-                            TRK_CUDA(launch_wake_conv_t(b->dip, b->wfun_t, W.n, W.p[2] * qm_base, b->Vt, b->stream));
+                    p0 = advance_p0(L, e_start, e_first, p0);
+                    if (s < ng) {
+                        trk_status st = collective(e_first, slot, p0, b->V, b->Vt);
+                        if (st != TRK_OK) return st;
+                        if (e_second >= 0) {   // same particles, same l: the window of `slot` stands
+                            TRK_CUDA(launch_wake_reset(b->st, slot, b->hist,
+                                                       transverse(e_second) ? b->dip : nullptr,
+                                                       L->elems[e_second].n, false, b->stream));
                             ++b->launches;
+                            st = collective(e_second, slot, p0, b->V2, b->Vt2);
+                            if (st != TRK_OK) return st;
                         }
                     }
-                    prev_wake = e_end;
+                    prev = s < ng ? e_first : -1;
+                    prev2 = e_second;
                     prev_slot = slot;
-                    e_start = e_end + 1;
+                    e_start = (e_second >= 0 ? e_second : e_first) + 1;
                 }
                 b->p0c = p0;
             }
@@ -732,7 +769,7 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     if (b->n == 0) return TRK_OK;
     trk_status s = ensure_wake(b, nbins, false);
     if (s != TRK_OK) return s;
-    TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nullptr, nbins, b->stream));
+    TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nullptr, nbins, true, b->stream));
     TRK_CUDA(launch_wake_minmax(b->coords, b->pitch, b->lt, b->st, 0, b->n, b->stream));
     TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, 0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
                               nullptr, b->n, b->stream));
@@ -751,6 +788,7 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     a.n_turns = 1;
     a.turn_abs0 = (int32_t)b->turn;
     a.kick_wake = 0;
+    a.kick_wake2 = -1;
     a.kick_slot = 0;
     a.minmax_slot = -1;
     a.p0c = p0c_ev;

@@ -81,7 +81,8 @@ struct TrackArgs {
     int32_t turn_abs0;      // absolute turn number of the first turn
     int32_t local_turn0;    // row of the first turn in the partial-sum buffer
     int32_t kick_wake;      // element index of a wake to kick with first, or -1
-    int32_t kick_slot;      // its key slot
+    int32_t kick_wake2;     // a second collective element right after it (same window), or -1
+    int32_t kick_slot;      // their key slot
     int32_t minmax_slot;    // key slot to fill with l min/max at the end, or -1
     int32_t do_moments;     // per-turn moments at the end of each turn
     int32_t n_tiles;        // stride of the partial-sum rows
@@ -91,6 +92,9 @@ struct TrackArgs {
     const double *wake_V;   // voltages of the kicking wake
     const double *wake_Vx;  // its transverse voltages (x then y, 2 x nbins), or null
     int32_t wake_nbins;
+    int32_t wake_nbins2;    // the same of the second kick
+    const double *wake_V2;
+    const double *wake_Vx2;
     int32_t tile;           // particles per tile (block * per_thread)
     double *mom_out;        // finalised moments of this launch's first turn (batched path)
 };
@@ -122,8 +126,10 @@ cudaError_t launch_batch_chunk(const TrackArgs *args, const CompactArgs *cargs, 
 cudaError_t launch_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n, cudaStream_t s);
 // Transverse dipole sums are 64-bit fixed point, 2^-40 m per unit.
 constexpr double kDipoleScale = 1099511627776.0;   // 2^40 per metre
+// Zero the histogram (and the dipole sums if dip) and, with reset_keys, the l
+// window of key slot `slot`.
 cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins,
-                              cudaStream_t s);
+                              bool reset_keys, cudaStream_t s);
 cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
                                int slot, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot, int nbins,

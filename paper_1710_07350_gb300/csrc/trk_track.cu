@@ -491,6 +491,32 @@ __device__ __forceinline__ void store_particle(const TrackArgs &a, int64_t i, co
     a.coords[5 * a.pitch + i] = q.d[p];
 }
 
+// Kick of one collective element on the window of key slot a.kick_slot: the
+// transverse slope kicks first (V_x / P, V_y / P with P = p0 (1 + delta)), then
+// the energy kick delta += V(l) / p0.
+template <int P>
+__device__ __forceinline__ void wake_kick(const TrackArgs &a, Tile<P> &q, const bool (&alive)[P], double p0,
+                                          const double *V, const double *Vx, int nbins) {
+    const uint64_t kmin = a.st->lkey[2 * a.kick_slot], kmax = a.st->lkey[2 * a.kick_slot + 1];
+    const double lmin = dkey_inv(kmin), lmax = dkey_inv(kmax);
+    const double dl = (lmax - lmin) / nbins;
+    const bool flat = !(dl > 0.0);
+    const double idl = flat ? 0.0 : 1.0 / dl;
+    const double ip0 = 1.0 / p0;
+    if (Vx) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!alive[p]) continue;
+            const double iP = ip0 / (1.0 + q.d[p]);
+            q.xp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, Vx, nbins), iP, q.xp[p]);
+            q.yp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, Vx + nbins, nbins), iP, q.yp[p]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, V, nbins), ip0, q.d[p]);
+}
+
 // Check the aperture of every alive particle after element e; a particle that
 // is lost is written out at once (coordinates at the loss point and the loss
 // record) and its registers are zeroed so that it keeps taking the fast paths.
@@ -574,29 +600,15 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
     for (int t = 0; t < a.n_turns; ++t) {
         const int turn = a.turn_abs0 + t;
         if (a.kick_wake >= 0) {
-            // Kick of the wake element that precedes this segment.
-            const uint64_t kmin = a.st->lkey[2 * a.kick_slot], kmax = a.st->lkey[2 * a.kick_slot + 1];
-            const double lmin = dkey_inv(kmin), lmax = dkey_inv(kmax);
-            const double dl = (lmax - lmin) / a.wake_nbins;
-            const bool flat = !(dl > 0.0);
-            const double idl = flat ? 0.0 : 1.0 / dl;
-            const double ip0 = 1.0 / p0;
-            if (a.wake_Vx) {
-                // transverse kicks first: slopes change by V_x / P, V_y / P with P = p0 (1 + delta)
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (!alive[p]) continue;
-                    const double iP = ip0 / (1.0 + q.d[p]);
-                    q.xp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_Vx, a.wake_nbins), iP, q.xp[p]);
-                    q.yp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_Vx + a.wake_nbins, a.wake_nbins), iP,
-                                  q.yp[p]);
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-                if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, a.wake_V, a.wake_nbins), ip0, q.d[p]);
+            // Kicks of the collective element(s) that precede this segment, in
+            // lattice order, each followed by the aperture test.
+            wake_kick<P>(a, q, alive, p0, a.wake_V, a.wake_Vx, a.wake_nbins);
             dirty = true;
             apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here, canon);
+            if (a.kick_wake2 >= 0) {
+                wake_kick<P>(a, q, alive, p0, a.wake_V2, a.wake_Vx2, a.wake_nbins2);
+                apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake2, lost_here, canon);
+            }
         }
         int type_next = a.e0 < a.e1 ? __ldg(&elems[a.e0].type) : 0;
         for (int e = a.e0; e < a.e1; ++e) {

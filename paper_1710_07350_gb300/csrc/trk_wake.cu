@@ -23,17 +23,18 @@ constexpr int kSmemBins = 8192;      // sub-histograms in shared memory up to th
 constexpr int kSubHists = 2;         // per block (one per half of the warps)
 constexpr int kConvOut = 16;         // outputs per convolution block
 constexpr int kConvThreads = 256;
-constexpr int kLscThreads = 256;     // threads per CTA of the space-charge transform
+constexpr int kLscThreads = 512;     // threads per CTA of the space-charge transform
 constexpr int kLscClusterMinN = 1024; // transforms of at least this many points run on a cluster of 8 CTAs
 
 namespace cg = cooperative_groups;
 
-__global__ void k_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins) {
+__global__ void k_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins,
+                             int reset_keys) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) {
         hist[i] = 0u;
         if (dip) dip[i] = dip[nbins + i] = 0ull;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (reset_keys && blockIdx.x == 0 && threadIdx.x == 0) {
         st->lkey[2 * slot] = ~0ull;
         st->lkey[2 * slot + 1] = 0ull;
     }
@@ -278,29 +279,41 @@ constexpr double kClight = 299792458.0;
 // x (`nodes`, 2 kLscNodes doubles); for this entire integrand the rule's error
 // stays at double rounding for every x > 2 at that step (checked against an
 // independent K1 to x = 80).  Above x = 45, x K1(x) < 1e-18 and 1 - x K1 rounds to 1.
+// The quadrature's nodes are split over a group of lanes (lsc_bracket_group).
 constexpr int kLscNodes = 48;   // t up to 6: exp(-2 e_j) c_j < 1e-150 there
-__device__ double lsc_bracket(double x, const double *nodes) {
+constexpr int kLscLanes = 8;    // lanes that share one impedance value's quadrature
+
+// The series branch (x <= 2) of the bracket.
+__device__ double lsc_series(double x) {
+    const double q = 0.25 * x * x;
+    double t = 1.0, harm = 0.0, sum_t = 1.0, sum_ct = 1.0 - 2.0 * kEulerGamma;
+    for (int k = 1; k < 40; ++k) {
+        t *= q / ((double)k * (double)(k + 1));
+        harm += 1.0 / (double)k;
+        sum_t += t;
+        sum_ct += (2.0 * harm + 1.0 / (double)(k + 1) - 2.0 * kEulerGamma) * t;
+        if (t < 1e-18 * sum_t) break;
+    }
+    return q * sum_ct - x * log(0.5 * x) * (0.5 * x * sum_t);
+}
+
+// The bracket evaluated by a group of kLscLanes lanes (lane j of the group, lane
+// mask gm; every lane of the group calls it with the same x and gets the value):
+// lane 0 takes the series, or the lanes split the quadrature nodes and add their
+// partial sums with shuffles.
+__device__ double lsc_bracket_group(double x, const double *nodes, int j, unsigned gm) {
     if (!(x > 0.0)) return 0.0;
+    double acc;
     if (x <= 2.0) {
-        const double q = 0.25 * x * x;
-        double t = 1.0, harm = 0.0, sum_t = 1.0, sum_ct = 1.0 - 2.0 * kEulerGamma;
-        for (int k = 1; k < 40; ++k) {
-            t *= q / ((double)k * (double)(k + 1));
-            harm += 1.0 / (double)k;
-            sum_t += t;
-            sum_ct += (2.0 * harm + 1.0 / (double)(k + 1) - 2.0 * kEulerGamma) * t;
-            if (t < 1e-18 * sum_t) break;
-        }
-        return q * sum_ct - x * log(0.5 * x) * (0.5 * x * sum_t);
+        acc = j == 0 ? lsc_series(x) : 0.0;
+    } else {
+        if (x > 45.0) return 1.0;
+        acc = j == 0 ? 0.5 : 0.0;
+        for (int k = 1 + j; k < kLscNodes; k += kLscLanes) acc += exp(-x * nodes[2 * k]) * nodes[2 * k + 1];
     }
-    if (x > 45.0) return 1.0;
-    double acc = 0.5;
-    for (int j = 1; j < kLscNodes; ++j) {
-        const double f = exp(-x * nodes[2 * j]) * nodes[2 * j + 1];
-        acc += f;
-        if (f < 1e-18 * acc) break;
-    }
-    return 1.0 - x * exp(-x) * (0.125 * acc);
+#pragma unroll
+    for (int o = kLscLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gm, acc, o);
+    return x <= 2.0 ? acc : 1.0 - x * exp(-x) * (0.125 * acc);
 }
 
 // Cosine taper at f (fraction of Nyquist): 1 to f0, 0 from f1, f1 <= 0: none.
@@ -318,7 +331,8 @@ __device__ __forceinline__ double lsc_dl(const BunchState *st, int slot, int nbi
 }
 
 // Impedance and twiddle tables of one impedance space-charge pass, spread over the
-// whole GPU (the bracket is the costly part): Z_m = i zs[m] for m = 0 .. N/2
+// whole GPU, kLscLanes lanes per impedance value (the bracket's quadrature is the
+// costly part): Z_m = i zs[m] for m = 0 .. N/2
 // (zs[N - m] = -zs[m]; m = 0 and the Nyquist term carry no field),
 // zs[m] = Z0 / (pi kappa r_b^2) (1 - xi K1(xi)) taper(m / (N/2)), kappa = 2 pi m / (N dl),
 // xi = kappa r_b / gamma; tw[2j], tw[2j+1] = cos, sin of 2 pi j / N for j < N/2.
@@ -334,22 +348,25 @@ __global__ void k_lsc_tables(const BunchState *st, int slot, int nbins, int logn
         nodes[2 * j + 1] = cosh(0.125 * (double)j);
     }
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N + 1; i += gridDim.x * blockDim.x) {
-        if (i <= N / 2) {
-            double z = 0.0;
-            if (i != 0 && 2 * i != N) {
-                const double kap = 2.0 * kPi * (double)i / ((double)N * dl);
-                z = kZ0 / (kPi * kap * rb * rb) * lsc_bracket(kap * rb / gamma, nodes) *
-                    lsc_taper((double)i / (0.5 * (double)N), f0, f1);
-            }
-            zs[i] = z;
-        } else {
-            const int j = i - (N / 2 + 1);
-            double sn, cs;
-            sincospi(2.0 * (double)j / (double)N, &sn, &cs);
-            tw[2 * j] = cs;
-            tw[2 * j + 1] = sn;
+    // groups of kLscLanes consecutive lanes; the stride is a multiple of kLscLanes,
+    // so a group stays together through the loop
+    const int nz = N / 2 + 1;
+    const unsigned gm = 0xFFu << ((threadIdx.x & 31) & ~(kLscLanes - 1));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nz * kLscLanes; t += gridDim.x * blockDim.x) {
+        const int i = t / kLscLanes, j = t % kLscLanes;
+        if (i == 0 || 2 * i == N) {
+            if (j == 0) zs[i] = 0.0;
+            continue;
         }
+        const double kap = 2.0 * kPi * (double)i / ((double)N * dl);
+        const double B = lsc_bracket_group(kap * rb / gamma, nodes, j, gm);
+        if (j == 0) zs[i] = kZ0 / (kPi * kap * rb * rb) * B * lsc_taper((double)i / (0.5 * (double)N), f0, f1);
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N / 2; j += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)j / (double)N, &sn, &cs);
+        tw[2 * j] = cs;
+        tw[2 * j + 1] = sn;
     }
 }
 
@@ -495,8 +512,8 @@ int grid_for(int64_t n, int threads, int cap) {
 }  // namespace
 
 cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned long long *dip, int nbins,
-                              cudaStream_t s) {
-    k_wake_reset<<<grid_for(nbins, 256, 64), 256, 0, s>>>(st, slot, hist, dip, nbins);
+                              bool reset_keys, cudaStream_t s) {
+    k_wake_reset<<<grid_for(nbins, 256, 64), 256, 0, s>>>(st, slot, hist, dip, nbins, reset_keys ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -558,8 +575,8 @@ cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot,
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int tb = 64;
-    int grid = (N + 1 + tb - 1) / tb;
+    const int tb = 128;   // a multiple of kLscLanes
+    int grid = ((N / 2 + 1) * kLscLanes + tb - 1) / tb;
     if (grid > 152 * 4) grid = 152 * 4;
     k_lsc_tables<<<grid, tb, 0, s>>>(st, slot, nbins, logn, rb, gamma, f0, f1, zs, tw);
     cudaError_t e = cudaGetLastError();

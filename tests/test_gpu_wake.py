@@ -194,3 +194,27 @@ def test_wake_histogram_on_and_next_to_bin_edges():
     o, oh, oV = orc.wake(z, nb, syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
     assert np.array_equal(gh, oh)
     assert np.allclose(gV, oV, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("order", ["wake-lsc", "lsc-wake", "three", "at-ends"])
+def test_adjacent_collective_elements_against_oracle(order):
+    """Adjacent collective elements (the parts of an RFCW cavity) share one l
+    window on the GPU and kick together, in lattice order, in the next segment's
+    prologue; the oracle applies them one after the other.  Different bin
+    counts, a transverse wake, impedance and long-wavelength space charge, a run
+    of three (a pair and a single), and groups at both ends of the lattice."""
+    wk = {"type": "WAKE", "nbins": 512, "W0": syn.C3_W0, "sc": syn.C3_SC, "charge": syn.C3_CHARGE,
+          "W0T": syn.C3_W0T}
+    sc = {"type": "LSC", "nbins": 1024, "L": 2.0, "charge": syn.C3_CHARGE, "rb": 1e-3, "mc2": MC2_E,
+          "f0": 0.2, "f1": 0.6}
+    lw = {"type": "LSC", "nbins": 256, "L": 1.0, "K": 4.0e4, "charge": syn.C3_CHARGE, "passes": 2}
+    rf = {"type": "RFCA", "volt": syn.C3_VOLT, "phase_deg": syn.C3_PHASE, "freq_hz": syn.C3_FREQ}
+    dr = {"type": "EDRIFT", "L": 1.0}
+    els = {"wake-lsc": [rf, wk, sc, dr], "lsc-wake": [rf, sc, wk, dr], "three": [rf, wk, sc, lw, dr, rf],
+           "at-ends": [wk, sc, rf, dr, lw, wk]}[order]
+    lat = {"elements": els, "aperture": None, "p0c": 1.0e8}
+    z = offset_bunch(20_000, seed=21)
+    g = gpu_track(lat, z, 2)
+    o = orc.track(lat, z, 2)
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
