@@ -130,12 +130,12 @@ __device__ __noinline__ double drift_g_exact(double u) { return rsqrt(1.0 - u) -
 // series and exact branches, and then t = A B + h, l += A B.
 template <int P>
 __device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (&l)[P], const double (&qx)[P],
-                                        const double (&qy)[P], double h, double hh, double hq) {
+                                        const double (&qy)[P], double h, double hh, double hq, double z0) {
     double A[P], B[P];
     bool need = false;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double u = fma(qx[p], qx[p], qy[p] * qy[p]);
+        const double u = fma(qx[p], qx[p], fma(qy[p], qy[p], z0));
         A[p] = fma(hq, u, hh);
         B[p] = u;
         need |= !quad_ok(u);
@@ -163,7 +163,8 @@ __device__ __forceinline__ void v_drift(double (&x)[P], double (&y)[P], double (
 // sextupole qx -= hb (x^2 - y^2), qy += b x y with hb = K2 h/(2(1+delta)), b = 2 hb.
 template <int P, uint32_t FL>
 __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P], double (&qx)[P], double (&qy)[P],
-                                       const double (&a)[P], const double (&hb)[P], const double (&b)[P]) {
+                                       const double (&a)[P], const double (&hb)[P], const double (&b)[P],
+                                       double z0) {
     if (FL & 1u) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -175,9 +176,9 @@ __device__ __forceinline__ void v_kick(const double (&x)[P], const double (&y)[P
         // two products and three FMAs: w = x^2 - y^2 = fma(x, x, -y^2)
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const double w = fma(x[p], x[p], -(y[p] * y[p]));
+            const double w = fma(x[p], x[p], -fma(y[p], y[p], z0));
             qx[p] = fma(-hb[p], w, qx[p]);
-            qy[p] = fma(b[p] * y[p], x[p], qy[p]);
+            qy[p] = fma(fma(b[p], y[p], z0), x[p], qy[p]);
         }
     }
 }
@@ -251,34 +252,39 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
     const double d1 = __ldg(&E->p[0]), d2 = __ldg(&E->p[1]), dm = __ldg(&E->p[2]);
     const double d1h = __ldg(&E->p[7]), d1q = __ldg(&E->p[8]), d2h = __ldg(&E->p[9]), d2q = __ldg(&E->p[10]),
                  dmq = __ldg(&E->p[11]);
+    // z0 = +0 known only at run time: products (and doublings) are written
+    // fma(a, b, z0), which rounds as a * b (adding +0 to a rounded product is
+    // exact) but issues as an FMA, faster than a multiply or an add on this GPU's
+    // FP64 pipe
+    const double z0 = d1 * 0.0;
     double a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
     if (FL & 1u) {
         const double A1 = __ldg(&E->p[3]), A0 = __ldg(&E->p[4]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            a1[p] = A1 * iP[p];
-            a0[p] = A0 * iP[p];
+            a1[p] = fma(A1, iP[p], z0);
+            a0[p] = fma(A0, iP[p], z0);
         }
     }
     if (FL & 2u) {
         const double H1 = __ldg(&E->p[5]), H0 = __ldg(&E->p[6]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            hb1[p] = H1 * iP[p];
-            hb0[p] = H0 * iP[p];
-            b1[p] = hb1[p] + hb1[p];
-            b0[p] = hb0[p] + hb0[p];
+            hb1[p] = fma(H1, iP[p], z0);
+            hb0[p] = fma(H0, iP[p], z0);
+            b1[p] = fma(2.0, hb1[p], z0);
+            b0[p] = fma(2.0, hb0[p], z0);
         }
     }
-    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1, d1h, d1q);
+    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d1, d1h, d1q, z0);
     for (int s = 0; s < n; ++s) {
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0, b0);
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q);
-        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1, z0);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q, z0);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a0, hb0, b0, z0);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, d2, d2h, d2q, z0);
+        v_kick<P, FL>(q.x, q.y, q.xp, q.yp, a1, hb1, b1, z0);
         const bool mid = s + 1 < n;   // merged drift dm = 2 d1, so dm / 2 = d1
-        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, mid ? dm : d1, mid ? d1 : d1h, mid ? dmq : d1q);
+        v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, mid ? dm : d1, mid ? d1 : d1h, mid ? dmq : d1q, z0);
     }
 }
 
@@ -625,7 +631,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                 // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
                 // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
                 if (canon)
-                    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]), __ldg(&E->p[1]), __ldg(&E->p[2]));
+                    v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]), __ldg(&E->p[1]), __ldg(&E->p[2]),
+                               __ldg(&E->p[0]) * 0.0);
                 else
                     v_edrift<P>(q, __ldg(&E->p[0]));
                 break;
