@@ -84,23 +84,24 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                 const int rr = r < 6 ? r : 0;
                 const int kb = rb[rr], len = r < 6 ? rb[rr + 1] - rb[rr] : 0;
                 double acc = (r < 6 && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
+                const double z0 = __ldg(&E->p[0]) * 0.0;   // as the tracking kernel's map
                 for (int k = 0; k < len; ++k) {
                     const double2 tv = __ldg(t + kb + k);
                     const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
                     const int deg = code & 3, j = (code >> 2) & 7, jk = (code >> 5) & 7, jl = (code >> 8) & 7;
                     double m = 1.0;
                     if (deg >= 1) m = sel6(q, j);
-                    if (deg >= 2) m *= sel6(q, jk);
-                    if (deg >= 3) m *= sel6(q, jl);
+                    if (deg >= 2) m = fma(m, sel6(q, jk), z0);
+                    if (deg >= 3) m = fma(m, sel6(q, jl), z0);
                     acc = fma(tv.x, m, acc);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
             } else if (type == TRK_THINSEXT) {
                 const double k2 = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
-                const double x = q[0], y = q[2];
-                q[1] = fma(-hk, (x - y) * (x + y), q[1]);
-                q[3] = fma(k2, x * y, q[3]);
+                const double x = q[0], y = q[2], z0 = k2 * 0.0;   // as the tracking kernel
+                q[1] = fma(-hk, fma(x, x, -fma(y, y, z0)), q[1]);
+                q[3] = fma(k2, fma(x, y, z0), q[3]);
             } else if (type == TRK_EDRIFT) {
                 const double Ld = __ldg(&E->p[0]);
                 const double xp = q[1], yp = q[3];

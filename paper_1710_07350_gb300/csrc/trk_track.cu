@@ -51,6 +51,9 @@ __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E,
     const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
     const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
     const double2 *t = reinterpret_cast<const double2 *>(terms + __ldg(&E->term0));
+    // +0 known only at run time (a map's p[] is zero): monomial products are
+    // fma(m, x_j, z0), rounded as m * x_j but issued at the DFMA rate
+    const double z0 = __ldg(&E->p[0]) * 0.0;
     double acc[6][P];
     int len[6], n = 0;
 #pragma unroll
@@ -71,8 +74,8 @@ __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E,
             for (int p = 0; p < P; ++p) {
                 double m = 1.0;
                 if (deg >= 1) m = tget(q, p, j);
-                if (deg >= 2) m *= tget(q, p, jk);
-                if (deg >= 3) m *= tget(q, p, jl);
+                if (deg >= 2) m = fma(m, tget(q, p, jk), z0);
+                if (deg >= 3) m = fma(m, tget(q, p, jl), z0);
                 acc[r][p] = fma(tv.x, m, acc[r][p]);
             }
         }
@@ -94,12 +97,13 @@ __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E,
 // sqrt(1+v) - 1 = v/2 - v^2/8 + v^3/16 - 5 v^4/128 to FP64 rounding.
 template <int P>
 __device__ __forceinline__ void v_edrift(Tile<P> &q, double L) {
+    const double z0 = L * 0.0;   // run-time +0: products issued as FMAs (as in v_map)
     double g[P];
     bool need = false;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double v = fma(q.xp[p], q.xp[p], q.yp[p] * q.yp[p]);
-        g[p] = v * fma(v, fma(v, fma(v, -0.0390625, 0.0625), -0.125), 0.5);
+        const double v = fma(q.xp[p], q.xp[p], fma(q.yp[p], q.yp[p], z0));
+        g[p] = fma(v, fma(v, fma(v, fma(v, -0.0390625, 0.0625), -0.125), 0.5), z0);
         need |= !series_ok(v);
         q.x[p] = fma(L, q.xp[p], q.x[p]);
         q.y[p] = fma(L, q.yp[p], q.y[p]);
@@ -309,14 +313,16 @@ __device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &
     }
 }
 
+// Thin sextupole (Table 1 THINSEXT): x' -= (K2L/2)(x^2 - y^2), y' += K2L x y.
 template <int P>
 __device__ __forceinline__ void v_thin_sext(Tile<P> &q, const DevElem *__restrict__ E) {
     const double k = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
+    const double z0 = k * 0.0;   // run-time +0: products issued as FMAs (as in v_map)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double t = (q.x[p] - q.y[p]) * (q.x[p] + q.y[p]);
+        const double t = fma(q.x[p], q.x[p], -fma(q.y[p], q.y[p], z0));
         q.xp[p] = fma(-hk, t, q.xp[p]);
-        q.yp[p] = fma(k, q.x[p] * q.y[p], q.yp[p]);
+        q.yp[p] = fma(k, fma(q.x[p], q.y[p], z0), q.yp[p]);
     }
 }
 
