@@ -179,6 +179,67 @@ def cpu_baseline():
             "single_thread_value": rate1}
 
 
+def _threads_map(fn, parts):
+    if len(parts) == 1:
+        return [fn(parts[0])]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(len(parts)) as ex:
+        return list(ex.map(fn, parts))
+
+
+def da_cpu_baseline():
+    """The oracle's dynamic-aperture scan rate on all host cores: one variant's
+    512^2 grid sampled every 4th cell in x and y (128^2 cells, 1/16 of a scan),
+    1000 turns, split over the cores; scans/s = 1 / (16 x wall time)."""
+    import synthetic as syn
+    from oracle import oracle as orc
+    cores = host_cores()
+    n = syn.DA_N
+    lat = syn.lattice_c5(0)
+    sub = syn.da_particles(n=n).reshape(n, n, 6)[::4, ::4].reshape(-1, 6)
+    parts = np.array_split(sub, cores)
+    t0 = time.perf_counter()
+    _threads_map(lambda zz: orc.track(lat, zz, 1000, moments=False), parts)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / (16.0 * dt), "unit": "DA scans/s", "cores": cores, "kind": "oracle",
+            "sample": "variant 0, every 4th cell of the 512^2 grid in x and y (16384 cells = 1/16 of a scan), "
+                      "1000 turns, %d threads, %.1f s wall, scaled by 16" % (cores, dt)}
+
+
+def c3_cpu_baseline(lat):
+    """The oracle on the linac: 2e6 particles through 5 of the 200 periods on one
+    thread (the wakes need the whole bunch, so the oracle is not split)."""
+    import synthetic as syn
+    from oracle import oracle as orc
+    per = len(lat["elements"]) // syn.C3_PERIODS
+    sample = {**lat, "elements": lat["elements"][:5 * per]}
+    n = 2_000_000
+    z = syn.bunch("c3", n=n)
+    t0 = time.perf_counter()
+    orc.track(sample, z, 1, moments=False)
+    dt = time.perf_counter() - t0
+    return {"value": n * len(sample["elements"]) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "2e6 particles through the first 5 of the 200 periods (%d elements), one thread, %.1f s"
+                      % (len(sample["elements"]), dt)}
+
+
+def c4_cpu_baseline():
+    """The oracle on the batched-variant ring: the first `cores` variants, 1000
+    particles of each through 300 turns, one variant per host thread."""
+    import synthetic as syn
+    from oracle import oracle as orc
+    cores = host_cores()
+    vs = syn.c4_variants()[:cores]
+    jobs = [(syn.lattice_c4(v), syn.c4_bunch(k, v[2])[:1000]) for k, v in enumerate(vs)]
+    t0 = time.perf_counter()
+    _threads_map(lambda j: orc.track(j[0], j[1], 300, moments=False), jobs)
+    dt = time.perf_counter() - t0
+    passes = sum(j[1].shape[0] * len(j[0]["elements"]) * 300 for j in jobs)
+    return {"value": passes / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d variants x 1000 particles x 300 turns, one variant per thread, %.1f s wall; passes "
+                      "counted as if all survive" % (len(jobs), dt)}
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
@@ -333,6 +394,8 @@ def run_ours(args):
     probe = trk.trk_probe_fp64()            # measured FP64 rates, after the timed region
     measured_peak = 2.0 * probe[0] / 1e12
     da = None if args.no_da else run_da(args.da_variants, trk, syn, torch)
+    if da is not None and not args.no_cpu_baseline:
+        da["cpu_baseline"] = da_cpu_baseline()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -514,7 +577,8 @@ def run_c3(args):
                       "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
                       "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
                       "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, "launches": times[0][1]["launches"],
-                      "steps": args.steps, "warmup": args.warmup}))
+                      "steps": args.steps, "warmup": args.warmup,
+                      "cpu_baseline": None if args.no_cpu_baseline else c3_cpu_baseline(lat)}))
     return 0
 
 
@@ -603,7 +667,8 @@ def run_c4(args):
     print(json.dumps({"workload": "c4: 256 variants of the FODO ring + thin sextupoles, %d particles, 1000 turns" % n_tot,
                       "metric": UNIT, "batched_value": passes / res["batched"], "plain_value": passes / res["plain"],
                       "batched_s": res["batched"], "plain_s": res["plain"], "speedup": res["plain"] / res["batched"],
-                      "autotuned_schedule": tuned, "alive_end": alive, "note": "passes counted as if all survive"}))
+                      "autotuned_schedule": tuned, "alive_end": alive, "note": "passes counted as if all survive",
+                      "cpu_baseline": None if args.no_cpu_baseline else c4_cpu_baseline()}))
     return 0
 
 
