@@ -45,8 +45,10 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
                                               float *__restrict__ Cf, int ldc, __nv_bfloat16 *__restrict__ Cb,
                                               const float *__restrict__ bias, const float *__restrict__ aux,
                                               int k_split, size_t c_split) {
-    __shared__ __align__(16) __nv_bfloat16 sA[BM * SK];
-    __shared__ __align__(16) __nv_bfloat16 sB[BN * SK];
+    // two shared-memory stages: the next tile's global loads are in flight in
+    // registers while the current tile's MMAs run, then land in the other stage
+    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * SK];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][BN * SK];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
@@ -61,52 +63,80 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
 
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // A tile BM x BK and B tile (stored n-major, sB[n][k]) BN x BK: 256
-        // 16-byte vectors each, two per thread.
+    // A tile BM x BK and B tile (stored n-major, sB[n][k]) BN x BK: 256 16-byte
+    // vectors each, two per thread.
+    uint4 ra[2], rb[2];
+    const auto load = [&](int k0) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int e = tid + q * 128;
             if (!A_T) {
                 const int m = e >> 2, k = (e & 3) * 8;
-                *reinterpret_cast<uint4 *>(&sA[m * SK + k]) =
-                    *reinterpret_cast<const uint4 *>(&A[(size_t)(m0 + m) * lda + (k0 + k)]);
+                ra[q] = *reinterpret_cast<const uint4 *>(&A[(size_t)(m0 + m) * lda + (k0 + k)]);
             } else {
                 const int k = e >> 3, m = (e & 7) * 8;
-                const uint4 v = *reinterpret_cast<const uint4 *>(&A[(size_t)(k0 + k) * lda + (m0 + m)]);
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) sA[(m + i) * SK + k] = h[i];
+                ra[q] = *reinterpret_cast<const uint4 *>(&A[(size_t)(k0 + k) * lda + (m0 + m)]);
             }
             if (B_NK) {
                 const int n = e >> 2, k = (e & 3) * 8;
-                *reinterpret_cast<uint4 *>(&sB[n * SK + k]) =
-                    *reinterpret_cast<const uint4 *>(&B[(size_t)(n0 + n) * ldb + (k0 + k)]);
+                rb[q] = *reinterpret_cast<const uint4 *>(&B[(size_t)(n0 + n) * ldb + (k0 + k)]);
             } else {
                 const int k = e >> 3, n = (e & 7) * 8;
-                const uint4 v = *reinterpret_cast<const uint4 *>(&B[(size_t)(k0 + k) * ldb + (n0 + n)]);
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) sB[(n + i) * SK + k] = h[i];
+                rb[q] = *reinterpret_cast<const uint4 *>(&B[(size_t)(k0 + k) * ldb + (n0 + n)]);
             }
         }
-        __syncthreads();
+    };
+    const auto store = [&](int st) {
+        __nv_bfloat16 *a = sA[st], *b = sB[st];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * 128;
+            if (!A_T) {
+                const int m = e >> 2, k = (e & 3) * 8;
+                *reinterpret_cast<uint4 *>(&a[m * SK + k]) = ra[q];
+            } else {
+                const int k = e >> 3, m = (e & 7) * 8;
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&ra[q]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[(m + i) * SK + k] = h[i];
+            }
+            if (B_NK) {
+                const int n = e >> 2, k = (e & 3) * 8;
+                *reinterpret_cast<uint4 *>(&b[n * SK + k]) = rb[q];
+            } else {
+                const int k = e >> 3, n = (e & 7) * 8;
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&rb[q]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) b[(n + i) * SK + k] = h[i];
+            }
+        }
+    };
+    int st = 0;
+    if (kbeg < kend) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        const bool more = k0 + BK < kend;
+        if (more) load(k0 + BK);
+        const __nv_bfloat16 *a = sA[st], *b = sB[st];
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t af[2][4], bf[4][2];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int r = wm + i * 16 + g, c = kk + tg * 2;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&sA[r * SK + c]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&sA[(r + 8) * SK + c]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&sA[r * SK + c + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&sA[(r + 8) * SK + c + 8]);
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&a[r * SK + c]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&a[(r + 8) * SK + c]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&a[r * SK + c + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&a[(r + 8) * SK + c + 8]);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int n = wn + j * 8 + g, c = kk + tg * 2;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&sB[n * SK + c]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&sB[n * SK + c + 8]);
+                bf[j][0] = *reinterpret_cast<const uint32_t *>(&b[n * SK + c]);
+                bf[j][1] = *reinterpret_cast<const uint32_t *>(&b[n * SK + c + 8]);
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -119,7 +149,10 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
                         : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]),
                           "r"(bf[j][1]));
         }
+        // the other stage was last read before the previous barrier
+        if (more) store(st ^ 1);
         __syncthreads();
+        st ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
