@@ -227,10 +227,15 @@ __global__ void k_head_back(const float *__restrict__ logit, const float *__rest
 }
 
 // out[n] = sum_m A[m][n] (* w[m] if w): column sums over N = 256 columns in a
-// fixed order (kColSlices row slices, then the slices), FP32.
+// fixed order, FP32, in one launch: each of kColSlices blocks writes the partial
+// sums of its row slice; the last block to finish (a ticket counter, reset for
+// the next call) adds the partials in slice order, so the result does not
+// depend on which block came last.
 constexpr int kColSlices = 64;
-__global__ void k_colsum_part(const float *__restrict__ A, const __nv_bfloat16 *__restrict__ Ab,
-                              const float *__restrict__ w, int64_t M, float *__restrict__ part) {
+__global__ void k_colsum(const float *__restrict__ A, const __nv_bfloat16 *__restrict__ Ab,
+                         const float *__restrict__ w, int64_t M, float *part, unsigned *ticket,
+                         float *__restrict__ out) {
+    __shared__ bool last;
     const int n = threadIdx.x;  // blockDim.x == kW
     const int64_t per = (M + kColSlices - 1) / kColSlices;
     const int64_t m0 = blockIdx.x * per, m1 = m0 + per < M ? m0 + per : M;
@@ -240,16 +245,23 @@ __global__ void k_colsum_part(const float *__restrict__ A, const __nv_bfloat16 *
         s += w ? a * w[m] : a;
     }
     part[blockIdx.x * kW + n] = s;
-}
-__global__ void k_colsum_final(const float *__restrict__ part, float *__restrict__ out) {
-    const int n = threadIdx.x;
-    float s = 0.0f;
-    for (int j = 0; j < kColSlices; ++j) s += part[j * kW + n];
-    out[n] = s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    float t = 0.0f;
+    for (int j = 0; j < kColSlices; ++j) t += __ldcg(part + j * kW + n);
+    out[n] = t;
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
-__global__ void k_sum(const float *__restrict__ a, int64_t n, float scale, float *__restrict__ out) {
+// out[b] = scale[b] * sum_i a_b[i] for the two arrays b = blockIdx.x (one block each).
+__global__ void k_sum2(const float *__restrict__ a0, const float *__restrict__ a1, int64_t n, float scale0,
+                       float scale1, float *__restrict__ out0, float *__restrict__ out1) {
     __shared__ float sh[256];
+    const float *a = blockIdx.x ? a1 : a0;
     float s = 0.0f;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
     sh[threadIdx.x] = s;
@@ -258,7 +270,7 @@ __global__ void k_sum(const float *__restrict__ a, int64_t n, float scale, float
         if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+    if (threadIdx.x == 0) *(blockIdx.x ? out1 : out0) = sh[0] * (blockIdx.x ? scale1 : scale0);
 }
 
 // out[i] = sum over slices s = 0, 1, ... of part[s * n + i], in slice order.
@@ -327,7 +339,7 @@ struct trk_mlp {
     float *dz = nullptr;                                           // FP32 dz of the current layer
     __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
     float *logit = nullptr, *dl = nullptr, *loss_terms = nullptr, *loss = nullptr;
-    float *part = nullptr;                                         // column-sum partials
+    float *part = nullptr;                                         // column-sum partials, then the ticket
     float *splitk = nullptr;                                       // split-K partials of dW [kSplits][256][256]
     uint16_t *wt = nullptr;                                        // BF16 weights of layers 0..3, tcgen05 tiled layout
     size_t wt_off[kHidden] = {};
@@ -338,6 +350,9 @@ struct trk_mlp {
 };
 
 static trk_status mlp_fail(trk_status s, const std::string &m) { return set_error(s, m); }
+
+// The column sums' ticket counter, kept after the partials (zero between calls).
+static unsigned *col_ticket(trk_mlp *N) { return reinterpret_cast<unsigned *>(N->part + kColSlices * kW); }
 
 static void mlp_free_acts(trk_mlp *N) {
     for (auto &h : N->H) {
@@ -413,7 +428,8 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
     if (e == cudaSuccess) e = cudaMalloc(&N->g, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->pb, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&N->loss, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&N->part, kColSlices * kW * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->part, (kColSlices * kW + 4) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(N->part + kColSlices * kW, 0, 4 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->splitk, (size_t)kSplits * kW * kW * sizeof(float));
     {
         size_t o = 0;
@@ -544,10 +560,9 @@ static cudaError_t mlp_grad_rows(trk_mlp *N, const float *X, const float *y, int
     // head backward: dlogit, dz4 (rows beyond M are zero)
     k_head_back<<<grid_for(m_pad * kW), 256, 0, s>>>(N->logit, y, M, m_pad, N->pb + N->w_off[4], N->Z[kHidden - 1],
                                                     N->dl, N->dz, N->dzb, N->loss_terms);
-    k_colsum_part<<<kColSlices, kW, 0, s>>>(nullptr, N->H[kHidden], N->dl, M, N->part);
-    k_colsum_final<<<1, kW, 0, s>>>(N->part, N->g + N->w_off[4]);
-    k_sum<<<1, 256, 0, s>>>(N->dl, M, 1.0f, N->g + N->b_off[4]);
-    k_sum<<<1, 256, 0, s>>>(N->loss_terms, M, 1.0f / (float)M, N->loss);
+    k_colsum<<<kColSlices, kW, 0, s>>>(nullptr, N->H[kHidden], N->dl, M, N->part, col_ticket(N),
+                                       N->g + N->w_off[4]);
+    k_sum2<<<2, 256, 0, s>>>(N->dl, N->loss_terms, M, 1.0f, 1.0f / (float)M, N->g + N->b_off[4], N->loss);
     // dW reduces over the rows: split them into at most kSplits slices of
     // k_split rows, one block column each, then sum the partials in slice order.
     int splits = (int)(m_pad / 256) < kSplits ? (int)(m_pad / 256) : kSplits;
@@ -563,8 +578,7 @@ static cudaError_t mlp_grad_rows(trk_mlp *N, const float *X, const float *y, int
         k_reduce_splits<<<grid_for((int64_t)kW * K), 256, 0, s>>>(N->splitk, splits, (int64_t)kW * K,
                                                                   N->g + N->w_off[l]);
         // db_l = sum_m dz (FP32)
-        k_colsum_part<<<kColSlices, kW, 0, s>>>(N->dz, nullptr, nullptr, M, N->part);
-        k_colsum_final<<<1, kW, 0, s>>>(N->part, N->g + N->b_off[l]);
+        k_colsum<<<kColSlices, kW, 0, s>>>(N->dz, nullptr, nullptr, M, N->part, col_ticket(N), N->g + N->b_off[l]);
         if (l > 0) {
             // dz_{l-1} = (dzb W_l) * gelu'(z_{l-1}), W_l [256 x 256] as B[k = out][n = in]
             k_gemm<false, false, EPI_DGELU><<<dim3(kW / BN, (unsigned)(m_pad / BM)), 128, 0, s>>>(
