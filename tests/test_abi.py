@@ -90,6 +90,66 @@ def test_invalid_descriptors_rejected_without_gpu():
     assert lib.trk_track(None, None, 1) == 1
 
 
+def test_space_charge_and_bend_descriptors_rejected_without_gpu():
+    """The impedance space charge and the sector bend validate on the host."""
+    lib = trk.lib()
+    h = ctypes.c_void_p()
+    o = trk.trk_lattice_opts()
+    o.p0c_ev = 1e9
+    d = (trk.trk_element_desc * 1)()
+    d[0].type = trk.TYPES["LSC"]
+    d[0].length, d[0].charge, d[0].lsc_rb, d[0].lsc_mc2 = 1.0, 1e-9, 1e-3, 0.511e6
+    for nbins in (1000, 8192):                       # a power of two up to 4096
+        d[0].nbins = nbins
+        assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+        assert b"impedance" in lib.trk_last_error()
+    d[0].nbins = 256
+    for field, value in (("lsc_mc2", 0.0), ("lsc_rb", -1e-3), ("lsc_rb", float("nan")), ("lsc_f1", 1.5)):
+        old = getattr(d[0], field)
+        setattr(d[0], field, value)
+        assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+        setattr(d[0], field, old)
+    d[0].lsc_f0, d[0].lsc_f1 = 0.6, 0.5                # f0 < f1 when filtering
+    assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    d = (trk.trk_element_desc * 1)()
+    d[0].type = trk.TYPES["SBEND"]
+    for length, angle in ((1.0, 3.2), (0.0, 0.1), (-1.0, 0.1), (1.0, float("nan"))):
+        d[0].length, d[0].angle = length, angle
+        assert lib.trk_create_lattice(d, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+        assert b"sector bend" in lib.trk_last_error()
+
+
+def test_collective_and_bend_flop_accounting():
+    from paper_1710_07350_gb300 import flops
+    assert flops.element_flops({"type": "LSC", "nbins": 64}) == 0
+    assert flops.element_flops({"type": "SBEND", "L": 1.0, "angle": 0.1}) == 64
+    assert flops.element_flops({"type": "SBEND", "L": 1.0, "angle": 0.0}) == 12
+    # two complex transforms of N = 8192 points (5 N log2 N each) and N impedance values
+    assert flops.lsc_imp_flops(4096) == 2 * 5 * 8192 * 13 + 8192 * (flops.LSC_BRACKET_FLOPS + 6)
+
+
+def test_reference_arm_prints_one_line_on_the_host(tmp_path):
+    """`bench.py --impl reference` times the oracle on the host cores and prints
+    the contract's line without touching a GPU."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root,
+                         env={**os.environ, "CUDA_VISIBLE_DEVICES": ""})
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config",
+              "cpu_baseline", "e2e", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
 def test_step_work_accounting():
     """Passes and flops of a step from loss records (used by the bench)."""
     import numpy as np
