@@ -218,3 +218,24 @@ def test_adjacent_collective_elements_against_oracle(order):
     o = orc.track(lat, z, 2)
     err = compare_tracking(g, o, TOL_PASS)
     compare_moments(g["moments"], o["moments"], coord_err=err)
+
+
+def test_space_charge_and_wake_with_losses_and_bends():
+    """A sector-bend ring with a wake + impedance space-charge group and an
+    aperture that removes part of a wide bunch: the collective elements see only
+    the particles still alive, on both sides."""
+    ring = syn.lattice_bend_ring(cells=2, aperture=("rect", 2.0e-3, 1.5e-3))
+    wk = {"type": "WAKE", "nbins": 512, "W0": syn.C3_W0, "sc": syn.C3_SC, "charge": syn.C3_CHARGE}
+    sc = {"type": "LSC", "nbins": 512, "L": 2.0, "charge": syn.C3_CHARGE, "rb": 1e-3, "mc2": MC2_E,
+          "f0": 0.25, "f1": 0.5}
+    els = ring["elements"]
+    lat = {**ring, "elements": els[:4] + [wk, sc] + els[4:]}
+    z = syn.bend_ring_bunch(20_000, seed=31)
+    z[:, 0] *= 1.5
+    z[:, 2] *= 1.5
+    z[:, 4] = np.random.Generator(np.random.Philox(key=32)).normal(0.0, 1e-4, z.shape[0])
+    g = gpu_track(lat, z, 3)
+    o = orc.track(lat, z, 3)
+    assert 0.05 < 1.0 - o["n_alive"] / z.shape[0] < 0.6
+    err = compare_tracking(g, o, TOL_PASS * 10)
+    compare_moments(g["moments"], o["moments"], coord_err=err)
