@@ -157,7 +157,19 @@ class Lattice:
 
 
 def trk_create_lattice(lattice, moments=True):
-    """lattice: {"elements": [...], "aperture": (kind, a, b) | None, "p0c": eV}."""
+    """lattice: {"elements": [...], "aperture": (kind, a, b) | None, "p0c": eV}.
+
+    Element dicts by "type" (units as in include/trk.h):
+      MAP      {"map": {"order", "C", "R", "T", "U"}}
+      EDRIFT   {"L"}
+      KQUAD / KSEXT {"L", "K1", "K2", "n_kicks"}
+      THINSEXT {"K2L"}
+      RFCA     {"volt", "phase_deg", "freq_hz"}
+      WAKE     {"nbins", "W0", "sc", "charge", "W0T" (transverse, optional)}
+      LSC      {"nbins", "L", "charge"} and either {"K", "passes"} (long-wavelength
+               limit) or {"rb", "mc2", "f0", "f1"} (round-beam impedance)
+      SBEND    {"L", "angle"}
+    """
     els = lattice["elements"]
     descs = (trk_element_desc * max(len(els), 1))()
     keep = []
