@@ -152,12 +152,31 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     }
 }
 
+// Sum over the block of every thread's kConvOut partial sums: the partials go to
+// shared memory, then 16 lanes per output add 16 of them each and fold the 16
+// results with four shuffles (20 adds per thread instead of five shuffle steps
+// for each of the kConvOut sums).  Returns output t >> 4's sum in lanes with
+// (t & 15) == 0.
+static_assert(kConvThreads == 256 && kConvOut == 16, "reduction layout");
+__device__ __forceinline__ double conv_block_sum(const double (&acc)[kConvOut], double *red) {
+#pragma unroll
+    for (int i = 0; i < kConvOut; ++i) red[i * kConvThreads + threadIdx.x] = acc[i];
+    __syncthreads();
+    const int o = threadIdx.x >> 4, p = threadIdx.x & 15;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kConvThreads / 16; ++q) s += red[o * kConvThreads + p + 16 * q];
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
 // V_k = -q_m sum_{j <= k} h_j W((k - j) dl); a block owns kConvOut outputs and
 // its threads split the source bins.
 __global__ void __launch_bounds__(kConvThreads) k_wake_conv(const uint32_t *__restrict__ hist,
                                                              const double *__restrict__ wfun, int nbins, double qm,
                                                              double *__restrict__ V) {
-    __shared__ double sh[(kConvThreads / 32) * kConvOut];
+    __shared__ double red[kConvThreads * kConvOut];
     const int k0 = blockIdx.x * kConvOut;
     const int kend = min(k0 + kConvOut, nbins);
     double acc[kConvOut];
@@ -173,20 +192,9 @@ __global__ void __launch_bounds__(kConvThreads) k_wake_conv(const uint32_t *__re
             if (k >= j && k < kend) acc[i] = fma(h, __ldg(wfun + (k - j)), acc[i]);
         }
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < kConvOut; ++i) {
-        double s = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[w * kConvOut + i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < kConvOut && k0 + threadIdx.x < kend) {
-        double s = 0.0;
-        for (int j = 0; j < kConvThreads / 32; ++j) s += sh[j * kConvOut + threadIdx.x];
-        V[k0 + threadIdx.x] = -qm * s;
-    }
+    const double s = conv_block_sum(acc, red);
+    const int o = threadIdx.x >> 4;
+    if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[k0 + o] = -qm * s;
 }
 
 // V_c[k] = q_m sum_{j <= k} D_c[j] W_T((k - j) dl), D in fixed point; blocks of
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wake_conv(const uint32_t *__re
 __global__ void __launch_bounds__(kConvThreads) k_wake_conv_t(const unsigned long long *__restrict__ dip,
                                                                const double *__restrict__ wfun_t, int nbins,
                                                                double qm, double *__restrict__ V) {
-    __shared__ double sh[(kConvThreads / 32) * kConvOut];
+    __shared__ double red[kConvThreads * kConvOut];
     const unsigned long long *D = dip + (size_t)blockIdx.y * nbins;
     const int k0 = blockIdx.x * kConvOut;
     const int kend = min(k0 + kConvOut, nbins);
@@ -211,20 +219,9 @@ __global__ void __launch_bounds__(kConvThreads) k_wake_conv_t(const unsigned lon
             if (k >= j && k < kend) acc[i] = fma(d, __ldg(wfun_t + (k - j)), acc[i]);
         }
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < kConvOut; ++i) {
-        double s = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[w * kConvOut + i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < kConvOut && k0 + threadIdx.x < kend) {
-        double s = 0.0;
-        for (int j = 0; j < kConvThreads / 32; ++j) s += sh[j * kConvOut + threadIdx.x];
-        V[(size_t)blockIdx.y * nbins + k0 + threadIdx.x] = qm * s;
-    }
+    const double s = conv_block_sum(acc, red);
+    const int o = threadIdx.x >> 4;
+    if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[(size_t)blockIdx.y * nbins + k0 + o] = qm * s;
 }
 
 // One block: line density, `passes` 1-2-1 smoothing passes, central
