@@ -399,18 +399,30 @@ trk_status trk_bunch_stats(trk_bunch *b, trk_stats *out, int32_t reset);
  * allocated.  The working arrays live in one file-scope device array of fixed
  * size (nbins <= 16384, 320.25 KiB) that every GPU loading the library holds
  * until the process exits.
- *   d_coords   [6 * pitch] FP64 SoA coordinates; all n particles count as alive;
+ * Unlike trk_wake, which works on a bunch's alive particles, this call has no
+ * id or alive array: EVERY one of the n particles counts as alive (in the l
+ * window, the histogram and the kick), so a caller with lost particles passes
+ * only the alive ones (compacted to the front).
+ *   d_coords   [6 * pitch] FP64 SoA coordinates (caller-owned, device);
  *              delta (coordinate 5) receives the kick in place
- *   q_m        charge / n
+ *   pitch, n   row pitch and particle count (0 <= n <= pitch)
+ *   nbins      histogram bins over [min l, max l], 1..16384
+ *   w0, sc     wake amplitude [V m^(1/2) / C] and cutoff distance [m]:
+ *              W(s) = w0 / sqrt(max(s, sc)), as for trk_wake
+ *   charge     total bunch charge [C]; divided by n inside as the charge per
+ *              macro-particle q_m
+ *   p0c_ev     reference momentum [eV] for the kick delta += V(l) / p0c
  *   d_hist     [nbins] uint32 counts, d_volt [nbins] FP64 voltages: optional
  *              caller device outputs (NULL to skip)
  *   stream     cudaStream_t (NULL = legacy default stream)
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the array and leaves its contents to
- * the next; each call clears what must start at zero, and calls whose work
- * overlaps on the GPU race on it.  Returns TRK_EINVAL for nbins outside
- * 1..16384, n < 0, pitch < n or p0c_ev <= 0. */
+ * (cudaGetSymbolAddress) with that device current and caches it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * use the library across a cudaDeviceReset (the cached address would then
+ * point at memory that no longer exists).  Every call shares the array and
+ * leaves its contents to the next; each call clears what must start at zero,
+ * and calls whose work overlaps on the GPU race on it.  Returns TRK_EINVAL
+ * for nbins outside 1..16384, n < 0, pitch < n or p0c_ev <= 0. */
 trk_status trk_wake_static(double *d_coords, int64_t pitch, int64_t n, int32_t nbins, double w0, double sc,
                            double charge, double p0c_ev, uint32_t *d_hist, double *d_volt, void *stream);
 

@@ -12,7 +12,9 @@
 //
 // The device address of that array is obtained once per device, with the
 // device current, by cudaGetSymbolAddress on the first call made on that
-// device; make that first call before any stream capture.  All calls share the
+// device, and cached for the life of the process; make that first call before
+// any stream capture, and do not use the library across a cudaDeviceReset (the
+// cached address would then point at freed memory).  All calls share the
 // array and it keeps the last call's contents, so each call clears what must
 // start at zero; calls whose work overlaps on the GPU (different streams, or
 // different host threads on one stream without ordering) race on it.

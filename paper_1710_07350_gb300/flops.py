@@ -1,27 +1,39 @@
 """Algorithmic work of the tracking path, for the roofline.
 
-Convention: one flop per +, -, *, /, sqrt or cos of the element model as the
-paper and the oracle state it (an FMA is two flops); per-element constants
-(K1 h, 0.5 K2 h, ...) are not counted.  This is the work the method needs,
-whatever instructions the kernel spends on it.
+Convention: one flop per +, -, *, /, sqrt, rsqrt or cos of the element model
+(an FMA is two flops); per-element constants (K1 h, K2 h / 2, ...) are not
+counted.  The model is counted in the form the method evaluates it: inside a
+run of consecutive kick-drift elements and exact drifts the momenta are the
+scaled canonical momenta q = p / (1 + delta) (Sec. 3 "canonical kick"; the
+exit conversion of one element and the entry conversion of the next are
+inverse maps, so a run converts once at each end), and the drifts of the
+Yoshida scheme are the exact-Hamiltonian drift in those variables.  Every
+operation counted is one the element model needs; no count exceeds the
+instructions the fused kernel issues for it.
 
 Per particle and pass (alive particle entering the element):
-  EDRIFT        x += L x', y += L y' (4); l += L (sqrt(1 + x'^2 + y'^2) - 1) (8)  -> 12
-  kick-drift    entry P = 1 + delta, r = sqrt(1 + x'^2 + y'^2), px, py          -> 10
-                per merged drift (n_steps * 3 + 1 of them): pz = sqrt(P^2 - px^2 - py^2) (6),
-                x += h px/pz (3), y (3), l += h (P/pz - 1) (4)                     -> 16
-                per quad kick (3 per step): px -= a x, py += a y                   -> 4
-                per sextupole kick (3 per step): (x^2 - y^2) (3), *c, -= (2); x y * c += (3) -> 8
-                exit: pz (6), x' = px/pz, y' = py/pz (2)                           -> 8
-  THINSEXT      x' -= (K2L/2)(x^2 - y^2) (5), y' += K2L x y (3)                      -> 8
-  SBEND         slopes -> px, py, pz (9), p_h (4), S (6), beta: atan2, asin, divide,
-                add (4), alpha (1), sin and cos of alpha and beta (4), exit point
-                (14), px_f (3), 1/pz_f (6), x_f (5), slopes, y, l (9)               -> 64
-  RFCA          P (2), phi + k l (2), cos (1), V * (1), + (1), P/P' (1), 2 *, delta (2) -> 12
-  MAP           per nonzero term of degree d (the R_rr = 1 diagonal is free): d * (products) + 1 add
-                i.e. deg 0: 1, deg 1: 2, deg 2: 3, deg 3: 4
-  aperture      RECT |x| <= a, |y| <= b: 4;  ELLIPSE (x/a)^2 + (y/b)^2 <= 1: 6
-  moments       per alive particle and turn: 6 means + 21 centred products: 54
+  EDRIFT, slopes     x += L x', y += L y' (4); v = x'^2 + y'^2 (3);
+                     l += L (sqrt(1 + v) - 1) (5)                                 -> 12
+  drift on q         u = qx^2 + qy^2 (3); g = (1 - u)^(-1/2) - 1 (3);
+                     t = h (1 + g) (2); x += t qx, y += t qy (4); l += h g (2)    -> 14
+                     (an EDRIFT inside a run, and every merged Yoshida drift)
+  kick-drift body    strengths / (1 + delta): 2 (quad) or 4 (sextupole);
+                     (3 n + 1) merged drifts (14 each); 3 n kicks:
+                     quad qx -= a x, qy += a y (4);
+                     sextupole w = x^2 - y^2 (3), qx -= hb w (2), qy += (b y) x (3) (8)
+  run entry          1/(1 + delta) (2); v (3), (1 + v)^(-1/2) (2), q = c x' (2)     -> 9
+  run exit           u (3), g (3), x' = q (1 + g) (4)                                 -> 10
+                     charged to the element after the run (or the run's last
+                     element at the end of the turn, where the moments need slopes)
+  THINSEXT           x' -= (K2L/2)(x^2 - y^2) (5), y' += K2L x y (3)                  -> 8
+  SBEND              slopes -> px, py, pz (9), p_h (4), S (6), beta: atan2, asin, divide,
+                     add (4), alpha (1), sin and cos of alpha and beta (4), exit point
+                     (14), px_f (3), 1/pz_f (6), x_f (5), slopes, y, l (9)               -> 64
+  RFCA               P (2), phi + k l (2), cos (1), V * (1), + (1), P/P' (1), 2 *, delta (2) -> 12
+  MAP                per nonzero term of degree d (the R_rr = 1 diagonal is free): d * (products) + 1 add
+                     i.e. deg 0: 1, deg 1: 2, deg 2: 3, deg 3: 4
+  aperture           RECT |x| <= a, |y| <= b: 4;  ELLIPSE (x/a)^2 + (y/b)^2 <= 1: 6
+  moments            per alive particle and turn: 6 means + 21 centred products: 54
 """
 import numpy as np
 
@@ -79,14 +91,31 @@ def map_flops(m):
     return f
 
 
-def element_flops(el):
+DRIFT_Q_FLOPS = 14          # exact-Hamiltonian drift on the scaled canonical momenta
+EDRIFT_SLOPE_FLOPS = 12
+RUN_ENTRY_FLOPS = 9
+RUN_EXIT_FLOPS = 10
+_RUN_TYPES = ("KQUAD", "KSEXT", "EDRIFT")
+
+
+def kick_drift_body_flops(el):
+    """One kick-drift element inside a run (no conversions)."""
+    n = el["n_kicks"]
+    quad = el.get("K1", 0.0) != 0.0
+    sext = el["type"] == "KSEXT" and el.get("K2", 0.0) != 0.0
+    setup = (2 if quad else 0) + (4 if sext else 0)
+    kick = (4 if quad else 0) + (8 if sext else 0)
+    return setup + (3 * n + 1) * DRIFT_Q_FLOPS + 3 * n * kick
+
+
+def element_flops(el, canonical=False):
+    """Flops of one pass through `el`; `canonical`: the particle arrives with
+    scaled canonical momenta (inside a run of kick-drift elements)."""
     t = el["type"]
     if t == "EDRIFT":
-        return 12
+        return DRIFT_Q_FLOPS if canonical else EDRIFT_SLOPE_FLOPS
     if t in ("KQUAD", "KSEXT"):
-        n = el["n_kicks"]
-        kick = (4 if el.get("K1", 0.0) != 0.0 else 0) + (8 if el.get("K2", 0.0) != 0.0 and t == "KSEXT" else 0)
-        return 10 + (3 * n + 1) * 16 + 3 * n * kick + 8
+        return kick_drift_body_flops(el) + (0 if canonical else RUN_ENTRY_FLOPS)
     if t == "THINSEXT":
         return 8
     if t == "SBEND":
@@ -101,10 +130,29 @@ def element_flops(el):
 
 
 def lattice_pass_flops(lat):
-    """Per element: flops of one particle pass including the aperture test."""
+    """Per element: flops of one particle pass including the aperture test and
+    the representation changes at the ends of kick-drift runs (a run starts at a
+    kick-drift element; an exact drift before any kick-drift element of the
+    turn works on slopes; slopes are restored before any other element and at
+    the end of the turn)."""
     ap = lat.get("aperture")
     fa = APERTURE_FLOPS[ap[0] if ap else None]
-    return np.array([element_flops(el) + fa for el in lat["elements"]], dtype=np.float64)
+    els = lat["elements"]
+    out = np.zeros(len(els), dtype=np.float64)
+    canon = False
+    for i, el in enumerate(els):
+        t = el["type"]
+        f = 0
+        if canon and t not in _RUN_TYPES:
+            f += RUN_EXIT_FLOPS
+            canon = False
+        f += element_flops(el, canonical=canon)
+        if t in ("KQUAD", "KSEXT"):
+            canon = True
+        out[i] = f + fa
+    if canon and len(els):
+        out[-1] += RUN_EXIT_FLOPS
+    return out
 
 
 def step_work(lat, n_start, n_turns, lost_turn_local=(), lost_elem=(), moments=True):

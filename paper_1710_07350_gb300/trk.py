@@ -519,12 +519,33 @@ def trk_bunch_stats(b, reset=False):
 
 
 def trk_wake_static(coords, n, nbins, w0, sc, charge, p0c, hist=None, volt=None, stream=None):
-    """Allocation-free standalone wake on a (6, pitch) float64 CUDA tensor."""
+    """Allocation-free standalone wake on the first n columns of a contiguous
+    (6, pitch) float64 CUDA tensor (every one of the n particles counts as
+    alive).  hist (int32) and volt (float64), if given, are CUDA tensors of at
+    least nbins elements on the same device; the library itself checks nbins
+    against its fixed maximum.  The shapes, types and devices are checked here
+    because the C call receives bare device pointers and cannot."""
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream(coords.device)
-    _check(lib().trk_wake_static(_dptr(coords), coords.shape[1], n, nbins, w0, sc, charge, p0c,
-                                 _dptr(hist), _dptr(volt), c_void_p(stream.cuda_stream)))
+    if not (isinstance(coords, torch.Tensor) and coords.is_cuda and coords.dtype == torch.float64
+            and coords.dim() == 2 and coords.shape[0] == 6 and coords.is_contiguous()):
+        raise ValueError("trk_wake_static: coords must be a contiguous (6, pitch) float64 CUDA tensor")
+    n = int(n)
+    if n < 0 or n > coords.shape[1]:
+        raise ValueError("trk_wake_static: n must be in 0..pitch")
+    for name, t, dt in (("hist", hist, torch.int32), ("volt", volt, torch.float64)):
+        if t is None:
+            continue
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError("trk_wake_static: %s must be a contiguous %s CUDA tensor" % (name, dt))
+        if t.device != coords.device:
+            raise ValueError("trk_wake_static: %s is on %s, coords on %s" % (name, t.device, coords.device))
+        if t.numel() < int(nbins):
+            raise ValueError("trk_wake_static: %s holds %d elements, nbins is %d" % (name, t.numel(), nbins))
+    with torch.cuda.device(coords.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(coords.device)
+        _check(lib().trk_wake_static(_dptr(coords), coords.shape[1], n, nbins, w0, sc, charge, p0c,
+                                     _dptr(hist), _dptr(volt), c_void_p(stream.cuda_stream)))
 
 
 def trk_probe_fp64(stream=None):

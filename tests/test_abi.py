@@ -164,9 +164,27 @@ def test_step_work_accounting():
     p2, f2 = flops.step_work(lat, 10, 3, [1], [2])
     assert p2 == 9 * 3 * ne + (1 * ne + 3)
     assert f2 == 9 * 3 * (per.sum() + 54) + (per.sum() + 54) + per[:3].sum()
-    # kick-drift quad with 4 steps: entry 10 + 13 drifts x 16 + 12 kicks x 4 + exit 8
-    assert flops.element_flops({"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}) == 274
-    assert flops.element_flops({"type": "KSEXT", "L": 0.1, "K2": 20.0, "n_kicks": 4}) == 322
+    # kick-drift quad with 4 steps: strengths 2 + 13 drifts x 14 + 12 kicks x 4 (+ run entry 9)
+    assert flops.element_flops({"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}, canonical=True) == 232
+    assert flops.element_flops({"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 4}) == 241
+    assert flops.element_flops({"type": "KSEXT", "L": 0.1, "K2": 20.0, "n_kicks": 4}, canonical=True) == 282
+    # one c2 cell: the run [QF, SF, D, QD, SF, D] converts at entry (QF) and before the RF cavity
+    ell = flops.APERTURE_FLOPS["ellipse"]
+    assert list(per) == [241 + ell, 282 + ell, 14 + ell, 232 + ell, 282 + ell, 14 + ell, 12 + 10 + ell]
+
+
+def test_flop_runs_at_the_turn_end():
+    """A run that reaches the end of the turn converts back there; an exact
+    drift before the first kick-drift element works on slopes."""
+    from paper_1710_07350_gb300 import flops
+    q = {"type": "KQUAD", "L": 0.2, "K1": 1.2, "n_kicks": 1}
+    d = {"type": "EDRIFT", "L": 1.0}
+    lat = {"elements": [d, q, d], "aperture": None}
+    body = 2 + 4 * 14 + 3 * 4
+    assert list(flops.lattice_pass_flops(lat)) == [12, body + 9, 14 + 10]
+    sb = {"type": "SBEND", "L": 1.0, "angle": 0.1}
+    lat = {"elements": [q, sb, q], "aperture": ("rect", 0.02, 0.02)}
+    assert list(flops.lattice_pass_flops(lat)) == [body + 9 + 4, 10 + 64 + 4, body + 9 + 10 + 4]
 
 
 def test_da_boundary_metric():

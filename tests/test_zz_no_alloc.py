@@ -4,13 +4,17 @@ It exists for callers that may not allocate device memory when they need a wake
 step (a fixed memory pool that must not grow, a host application that forbids
 cudaMalloc after start-up, a device already full).  Its result must equal that
 of trk_wake on the same particles, also on the second of two calls in a row,
-where the shared fixed-size working array still holds the first call's data.
+where the shared fixed-size working array still holds the first call's data,
+and it must match the CPU oracle's wake (histogram bit for bit, voltages to
+1e-13 relative) at bin counts that take the shared-memory histogram (up to
+8192 bins), the global-atomic one (8193 to 16384) and the 16384-bin maximum.
 This file is collected last so that a stopping run has run every other test.
 """
 import numpy as np
 import pytest
 
 import synthetic as syn
+from oracle import oracle as orc
 from paper_1710_07350_gb300 import trk
 
 pytestmark = pytest.mark.gpu
@@ -40,9 +44,10 @@ def _with_static(z, nbins, p0c):
 
 def test_wake_static_equals_trk_wake_on_two_calls():
     p0c = 2.0e9
-    # the second call uses more bins than the first, so stale histogram entries
-    # left by the first call would show up if they were not cleared
-    for n, nbins, seed in ((20_000, 1000, 31), (7_777, 4096, 32)):
+    # each call uses more bins than the one before, so stale histogram entries
+    # left by an earlier call would show up if they were not cleared; 12000 and
+    # 16384 bins take the global-atomic histogram, 16384 is the maximum
+    for n, nbins, seed in ((20_000, 1000, 31), (7_777, 4096, 32), (15_000, 12_000, 33), (9_000, 16_384, 34)):
         z = syn.bunch("c3", n=n, seed=seed)
         ref_c, ref_h, ref_v = _with_trk_wake(z, nbins, p0c)
         got_c, got_h, got_v = _with_static(z, nbins, p0c)
@@ -51,6 +56,26 @@ def test_wake_static_equals_trk_wake_on_two_calls():
         assert np.allclose(got_v, ref_v, rtol=1e-13, atol=0)
         assert np.array_equal(got_c[:5], ref_c[:5])
         assert np.max(np.abs(got_c[5] - ref_c[5])) <= 1e-15
+        # and against the CPU oracle on the same particles
+        o, oh, oV = orc.wake(z, nbins, syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, p0c)
+        assert np.array_equal(got_h.astype(np.int64), oh), "histogram must be bit-exact on identical l"
+        assert np.allclose(got_v, oV, rtol=1e-13, atol=0)
+        assert np.array_equal(got_c[:5], o[:, :5].T)
+        assert np.max(np.abs(got_c[5] - o[:, 5])) <= 1e-15
+
+
+def test_wake_static_rejects_bad_tensors():
+    """The binding checks what the C call cannot see behind bare pointers."""
+    coords, _ = trk.upload(syn.bunch("c3", n=100))
+    args = (syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 1e9)
+    with pytest.raises(ValueError):
+        trk.trk_wake_static(coords.float(), 100, 64, *args)
+    with pytest.raises(ValueError):
+        trk.trk_wake_static(coords, coords.shape[1] + 1, 64, *args)
+    with pytest.raises(ValueError):
+        trk.trk_wake_static(coords, 100, 64, *args, hist=torch.zeros(63, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        trk.trk_wake_static(coords, 100, 64, *args, volt=torch.zeros(64, dtype=torch.float32, device="cuda"))
 
 
 def test_wake_static_rejects_oversize():
