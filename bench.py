@@ -62,8 +62,11 @@ def parse():
     p.add_argument("--turns-per-step", type=int, default=TURNS_PER_STEP)
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-da", action="store_true", help="skip the dynamic-aperture scan measurements")
+    p.add_argument("--no-c3", action="store_true", help="skip the wake-linac record of the default line")
+    p.add_argument("--no-c4", action="store_true", help="skip the batched-variant record of the default line")
+    p.add_argument("--no-sweep", action="store_true", help="skip the particle-count sweeps of the default line")
     p.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi samples (default: temp dir)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train", "sweep", "bend"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "mlp", "mlp-train", "sweep", "c3sweep", "bend"],
                    help="c2 (default, the headline line); c3 wake linac, c4 batched variants, the "
                         "surrogate's inference (mlp) and training (mlp-train), the particle-count "
                         "sweep of the map ring (sweep) and the sector-bend ring (bend) print their own "
@@ -396,6 +399,9 @@ def run_ours(args):
     da = None if args.no_da else run_da(args.da_variants, trk, syn, torch)
     if da is not None and not args.no_cpu_baseline:
         da["cpu_baseline"] = da_cpu_baseline()
+    c3 = None if args.no_c3 else c3_record(args, 2, 1, not args.no_cpu_baseline, clocks_index=local)
+    c4 = None if args.no_c4 else c4_record(args, 0, not args.no_cpu_baseline, clocks_index=local, plain_stride=8)
+    sweep = None if args.no_sweep else {"c3_parts": c3_sweep_record(args), "c1_maps": map_sweep_points()}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -422,6 +428,9 @@ def run_ours(args):
         "passes": passes_all,
         "alive_end": n_alive,
         "da": da,
+        "c3": c3,
+        "c4": c4,
+        "sweep": sweep,
     }
     print(json.dumps(out))
     if dist is not None:
@@ -461,13 +470,13 @@ def run_da(n_var, trk, syn, torch):
     ncoarse = n_var * ((n - stride // 2 + stride - 1) // stride) ** 2
     perm = torch.from_numpy(np.stack([g.permutation(ncoarse) for _ in range(epochs)]).astype(np.int32)).cuda()
     out = {"variants": n_var, "grid": [n, n], "turns": turns, "coarse_stride": stride, "band_radius": 2,
-           "audit_fraction": 0.005, "sentinel_stride": 5, "expand_radius": 4}
+           "audit_fraction": 0.005, "sentinel_stride": 5, "expand_radius": 0}
     res = {}
     for name, use in (("surrogate", 1), ("nonlearned", 0)):
         net = trk.trk_mlp_create(syn.mlp_init(7)) if use else None
         opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
                 "band_radius": 2, "use_mlp": use, "epochs": epochs, "batch": batch, "lr": 2e-3,
-                "sentinel_stride": 5, "expand_radius": 4}
+                "sentinel_stride": 5, "expand_radius": 0}
         torch.cuda.synchronize()
         t = time.perf_counter()
         mask, _, st = trk.trk_da_triage(L, params, opts, net=net, audit=audit, perm=perm if use else None)
@@ -531,6 +540,11 @@ def profiled_traffic_per_launch(npart, tps):
 
 
 def run_c3(args):
+    print(json.dumps(c3_record(args, args.steps, args.warmup, not args.no_cpu_baseline)))
+    return 0
+
+
+def c3_record(args, steps, warmup, with_cpu, clocks_index=None):
     """Wake linac: 10M particles through 200 x [RF, WAKE(4096), drift, quad];
     one step = one pass of the whole linac from the initial bunch."""
     import torch
@@ -546,7 +560,10 @@ def run_c3(args):
     coords0, ids0 = trk.upload(z0)
     n = z0.shape[0]
     times = []
-    for k in range(args.warmup + args.steps):
+    clocks = Clocks(clocks_index, args.clocks_dir) if clocks_index is not None else None
+    for k in range(warmup + steps):
+        if clocks is not None and k == warmup:
+            clocks.start()
         coords, ids = coords0.clone(), ids0.clone()
         b = trk.trk_bunch_wrap(coords, ids)
         trk.trk_bunch_set_schedule(b, block=args.block, per_thread=args.per_thread)
@@ -558,9 +575,10 @@ def run_c3(args):
         e1.record()
         e1.synchronize()
         st = trk.trk_bunch_stats(b)
-        if k >= args.warmup:
+        if k >= warmup:
             times.append((e0.elapsed_time(e1), st))
         del b
+    clk = clocks.stop() if clocks is not None else None
     ms = sum(t for t, _ in times) / len(times)
     kms = sum(st["track_kernel_ms"] for _, st in times) / len(times)
     passes = n * len(lat["elements"])
@@ -572,14 +590,66 @@ def run_c3(args):
         f += n * 200 * flops.LSC_FLOPS_PER_PARTICLE + 200 * flops.lsc_imp_flops(syn.C3_NBINS)
     extra = (" + transverse dipole wake, offset bunch" if args.transverse else "") + \
             (" + impedance space charge (4096 bins, r_b 1 mm, L 3 m)" if args.lsc else "")
-    print(json.dumps({"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins%s, drift, quad], 1e7 particles"
-                                  % extra,
-                      "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
-                      "tracking_kernel_share": kms / ms, "achieved_tflops": f / (ms / 1e3) / 1e12,
-                      "frac_of_fp64_peak": f / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, "launches": times[0][1]["launches"],
-                      "steps": args.steps, "warmup": args.warmup,
-                      "cpu_baseline": None if args.no_cpu_baseline else c3_cpu_baseline(lat)}))
-    return 0
+    ach = f / (ms / 1e3) / 1e12
+    return {"workload": "c3 wake linac: 200 x [RFCA -10 deg, WAKE 4096 bins%s, drift, quad], 1e7 particles" % extra,
+            "metric": UNIT, "value": passes / (ms / 1e3), "ms_per_pass_of_linac": ms,
+            "tracking_kernel_share": kms / ms,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / PEAK_FP64_TFLOPS, "flops_per_pass_of_linac": f,
+                         "count": "element model (cos, division = 1 flop) + histogram window/bin/kick 14 per "
+                                  "particle per wake + nbins (nbins + 1) per convolution"},
+            "launches": times[0][1]["launches"], "steps": steps, "warmup": warmup, "clocks": clk,
+            "cpu_baseline": c3_cpu_baseline(lat) if with_cpu else None}
+
+
+def c3_sweep_record(args):
+    """Particle-count sweep of the wake linac (20 of its periods: RF cavity,
+    4096-bin wake, drift, quadrupole): one pass for 1e6, 1e7 and 1e8 particles
+    as one resident bunch, and for 1e8 particles held in 4 parts whose wakes
+    are reduced across the parts (trk_track_parts).  Bunches are drawn on the
+    device; passes/s counts every particle through every element."""
+    import torch
+
+    import synthetic as syn
+    from paper_1710_07350_gb300 import trk
+    periods = 20
+    lat = syn.lattice_c3(periods=periods)
+    L = trk.trk_create_lattice(lat)
+    ne = len(lat["elements"])
+    out = []
+    for n, parts in ((1_000_000, 1), (10_000_000, 1), (100_000_000, 1), (100_000_000, 4)):
+        z = syn.c3_bunch_device(n)
+        sizes = [n // parts] * parts
+        sizes[-1] += n - sum(sizes)
+        bunches, keep, start = [], [], 0
+        for m in sizes:
+            coords = z[:, start:start + m].contiguous() if parts > 1 else z
+            ids = torch.arange(start, start + m, dtype=torch.int32, device="cuda")
+            b = trk.trk_bunch_wrap(coords, ids, n=m)
+            trk.trk_bunch_set_schedule(b, block=args.block, per_thread=args.per_thread)
+            bunches.append(b)
+            keep.append((coords, ids))
+            start += m
+        if parts > 1:
+            del z
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if parts > 1:
+            trk.trk_track_parts(bunches, L, 1)
+        else:
+            trk.trk_track(bunches[0], L, 1)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"particles": n, "parts": parts, "ms": ms, "passes_per_s": n * ne / (ms / 1e3)})
+        del bunches, keep
+        if parts == 1:
+            del z
+        torch.cuda.empty_cache()
+    return {"workload": "c3 wake linac, %d periods (%d elements, 4096-bin wakes), one pass" % (periods, ne),
+            "metric": UNIT, "points": out,
+            "note": "the first point includes the first launches' set-up; bunches drawn on the device"}
 
 
 def run_bend(args):
@@ -624,6 +694,11 @@ def run_bend(args):
 
 
 def run_c4(args):
+    print(json.dumps(c4_record(args, args.warmup, not args.no_cpu_baseline)))
+    return 0
+
+
+def c4_record(args, warmup, with_cpu, clocks_index=None, plain_stride=1):
     """256 lattice variants (log-uniform 1000..65536 particles), 1000 turns:
     batched (autotuned schedule, one CUDA graph per call) against one
     lattice at a time."""
@@ -641,10 +716,18 @@ def run_c4(args):
         return [trk.trk_bunch_wrap(c.clone(), i.clone()) for c, i in inputs]
 
     tuned, probe_ms = trk.trk_autotune(fresh(), Ls, 20)
+    n_tot = sum(v[2] for v in vs)
+    # the plain arm (one lattice per call) on every 8th variant: its rate is
+    # per pass, and the whole set would take ~45 s
+    plain_idx = list(range(0, len(vs), plain_stride))
+    n_plain = sum(vs[k][2] for k in plain_idx)
     res = {}
+    clocks = Clocks(clocks_index, args.clocks_dir) if clocks_index is not None else None
+    if clocks is not None:
+        clocks.start()
     for mode in ("batched", "plain"):
         best = None
-        for k in range(args.warmup + 1):
+        for k in range(warmup + 1):
             bs = fresh()
             torch.cuda.synchronize()
             t = time.perf_counter()
@@ -653,23 +736,28 @@ def run_c4(args):
                 trk.trk_batch_set_schedule(B, **tuned)
                 trk.trk_batch_track(B, turns)
             else:
-                for b, L in zip(bs, Ls):
-                    trk.trk_bunch_set_schedule(b, block=128, per_thread=2, chunk_turns=100)
-                    trk.trk_track(b, L, turns)
+                for j in plain_idx:
+                    trk.trk_bunch_set_schedule(bs[j], block=128, per_thread=2, chunk_turns=100)
+                    trk.trk_track(bs[j], Ls[j], turns)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t
-            if k >= args.warmup:
+            if k >= warmup:
                 best = dt
-            alive = sum(trk.trk_n_alive(b) for b in bs)
+            if mode == "batched":
+                alive = sum(trk.trk_n_alive(b) for b in bs)
         res[mode] = best
-    n_tot = sum(v[2] for v in vs)
+    clk = clocks.stop() if clocks is not None else None
     passes = n_tot * 60 * turns
-    print(json.dumps({"workload": "c4: 256 variants of the FODO ring + thin sextupoles, %d particles, 1000 turns" % n_tot,
-                      "metric": UNIT, "batched_value": passes / res["batched"], "plain_value": passes / res["plain"],
-                      "batched_s": res["batched"], "plain_s": res["plain"], "speedup": res["plain"] / res["batched"],
-                      "autotuned_schedule": tuned, "alive_end": alive, "note": "passes counted as if all survive",
-                      "cpu_baseline": None if args.no_cpu_baseline else c4_cpu_baseline()}))
-    return 0
+    passes_plain = n_plain * 60 * turns
+    return {"workload": "c4: 256 variants of the FODO ring + thin sextupoles, %d particles, 1000 turns" % n_tot,
+            "metric": UNIT, "value": passes / res["batched"], "batched_value": passes / res["batched"],
+            "plain_value": passes_plain / res["plain"], "batched_s": res["batched"], "plain_s": res["plain"],
+            "plain_sample": "every %dth variant (%d variants, %d particles), one call each" % (plain_stride, len(plain_idx),
+                                                                                             n_plain),
+            "speedup": (passes / res["batched"]) / (passes_plain / res["plain"]), "autotuned_schedule": tuned,
+            "alive_end": alive,
+            "note": "passes counted as if all survive; wall time of the calls, host launch included", "clocks": clk,
+            "cpu_baseline": c4_cpu_baseline() if with_cpu else None}
 
 
 def run_mlp(args):
@@ -730,6 +818,12 @@ def run_mlp_train(args):
 
 
 def run_sweep(args):
+    print(json.dumps({"workload": "c1 map ring particle-count sweep (order 2 and 3 maps)", "metric": UNIT,
+                      "points": map_sweep_points()}))
+    return 0
+
+
+def map_sweep_points():
     """Particle-count sweep of the c1 map ring (10 FODO cells, 40 order-2 or
     order-3 maps, rectangle 20 mm): passes/s for N = 1e4 .. 1e8 particles, each
     point about 1e8 particle-turns (turns = 1e8 / N, 1 to 1000) in one launch
@@ -768,9 +862,7 @@ def run_sweep(args):
                         "tflops": passes * f_pass / (ms / 1e3) / 1e12, "alive_end": alive})
             del b, coords, ids
             torch.cuda.empty_cache()
-    print(json.dumps({"workload": "c1 map ring particle-count sweep (order 2 and 3 maps)", "metric": UNIT,
-                      "points": out}))
-    return 0
+    return out
 
 
 def main():
@@ -787,6 +879,9 @@ def main():
         return run_mlp_train(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "c3sweep":
+        print(json.dumps(c3_sweep_record(args)))
+        return 0
     if args.workload == "bend":
         return run_bend(args)
     return run_ours(args)

@@ -213,6 +213,23 @@ trk_status trk_bunch_set_schedule(trk_bunch *b, const trk_schedule *s);
  * (counted over all trk_track calls of this bunch) and the element index. */
 trk_status trk_track(trk_bunch *b, const trk_lattice *lat, int32_t n_turns);
 
+/* Track one physical bunch held in n_parts parts (Sec. 4: the particle count
+ * grows beyond one kernel's working set, 8M particles per GPU and 1e9 in all;
+ * Sec. 2.2-2.3: a wake's histogram is taken over the whole bunch).  Each part
+ * is a trk_bunch over its own caller arrays (ids distinct across parts if the
+ * caller wants to tell particles apart); the parts are tracked, compacted and
+ * get per-turn moments each on their own (moments of part k are those of its
+ * alive particles), but every collective element (TRK_WAKE, TRK_LSC) acts on
+ * the union of the parts' alive particles: one l window over all parts, one
+ * histogram, the field computed once with q_m = charge / (sum of the parts' n),
+ * and the kick applied to every part.  The coordinates equal, bit for bit,
+ * those of trk_track on one bunch holding all the particles: the window is an
+ * exact min/max and the histogram and dipole sums are integer sums, whatever
+ * the split.  All parts must use the same stream and share the
+ * reference momentum and the turn counter (TRK_EINVAL otherwise); the first
+ * part holds the collective scratch.  n_parts = 1 is trk_track. */
+trk_status trk_track_parts(trk_bunch *const *parts, int32_t n_parts, const trk_lattice *lat, int32_t n_turns);
+
 /* Per-turn moments of the last trk_track call, host_out[t*28 + q]:
  *   q = 0      number of alive particles after turn t
  *   q = 1..6   means of the 6 coordinates
@@ -273,8 +290,11 @@ trk_status trk_track_batch(trk_bunch *const *bunches, const trk_lattice *const *
  * was lost, or n_turns + 1 if it survived.  offsets is a HOST array of n_var+1
  * entries starting at 0.  sched = NULL uses block 128, 2 particles per thread,
  * chunks of 1, 2, 4, ... 128 turns, or, for at most 16384 points on lattices of
- * MAP, EDRIFT and THINSEXT elements, trk_da_survival_lanes.  Allocates its
- * particle arrays and synchronises the stream before returning. */
+ * MAP, EDRIFT and THINSEXT elements, trk_da_survival_lanes.  Only loss turns
+ * leave the call, so map rows on which no aperture test depends (directly or
+ * through other rows; for a ring of maps and thin sextupoles, the path-length
+ * row) are not evaluated: every loss decision is the one full tracking takes.
+ * Allocates its particle arrays and synchronises the stream before returning. */
 trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const int64_t *offsets,
                            const double *d_x0, const double *d_y0, int32_t n_turns, const trk_schedule *sched,
                            int32_t *d_survival, void *stream);
@@ -317,6 +337,13 @@ typedef struct trk_mlp trk_mlp;
 trk_status trk_mlp_create(const float *const *W, const float *const *b, trk_mlp **out);
 trk_status trk_mlp_destroy(trk_mlp *net);
 trk_status trk_mlp_forward(trk_mlp *net, const float *d_X, int64_t M, float *d_logits, void *stream);
+/* trk_mlp_forward that also copies each hidden layer's BF16 output (the
+ * activations the next product reads) to d_hidden, device uint16 [4][M][256]
+ * row-major (layer l, row m at (l * M + m) * 256); d_hidden NULL is plain
+ * trk_mlp_forward.  For inspecting the network and for checking its rounding
+ * layer by layer. */
+trk_status trk_mlp_forward_hidden(trk_mlp *net, const float *d_X, int64_t M, float *d_logits, uint16_t *d_hidden,
+                                  void *stream);
 trk_status trk_mlp_grad(trk_mlp *net, const float *d_X, const float *d_y, int32_t M, float *d_loss, void *stream);
 trk_status trk_mlp_adam(trk_mlp *net, float lr, float beta1, float beta2, float eps, void *stream);
 trk_status trk_mlp_train(trk_mlp *net, const float *d_X, const float *d_y, int64_t n, int32_t batch,

@@ -70,6 +70,50 @@ def forward(params, X, rounding=True):
     return logit, cache
 
 
+# Error model of a float32 evaluation of one hidden layer (the GPU's): the K
+# products of BF16 values are exact in float32, and the float32 sum of them,
+# in whatever order the tensor core takes, is taken to lie within ACC_ULPS
+# units of float32 rounding of sum |h W| (2^-24 sum |h W| each) of the exact
+# sum; adding the bias rounds once more (2^-24 |z|).  GELU in float32 (z * c,
+# erf to 2 ulp, 1 + erf, the final product) is within E_g of gelu at the
+# float32 z, and |gelu'| <= 1.129, so the float32 activation lies within delta
+# of gelu(z_exact) and rounds to a BF16 value in [bf16(g - delta), bf16(g + delta)].
+# ACC_ULPS = 4 is a realistic scale, not the worst case (K units): measured on
+# the GB300 tensor cores, the exact activation of every flipped BF16 rounding
+# lay within 1.1e-7 sum |h W| (below 2 units) of the rounding midpoint.
+GELU_GRAD_MAX = 1.1289
+ACC_ULPS = 4
+
+
+def layer_delta(h_prev, W, z, acc_ulps=ACC_ULPS):
+    """Per-activation bound delta on |gelu_f32(z_f32) - gelu(z)| (see above)."""
+    s_abs = np.abs(h_prev) @ np.abs(W).T
+    ez = acc_ulps * 2.0 ** -24 * s_abs + 2.0 ** -24 * np.abs(z)
+    g = gelu(z)
+    eg = 0.5 * np.abs(z) * (2.0 ** -24 * np.abs(z) + 2.0 ** -21 + 2.0 ** -23) + 2.0 ** -23 * np.abs(g)
+    return GELU_GRAD_MAX * ez + eg
+
+
+def hidden_layer_check(h_prev, W, b, acc_ulps=ACC_ULPS):
+    """One hidden layer on given BF16 inputs h_prev (exact values): returns
+    (h, lo, hi) with h = bf16(gelu(z)) from the exact FP64 pre-activation
+    z = h_prev bf16(W)^T + b, and [lo, hi] the BF16 values a float32 evaluation
+    can round to: bf16(gelu(z) - delta) .. bf16(gelu(z) + delta).  Where lo < hi
+    the exact activation sits within delta of a BF16 rounding midpoint, and
+    either neighbour is a correct float32 result."""
+    Wb = bf16(W)
+    z = h_prev @ Wb.T + b
+    g = gelu(z)
+    d = layer_delta(h_prev, Wb, z, acc_ulps)
+    return bf16(g), bf16(g - d), bf16(g + d)
+
+
+def head_delta(h4, w5, logit):
+    """Bound on |float32 logit - exact logit| for given h4: the 256-term float32
+    dot product and the bias addition."""
+    return 257 * 2.0 ** -23 * (np.abs(h4) @ np.abs(bf16(w5)).reshape(-1)) + 2.0 ** -23 * np.abs(logit)
+
+
 def loss(logit, y):
     """Mean binary cross-entropy with logits."""
     return float(np.mean(np.logaddexp(0.0, logit) - y * logit))

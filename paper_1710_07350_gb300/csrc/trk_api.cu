@@ -55,6 +55,7 @@ struct trk_lattice {
     std::vector<std::pair<int, int>> groups;
     int max_bins = 0;
     bool transverse = false; // a wake with a transverse part
+    uint32_t survival_rows = 0x3Fu;  // map rows a survival scan needs (survival_rows())
 };
 
 struct trk_bunch {
@@ -95,6 +96,9 @@ struct trk_bunch {
 
 // Fused tracking launch with optional event timing and launch counting.
 static cudaError_t track_launch(trk_bunch *b, const TrackArgs &a, int n_tiles) {
+    // a launch that kicks with a collective element or fills its window reads
+    // the window keys; never send it without them
+    if ((a.kick_wake >= 0 || a.minmax_slot >= 0) && !a.win) return cudaErrorInvalidValue;
     std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
     if (b->timing) {
         if (!b->ev_free.empty()) {
@@ -169,6 +173,43 @@ static trk_status compile_map(const trk_element_desc &d, int idx, DevElem &E, st
     return TRK_OK;
 }
 
+// Coordinates a survival scan needs: the aperture reads x and y; a map row
+// that is needed reads the coordinates of its terms (and its own, when its
+// diagonal coefficient is 1); a thin sextupole reads x and y; an exact drift
+// moves x, y by the slopes and l by a function of both.  The set is grown over
+// the whole lattice until it stops changing (the lattice repeats every turn).
+// Rows outside it never influence an aperture test, so a survival scan may
+// skip them and still take bit-identical decisions.  Any other element type
+// keeps every row.
+static uint32_t survival_rows(const trk_lattice &L) {
+    uint32_t need = 0x5u;   // x (0) and y (2)
+    for (int it = 0; it < 8; ++it) {
+        const uint32_t before = need;
+        for (const DevElem &E : L.elems) {
+            if (E.type == TRK_MAP) {
+                for (int r = 0; r < 6; ++r) {
+                    if (!((need >> r) & 1u)) continue;
+                    for (int k = E.rb[r]; k < E.rb[r + 1]; ++k) {
+                        const int code = L.terms[E.term0 + k].code;
+                        const int deg = code & 3;
+                        if (deg >= 1) need |= 1u << ((code >> 2) & 7);
+                        if (deg >= 2) need |= 1u << ((code >> 5) & 7);
+                        if (deg >= 3) need |= 1u << ((code >> 8) & 7);
+                    }
+                }
+            } else if (E.type == TRK_THINSEXT) {
+                need |= 0x5u;
+            } else if (E.type == TRK_EDRIFT) {
+                if (need & 0x15u) need |= 0xAu;   // x, y or l needs the slopes
+            } else {
+                return 0x3Fu;
+            }
+        }
+        if (need == before) break;
+    }
+    return need & 0x3Fu;
+}
+
 extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t n, const trk_lattice_opts *opts,
                                          trk_lattice **out) {
     if (!out) return fail(TRK_EINVAL, "trk_create_lattice: out is NULL");
@@ -234,6 +275,8 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
             E.p[1] = phi;
             E.p[2] = 2.0 * kPi * d.freq_hz / kClight;
             E.p[3] = d.volt * std::cos(phi);
+            E.p[4] = std::cos(phi);
+            E.p[5] = std::sin(phi);
             break;
         }
         case TRK_SBEND:
@@ -342,6 +385,8 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.terms = L->d_terms;
     v.n_elem = n;
     v.ap_type = opts->aperture;
+    v.row_mask = 0x3Fu;
+    L->survival_rows = survival_rows(*L);
     v.ap_a = opts->a;
     v.ap_b = opts->b;
     // |x| <= a as integers: bit patterns of the positive bounds shifted left by one
@@ -574,6 +619,7 @@ static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     a.loss_turn = b->lt;
     a.loss_elem = b->le;
     a.st = b->st;
+    a.win = reinterpret_cast<unsigned long long *>(b->st->lkey);
     a.lat = L->view;
     a.n_tiles = n_tiles;
     a.partials = b->partials;
@@ -587,87 +633,154 @@ static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     return a;
 }
 
-extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_turns) {
-    if (!b || !L) return fail(TRK_EINVAL, "trk_track: NULL bunch or lattice");
-    if (n_turns < 0) return fail(TRK_EINVAL, "trk_track: n_turns < 0");
-    if (b->turn + n_turns > 0x7fffffffll) return fail(TRK_EINVAL, "trk_track: turn counter overflow");
-    if (!b->p0c_set) {
-        b->p0c = L->p0c;
-        b->p0c_set = true;
+// Tracks one physical bunch held in np parts (np = 1: an ordinary bunch).  The
+// parts share the reference momentum and the turn counter; each part is
+// tracked, compacted and gets its moments on its own, while every collective
+// element (wake, space charge) sees the union of the parts' alive particles:
+// the l window is reduced over all parts into the first part's keys, every
+// part adds its particles to the first part's histogram, the field is computed
+// once with q_m = Q / (sum of the parts' n), and every part takes its kick from
+// those voltages in its next segment's prologue.
+static trk_status track_parts(trk_bunch *const *P, int np, const trk_lattice *L, int32_t n_turns,
+                              const char *who) {
+    trk_bunch *lead = P[0];
+    const std::string w(who);
+    for (int k = 0; k < np; ++k) {
+        trk_bunch *b = P[k];
+        if (b->turn + n_turns > 0x7fffffffll) return fail(TRK_EINVAL, w + ": turn counter overflow");
+        if (!b->p0c_set) {
+            b->p0c = L->p0c;
+            b->p0c_set = true;
+        }
+        b->moments_turns = 0;
     }
-    b->moments_turns = 0;
-    if (n_turns == 0 || b->n == 0) {
-        b->turn += n_turns;
+    for (int k = 1; k < np; ++k)
+        if (P[k]->p0c != lead->p0c || P[k]->turn != lead->turn)
+            return fail(TRK_EINVAL, w + ": the parts of a bunch must share the reference momentum and the turn");
+    int64_t n_total = 0;
+    for (int k = 0; k < np; ++k) n_total += P[k]->n;
+    if (n_turns == 0 || n_total == 0) {
+        for (int k = 0; k < np; ++k) P[k]->turn += n_turns;
         return TRK_OK;
     }
-    const int tile = b->block * b->per_thread;
-    const int n_tiles = (int)((b->n + tile - 1) / tile);
     const bool wakes = !L->wakes.empty();
-    const int chunk = b->chunk < n_turns ? b->chunk : n_turns;
-    if (L->moments) {
-        trk_status s = ensure_moments(b, n_turns, n_tiles, chunk);
-        if (s != TRK_OK) return s;
-    }
-    if (wakes) {
-        trk_status s = ensure_wake(b, L->max_bins, L->transverse);
-        if (s != TRK_OK) return s;
-    }
     const int ne = L->view.n_elem;
-    const double qm_base = 1.0 / (double)b->n;
-    for (int t0 = 0; t0 < n_turns; t0 += chunk) {
-        const int nt = chunk < n_turns - t0 ? chunk : n_turns - t0;
-        TrackArgs a = base_args(b, L, n_tiles);
-        if (!wakes) {
-            a.e0 = 0;
-            a.e1 = ne;
-            a.n_turns = nt;
-            a.turn_abs0 = (int32_t)(b->turn + t0);
-            a.local_turn0 = 0;
-            a.do_moments = L->moments;
-            a.p0c = b->p0c;
-            TRK_CUDA(track_launch(b, a, n_tiles));
-            for (int t = 0; t < nt; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
-        } else {
-            const int ng = (int)L->groups.size();
-            const auto transverse = [&](int e) {
-                return e >= 0 && L->elems[e].type == TRK_WAKE && L->elems[e].p[3] != 0.0;
-            };
-            // histogram and field of collective element e on the window of `slot`,
-            // voltages into V (and the transverse ones into Vt)
-            const auto collective = [&](int e, int slot, double p0, double *V, double *Vt) -> trk_status {
-                const DevElem &W = L->elems[e];
-                const bool lsc = W.type == TRK_LSC;
-                const bool tr = transverse(e);
-                TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, slot, W.n, lsc ? 0.0 : W.p[0],
-                                          lsc ? 1.0 : W.p[1], b->hist, b->wfun, lsc ? 0.0 : W.p[3],
-                                          tr ? b->dip : nullptr, b->wfun_t, b->n, b->stream));
-                if (lsc && W.p[5] > 0.0) {
-                    const double r = p0 / W.p[6];
-                    TRK_CUDA(launch_lsc_imp(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[9], W.p[5],
-                                            std::sqrt(1.0 + r * r), W.p[7], W.p[8], b->lsc, V, b->stream));
-                    b->launches += 3;
-                } else {
-                    if (lsc)
-                        TRK_CUDA(launch_lsc_field(b->hist, b->st, slot, W.n, W.p[2] / (double)b->n, W.p[4],
-                                                  (int)W.flags, b->wfun, b->lsc, V, b->stream));
-                    else
-                        TRK_CUDA(launch_wake_conv(b->hist, b->wfun, W.n, W.p[2] * qm_base, V, b->stream));
-                    b->launches += 2;
-                }
-                if (tr) {
-                    TRK_CUDA(launch_wake_conv_t(b->dip, b->wfun_t, W.n, W.p[2] * qm_base, Vt, b->stream));
+    if (!wakes) {
+        // no collective element: the parts are independent bunches
+        for (int k = 0; k < np; ++k) {
+            trk_bunch *b = P[k];
+            if (b->n == 0) {
+                b->turn += n_turns;
+                continue;
+            }
+            const int tile = b->block * b->per_thread;
+            const int n_tiles = (int)((b->n + tile - 1) / tile);
+            const int chunk = b->chunk < n_turns ? b->chunk : n_turns;
+            if (L->moments) {
+                trk_status s = ensure_moments(b, n_turns, n_tiles, chunk);
+                if (s != TRK_OK) return s;
+            }
+            for (int t0 = 0; t0 < n_turns; t0 += chunk) {
+                const int nt = chunk < n_turns - t0 ? chunk : n_turns - t0;
+                TrackArgs a = base_args(b, L, n_tiles);
+                a.e0 = 0;
+                a.e1 = ne;
+                a.n_turns = nt;
+                a.turn_abs0 = (int32_t)(b->turn + t0);
+                a.local_turn0 = 0;
+                a.do_moments = L->moments;
+                a.p0c = b->p0c;
+                TRK_CUDA(track_launch(b, a, n_tiles));
+                for (int t = 0; t < nt; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
+                if (L->moments) {
+                    TRK_CUDA(launch_moments_finalize(b->partials, n_tiles, nt, b->st, tile,
+                                                     b->moments + (size_t)t0 * kMomentsN, b->stream));
                     ++b->launches;
                 }
-                return TRK_OK;
-            };
-            for (int t = 0; t < nt; ++t) {
-                int e_start = 0, prev = -1, prev2 = -1, prev_slot = 0;
-                double p0 = b->p0c;
-                for (int s = 0; s <= ng; ++s) {
-                    const int e_first = s < ng ? L->groups[s].first : ne;
-                    const int e_second = s < ng ? L->groups[s].second : -1;
-                    const int slot = s & 1;
-                    TrackArgs g = a;
+                TRK_CUDA(launch_compact(compact_args(b, tile, n_tiles), n_tiles, b->stream));
+                b->launches += 4;
+            }
+            b->turn += n_turns;
+            b->moments_turns = L->moments ? n_turns : 0;
+        }
+        return TRK_OK;
+    }
+    const int chunk = lead->chunk < n_turns ? lead->chunk : n_turns;
+    std::vector<int> tiles(np), n_tiles(np);
+    for (int k = 0; k < np; ++k) {
+        trk_bunch *b = P[k];
+        tiles[k] = b->block * b->per_thread;
+        n_tiles[k] = (int)((b->n + tiles[k] - 1) / tiles[k]);
+        if (L->moments && b->n > 0) {
+            trk_status s = ensure_moments(b, n_turns, n_tiles[k], chunk);
+            if (s != TRK_OK) return s;
+        }
+    }
+    {
+        trk_status s = ensure_wake(lead, L->max_bins, L->transverse);
+        if (s != TRK_OK) return s;
+    }
+    const double qm_base = 1.0 / (double)n_total;
+    unsigned long long *win = reinterpret_cast<unsigned long long *>(lead->st->lkey);
+    const int ng = (int)L->groups.size();
+    const auto transverse = [&](int e) {
+        return e >= 0 && L->elems[e].type == TRK_WAKE && L->elems[e].p[3] != 0.0;
+    };
+    // histogram (over every part) and field of collective element e on the
+    // window of `slot`, voltages into V (and the transverse ones into Vt)
+    const auto collective = [&](int e, int slot, double p0, double *V, double *Vt) -> trk_status {
+        const DevElem &W = L->elems[e];
+        const bool lsc = W.type == TRK_LSC;
+        const bool tr = transverse(e);
+        for (int k = 0; k < np; ++k) {
+            trk_bunch *b = P[k];
+            if (b->n == 0) continue;
+            TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, win, slot, W.n, lsc ? 0.0 : W.p[0],
+                                      lsc ? 1.0 : W.p[1], lead->hist, lead->wfun, lsc ? 0.0 : W.p[3],
+                                      tr ? lead->dip : nullptr, lead->wfun_t, b->n, lead->stream));
+            ++b->launches;
+        }
+        if (lsc && W.p[5] > 0.0) {
+            const double r = p0 / W.p[6];
+            TRK_CUDA(launch_lsc_imp(lead->hist, lead->st, slot, W.n, W.p[2] / (double)n_total, W.p[9], W.p[5],
+                                    std::sqrt(1.0 + r * r), W.p[7], W.p[8], lead->lsc, V, lead->stream));
+            lead->launches += 2;
+        } else {
+            if (lsc)
+                TRK_CUDA(launch_lsc_field(lead->hist, lead->st, slot, W.n, W.p[2] / (double)n_total, W.p[4], (int)W.flags,
+                                          lead->wfun, lead->lsc, V, lead->stream));
+            else
+                TRK_CUDA(launch_wake_conv(lead->hist, lead->wfun, W.n, W.p[2] * qm_base, V, lead->stream));
+            ++lead->launches;
+        }
+        if (tr) {
+            TRK_CUDA(launch_wake_conv_t(lead->dip, lead->wfun_t, W.n, W.p[2] * qm_base, Vt, lead->stream));
+            ++lead->launches;
+        }
+        return TRK_OK;
+    };
+    double p0c = lead->p0c;
+    for (int t0 = 0; t0 < n_turns; t0 += chunk) {
+        const int nt = chunk < n_turns - t0 ? chunk : n_turns - t0;
+        for (int t = 0; t < nt; ++t) {
+            int e_start = 0, prev = -1, prev2 = -1, prev_slot = 0;
+            double p0 = p0c;
+            for (int s = 0; s <= ng; ++s) {
+                const int e_first = s < ng ? L->groups[s].first : ne;
+                const int e_second = s < ng ? L->groups[s].second : -1;
+                const int slot = s & 1;
+                if (s < ng) {
+                    TRK_CUDA(launch_wake_reset(lead->st, slot, lead->hist, transverse(e_first) ? lead->dip : nullptr,
+                                               L->elems[e_first].n, true, lead->stream));
+                    ++lead->launches;
+                }
+                for (int k = 0; k < np; ++k) {
+                    trk_bunch *b = P[k];
+                    if (b->n == 0) continue;
+                    TrackArgs g = base_args(b, L, n_tiles[k]);
+                    g.win = win;
+                    g.wake_V = lead->V;
+                    g.wake_V2 = lead->V2;
                     g.e0 = e_start;
                     g.e1 = e_first;
                     g.n_turns = 1;
@@ -677,50 +790,72 @@ extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_tu
                     g.kick_wake2 = prev2;
                     g.kick_slot = prev_slot;
                     g.wake_nbins = prev >= 0 ? L->elems[prev].n : 0;
-                    g.wake_Vx = transverse(prev) ? b->Vt : nullptr;
+                    g.wake_Vx = transverse(prev) ? lead->Vt : nullptr;
                     g.wake_nbins2 = prev2 >= 0 ? L->elems[prev2].n : 0;
-                    g.wake_Vx2 = transverse(prev2) ? b->Vt2 : nullptr;
+                    g.wake_Vx2 = transverse(prev2) ? lead->Vt2 : nullptr;
                     g.minmax_slot = s < ng ? slot : -1;
                     g.do_moments = L->moments && s == ng;
                     g.p0c = p0;
-                    if (s < ng) {
-                        TRK_CUDA(launch_wake_reset(b->st, slot, b->hist, transverse(e_first) ? b->dip : nullptr,
-                                                   L->elems[e_first].n, true, b->stream));
-                        ++b->launches;
-                    }
-                    TRK_CUDA(track_launch(b, g, n_tiles));
-                    p0 = advance_p0(L, e_start, e_first, p0);
-                    if (s < ng) {
-                        trk_status st = collective(e_first, slot, p0, b->V, b->Vt);
-                        if (st != TRK_OK) return st;
-                        if (e_second >= 0) {   // same particles, same l: the window of `slot` stands
-                            TRK_CUDA(launch_wake_reset(b->st, slot, b->hist,
-                                                       transverse(e_second) ? b->dip : nullptr,
-                                                       L->elems[e_second].n, false, b->stream));
-                            ++b->launches;
-                            st = collective(e_second, slot, p0, b->V2, b->Vt2);
-                            if (st != TRK_OK) return st;
-                        }
-                    }
-                    prev = s < ng ? e_first : -1;
-                    prev2 = e_second;
-                    prev_slot = slot;
-                    e_start = (e_second >= 0 ? e_second : e_first) + 1;
+                    TRK_CUDA(track_launch(b, g, n_tiles[k]));
                 }
-                b->p0c = p0;
+                p0 = advance_p0(L, e_start, e_first, p0);
+                if (s < ng) {
+                    trk_status st = collective(e_first, slot, p0, lead->V, lead->Vt);
+                    if (st != TRK_OK) return st;
+                    if (e_second >= 0) {   // same particles, same l: the window of `slot` stands
+                        TRK_CUDA(launch_wake_reset(lead->st, slot, lead->hist,
+                                                   transverse(e_second) ? lead->dip : nullptr,
+                                                   L->elems[e_second].n, false, lead->stream));
+                        ++lead->launches;
+                        st = collective(e_second, slot, p0, lead->V2, lead->Vt2);
+                        if (st != TRK_OK) return st;
+                    }
+                }
+                prev = s < ng ? e_first : -1;
+                prev2 = e_second;
+                prev_slot = slot;
+                e_start = (e_second >= 0 ? e_second : e_first) + 1;
             }
+            p0c = p0;
         }
-        if (L->moments) {
-            TRK_CUDA(launch_moments_finalize(b->partials, n_tiles, nt, b->st, tile,
-                                             b->moments + (size_t)t0 * kMomentsN, b->stream));
-            ++b->launches;
+        for (int k = 0; k < np; ++k) {
+            trk_bunch *b = P[k];
+            if (b->n == 0) continue;
+            if (L->moments) {
+                TRK_CUDA(launch_moments_finalize(b->partials, n_tiles[k], nt, b->st, tiles[k],
+                                                 b->moments + (size_t)t0 * kMomentsN, b->stream));
+                ++b->launches;
+            }
+            TRK_CUDA(launch_compact(compact_args(b, tiles[k], n_tiles[k]), n_tiles[k], b->stream));
+            b->launches += 4;
         }
-        TRK_CUDA(launch_compact(compact_args(b, tile, n_tiles), n_tiles, b->stream));
-        b->launches += 4;
     }
-    b->turn += n_turns;
-    b->moments_turns = L->moments ? n_turns : 0;
+    for (int k = 0; k < np; ++k) {
+        P[k]->p0c = p0c;
+        P[k]->turn += n_turns;
+        P[k]->moments_turns = L->moments && P[k]->n > 0 ? n_turns : 0;
+    }
     return TRK_OK;
+}
+
+extern "C" trk_status trk_track(trk_bunch *b, const trk_lattice *L, int32_t n_turns) {
+    if (!b || !L) return fail(TRK_EINVAL, "trk_track: NULL bunch or lattice");
+    if (n_turns < 0) return fail(TRK_EINVAL, "trk_track: n_turns < 0");
+    return track_parts(&b, 1, L, n_turns, "trk_track");
+}
+
+extern "C" trk_status trk_track_parts(trk_bunch *const *parts, int32_t n_parts, const trk_lattice *L,
+                                      int32_t n_turns) {
+    if (!parts || n_parts < 1 || !L) return fail(TRK_EINVAL, "trk_track_parts: need n_parts >= 1 bunches and a lattice");
+    if (n_turns < 0) return fail(TRK_EINVAL, "trk_track_parts: n_turns < 0");
+    for (int k = 0; k < n_parts; ++k) {
+        if (!parts[k]) return fail(TRK_EINVAL, "trk_track_parts: NULL part");
+        if (parts[k]->stream != parts[0]->stream)
+            return fail(TRK_EINVAL, "trk_track_parts: all parts must use the same stream");
+        for (int j = 0; j < k; ++j)
+            if (parts[j] == parts[k]) return fail(TRK_EINVAL, "trk_track_parts: a part appears twice");
+    }
+    return track_parts(parts, n_parts, L, n_turns, "trk_track_parts");
 }
 
 extern "C" trk_status trk_moments(trk_bunch *b, double *host_out, int32_t cap_turns, int32_t *n_turns) {
@@ -771,7 +906,8 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     if (s != TRK_OK) return s;
     TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nullptr, nbins, true, b->stream));
     TRK_CUDA(launch_wake_minmax(b->coords, b->pitch, b->lt, b->st, 0, b->n, b->stream));
-    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, 0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
+    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, reinterpret_cast<const unsigned long long *>(b->st->lkey),
+                              0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
                               nullptr, b->n, b->stream));
     TRK_CUDA(launch_wake_conv(b->hist, b->wfun, nbins, charge / (double)b->n, b->V, b->stream));
     const int tile = b->block * b->per_thread;
@@ -783,6 +919,7 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     a.loss_turn = b->lt;
     a.loss_elem = b->le;
     a.st = b->st;
+    a.win = reinterpret_cast<unsigned long long *>(b->st->lkey);   // the window the kick reads
     a.lat.ap_type = TRK_APERTURE_NONE;
     a.e0 = a.e1 = 0;
     a.n_turns = 1;
@@ -814,6 +951,7 @@ struct trk_batch {
     cudaStream_t capture = nullptr;  // private stream used only to capture the graph
     int block = 128, per_thread = 2, chunk = 100, growth = 0;
     bool moments = false;
+    bool survival_only = false;   // internal (survival scans): map rows limited to survival_rows
     // device tables
     TrackArgs *d_args = nullptr;
     size_t args_cap = 0;
@@ -978,6 +1116,7 @@ extern "C" trk_status trk_batch_track(trk_batch *B, int32_t n_turns) {
         int t0 = 0;
         for (int c = 0; c < nc; ++c) {
             TrackArgs a = base_args(b, L, nt);
+            if (B->survival_only) a.lat.row_mask = L->survival_rows;
             a.e0 = 0;
             a.e1 = ne;
             a.n_turns = chunks[c];
@@ -1070,7 +1209,10 @@ extern "C" trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int3
     if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival_lanes: NULL point or output array");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<LatticeView> hv(n_var);
-    for (int v = 0; v < n_var; ++v) hv[v] = lats[v]->view;
+    for (int v = 0; v < n_var; ++v) {
+        hv[v] = lats[v]->view;
+        hv[v].row_mask = lats[v]->survival_rows;
+    }
     LatticeView *dv = nullptr;
     int64_t *doff = nullptr;
     cudaError_t e = cudaMalloc(&dv, n_var * sizeof(LatticeView));
@@ -1132,6 +1274,7 @@ extern "C" trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_
         }
     }
     if (st == TRK_OK && !bunches.empty()) st = trk_batch_create(bunches.data(), L.data(), (int32_t)bunches.size(), &B);
+    if (st == TRK_OK && B) B->survival_only = true;   // only the loss turns leave this call
     if (st == TRK_OK && B) {
         trk_schedule def = {128, 2, 1, 2};  // short chunks first: most lost particles leave early
         st = trk_batch_set_schedule(B, sched ? sched : &def);

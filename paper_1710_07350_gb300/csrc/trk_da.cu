@@ -8,6 +8,13 @@
 // and exchanged by warp shuffles; everything else runs replicated on every
 // lane.  Each row sums its terms in the order, and with the operations, of the
 // tracking kernel, so the survival turns are bit-identical.
+//
+// Both scans (this kernel and the batched tracker under trk_da_survival)
+// evaluate only the map rows in the lattice's survival rows: the rows on which
+// an aperture test depends, directly or through other rows (for a ring of maps
+// and thin sextupoles without RF, every row but the path length).  A skipped
+// row is never read by an evaluated one, so every loss decision is the one
+// full tracking takes.
 #include "trk_device.cuh"
 #include "trk_internal.cuh"
 
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                 const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
                 const double2 *t = reinterpret_cast<const double2 *>(L.terms + __ldg(&E->term0));
                 const int rr = r < 6 ? r : 0;
-                const int kb = rb[rr], len = r < 6 ? rb[rr + 1] - rb[rr] : 0;
+                const int kb = rb[rr], len = (r < 6 && ((L.row_mask >> rr) & 1u)) ? rb[rr + 1] - rb[rr] : 0;
                 double acc = (r < 6 && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
                 const double z0 = __ldg(&E->p[0]) * 0.0;   // as the tracking kernel's map
                 for (int k = 0; k < len; ++k) {

@@ -54,6 +54,10 @@ struct LatticeView {
     const DevTerm *terms;
     int32_t n_elem;
     int32_t ap_type;
+    // Map rows evaluated (bit r = row r): all six for tracking; in survival
+    // scans only the rows the aperture test depends on (see survival_rows).
+    uint32_t row_mask;
+    int32_t pad_;
     double ap_a, ap_b;
     unsigned long long ap_a_key, ap_b_key;   // bit patterns of a, b (> 0) shifted left by one
     unsigned long long ap_ia_key, ap_ib_key; // the same of 0.7 a, 0.7 b: inner box of the ellipse
@@ -75,6 +79,8 @@ struct TrackArgs {
     int32_t *loss_turn;     // -1 = alive
     int32_t *loss_elem;
     BunchState *st;
+    unsigned long long *win;  // l-window keys of the collective elements ([2s] min, [2s+1] max): st->lkey,
+                              // or the first part's for a bunch held in several parts
     LatticeView lat;
     int32_t e0, e1;
     int32_t n_turns;        // > 1 only when [e0, e1) is the whole lattice
@@ -132,7 +138,8 @@ cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned
                               bool reset_keys, cudaStream_t s);
 cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
                                int slot, int64_t n_max, cudaStream_t s);
-cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot, int nbins,
+cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, const BunchState *st,
+                             const unsigned long long *win, int slot, int nbins,
                              double w0, double sc, uint32_t *hist, double *wfun, double w0t, unsigned long long *dip,
                              double *wfun_t, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
@@ -161,6 +168,7 @@ size_t umma_layer_smem(int K);
 cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, const float *bias, int K,
                               int64_t n_tiles, uint16_t *out_tiled, int *d_err, cudaStream_t s);
 cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s);
+cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, cudaStream_t s);
 cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s);
 cudaError_t launch_head_tiled(const uint16_t *H4, const uint16_t *w5, const float *b5, int64_t M, float *logit,
                               cudaStream_t s);

@@ -510,8 +510,11 @@ static cudaError_t mlp_forward_rows(trk_mlp *N, const float *X, int64_t M, int64
 }
 
 // Inference on the tcgen05 layers: inputs and activations in the tiled layout
-// of trk_mlp_umma.cu, 2^18-row chunks (a multiple of the 128-row tile).
-extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, float *d_logits, void *stream) {
+// of trk_mlp_umma.cu, 2^18-row chunks (a multiple of the 128-row tile).  With
+// d_hidden, each hidden layer's BF16 output of rows [r0, r0 + m) is also copied
+// out row-major to d_hidden + (l * M + r0) * 256.
+extern "C" trk_status trk_mlp_forward_hidden(trk_mlp *N, const float *d_X, int64_t M, float *d_logits,
+                                             uint16_t *d_hidden, void *stream) {
     if (!N || M < 0 || (M > 0 && (!d_X || !d_logits))) return mlp_fail(TRK_EINVAL, "trk_mlp_forward: bad argument");
     if (M == 0) return TRK_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -536,9 +539,12 @@ extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, f
         const int64_t m_pad = (m + 127) / 128 * 128;
         e = launch_input_tiled(d_X + r0 * kIn, m, m_pad, N->act[0], s);
         int cur = 0;
-        for (int l = 0; l < kHidden && e == cudaSuccess; ++l, cur ^= 1)
+        for (int l = 0; l < kHidden && e == cudaSuccess; ++l, cur ^= 1) {
             e = launch_umma_layer(N->act[cur], N->wt + N->wt_off[l], N->p + N->b_off[l], N->in_pad[l], m_pad / 128,
                                   N->act[cur ^ 1], N->d_err, s);
+            if (e == cudaSuccess && d_hidden)
+                e = launch_from_tiled(N->act[cur ^ 1], m, d_hidden + ((size_t)l * M + r0) * kW, s);
+        }
         if (e == cudaSuccess) e = launch_head_tiled(N->act[cur], pb + N->w_off[4], N->p + N->b_off[4], m, d_logits + r0, s);
     }
     int herr = 0;
@@ -550,6 +556,10 @@ extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, f
         return mlp_fail(TRK_ETIMEOUT, "trk_mlp_forward: a tensor-core layer gave up waiting on a barrier");
     }
     return TRK_OK;
+}
+
+extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, float *d_logits, void *stream) {
+    return trk_mlp_forward_hidden(N, d_X, M, d_logits, nullptr, stream);
 }
 
 // Gradients of the mean BCE over M rows into N->g; loss into N->loss.

@@ -257,6 +257,21 @@ __global__ void k_to_tiled(const __nv_bfloat16 *__restrict__ src, int64_t rows, 
     }
 }
 
+// Tiled activations (K = 256, 128-row tiles) -> row-major [rows][256]: the
+// inverse of k_to_tiled for rows [0, rows) of an activation buffer.
+__global__ void k_from_tiled(const __nv_bfloat16 *__restrict__ src, int64_t rows, __nv_bfloat16 *__restrict__ dst) {
+    constexpr int K = UN, kc = K / KCH;
+    const int64_t pieces = rows * (K / 8);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < pieces; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = p / (K / 8);
+        const int cg = (int)(p % (K / 8));
+        const int64_t t = r / UM;
+        const int rr = (int)(r % UM), c = cg >> 3, kg = cg & 7;
+        const size_t off = (((size_t)t * kc + c) * (UM / 8) + (rr >> 3)) * 8 * 64 + (size_t)kg * 64 + (rr & 7) * 8;
+        *reinterpret_cast<uint4 *>(dst + r * K + cg * 8) = *reinterpret_cast<const uint4 *>(src + off);
+    }
+}
+
 // x [M x 8] FP32 -> h0 tiled (K = 64: one chunk; columns 8..63 zero; rows >= M zero).
 __global__ void k_input_tiled(const float *__restrict__ X, int64_t M, int64_t m_pad, __nv_bfloat16 *__restrict__ H0) {
     const int64_t pieces = m_pad * 8;
@@ -330,6 +345,12 @@ cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, 
 cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s) {
     k_to_tiled<<<grid_for(rows * (K / 8)), 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(src), rows, K,
                                                        tile_rows, reinterpret_cast<__nv_bfloat16 *>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, cudaStream_t s) {
+    k_from_tiled<<<grid_for(rows * (UN / 8)), 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(src), rows,
+                                                         reinterpret_cast<__nv_bfloat16 *>(dst));
     return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ double tget(const Tile<P> &q, int p, int j) {
 // rows (which is what bounds a lightly occupied GPU).
 template <int P>
 __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E, const DevTerm *__restrict__ terms,
-                                      bool &dirty) {
+                                      uint32_t rows, bool &dirty) {
     const uint32_t flags = __ldg(&E->flags);
     const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
     const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
@@ -58,7 +58,7 @@ __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E,
     int len[6], n = 0;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-        len[r] = rb[r + 1] - rb[r];
+        len[r] = ((rows >> r) & 1u) ? rb[r + 1] - rb[r] : 0;   // rows outside `rows` are not evaluated
         n = len[r] > n ? len[r] : n;
 #pragma unroll
         for (int p = 0; p < P; ++p) acc[r][p] = ((flags >> r) & 1u) ? tget(q, p, r) : 0.0;
@@ -361,16 +361,36 @@ __device__ __forceinline__ void v_sbend(Tile<P> &q, const DevElem *__restrict__ 
     }
 }
 
+// cos(phi + x) for |x| >= 2^-4 (or NaN), out of line: it runs only for the
+// particles that need it.
+__device__ __noinline__ double rf_cos_exact(double phi, double x) { return cos(phi + x); }
+
+// cos(phi + x) = cos(phi) C(x) - sin(phi) S(x) with the Taylor series of
+// C = cos and S = sin at 0 (Abramowitz & Stegun 4.3.65-66) through x^8 and x^9:
+// for |x| < 2^-4 the first dropped terms are below 3e-19, far under the
+// rounding of the result, so this is cos(phi + x) to FP64 rounding at about
+// half the instructions of a general cosine.  The test is an integer compare
+// of |x|'s high word (2^-4 = 0x3FB00000; NaN fails it).
+__device__ __forceinline__ double rf_cos(double cphi, double sphi, double phi, double x) {
+    const double x2 = x * x;
+    const double C = fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+    const double S = x * fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
+    double c = fma(cphi, C, -sphi * S);
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x3FB00000) c = rf_cos_exact(phi, x);
+    return c;
+}
+
 // Thin RF: P = (1+delta) p0, P' = P + V cos(phi + k l), delta' = P'/p0' - 1,
 // slopes scaled by P/P'.
 template <int P>
 __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E, double p0, double ip01,
                                        bool &dirty) {
     const double V = __ldg(&E->p[0]), phi = __ldg(&E->p[1]), k = __ldg(&E->p[2]);
+    const double cphi = __ldg(&E->p[4]), sphi = __ldg(&E->p[5]);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double Pp = (1.0 + q.d[p]) * p0;
-        const double P1 = fma(V, cos(fma(k, q.l[p], phi)), Pp);
+        const double P1 = fma(V, rf_cos(cphi, sphi, phi, k * q.l[p]), Pp);
         const double s = Pp / P1;
         q.xp[p] *= s;
         q.yp[p] *= s;
@@ -509,7 +529,7 @@ __device__ __forceinline__ void store_particle(const TrackArgs &a, int64_t i, co
 template <int P>
 __device__ __forceinline__ void wake_kick(const TrackArgs &a, Tile<P> &q, const bool (&alive)[P], double p0,
                                           const double *V, const double *Vx, int nbins) {
-    const uint64_t kmin = a.st->lkey[2 * a.kick_slot], kmax = a.st->lkey[2 * a.kick_slot + 1];
+    const uint64_t kmin = a.win[2 * a.kick_slot], kmax = a.win[2 * a.kick_slot + 1];
     const double lmin = dkey_inv(kmin), lmax = dkey_inv(kmax);
     const double dl = (lmax - lmin) / nbins;
     const bool flat = !(dl > 0.0);
@@ -632,7 +652,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                 canon = false;
             }
             switch (type) {
-            case TRK_MAP: v_map<P>(q, E, L.terms, dirty); break;
+            case TRK_MAP: v_map<P>(q, E, L.terms, L.row_mask, dirty); break;
             case TRK_EDRIFT:
                 // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
                 // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
@@ -693,8 +713,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicMin((unsigned long long *)&a.st->lkey[2 * a.minmax_slot], mm[0]);
-            atomicMax((unsigned long long *)&a.st->lkey[2 * a.minmax_slot + 1], mm[1]);
+            atomicMin(&a.win[2 * a.minmax_slot], mm[0]);
+            atomicMax(&a.win[2 * a.minmax_slot + 1], mm[1]);
         }
     }
 

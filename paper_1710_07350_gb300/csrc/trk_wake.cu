@@ -83,14 +83,15 @@ __device__ __forceinline__ unsigned long long dipole_units(double x) {
 
 __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__restrict__ coords, int64_t pitch,
                                                              const int32_t *__restrict__ lt, const BunchState *st,
-                                                             int slot, int nbins, double w0, double sc,
+                                                             const unsigned long long *win, int slot, int nbins,
+                                                             double w0, double sc,
                                                              uint32_t *__restrict__ hist, double *__restrict__ wfun,
                                                              double w0t, unsigned long long *__restrict__ dip,
                                                              double *__restrict__ wfun_t, int use_smem) {
     extern __shared__ __align__(8) unsigned char smem_raw[];
     uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw);
     const int64_t n = st->n_alive;
-    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const uint64_t kmin = win[2 * slot], kmax = win[2 * slot + 1];
     const bool any = kmin <= kmax;
     const double lmin = any ? dkey_inv(kmin) : 0.0;
     const double lmax = any ? dkey_inv(kmax) : 0.0;
@@ -520,7 +521,8 @@ cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st, int slot,
+cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, const BunchState *st,
+                             const unsigned long long *win, int slot,
                              int nbins, double w0, double sc, uint32_t *hist, double *wfun, double w0t,
                              unsigned long long *dip, double *wfun_t, int64_t n_max, cudaStream_t s) {
     // privatised sub-histograms up to kSmemBins bins, with the transverse sums up
@@ -542,8 +544,8 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
     int g = grid_for(n_max, kHistThreads, 152 * 2);
     const int gw = (nbins + kHistThreads - 1) / kHistThreads;
     if (g < gw) g = gw;
-    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, slot, nbins, w0, sc, hist, wfun, w0t, dip,
-                                              wfun_t, smem_ok ? 1 : 0);
+    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, nbins, w0, sc, hist, wfun, w0t,
+                                              dip, wfun_t, smem_ok ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,7 @@ def lib():
             "trk_bunch_p0c": [P, P],
             "trk_bunch_set_schedule": [P, P],
             "trk_track": [P, P, c_int32],
+            "trk_track_parts": [P, c_int32, P, c_int32],
             "trk_moments": [P, P, c_int32, P],
             "trk_lost": [P, P, P, P, c_int64, P],
             "trk_n_alive": [P, P],
@@ -106,6 +107,7 @@ def lib():
             "trk_mlp_create": [P, P, P],
             "trk_mlp_destroy": [P],
             "trk_mlp_forward": [P, P, c_int64, P, P],
+            "trk_mlp_forward_hidden": [P, P, c_int64, P, P, P],
             "trk_mlp_grad": [P, P, P, c_int32, P, P],
             "trk_mlp_adam": [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
             "trk_mlp_train": [P, P, P, c_int64, c_int32, c_int32, P, ctypes.c_float, P, P],
@@ -280,6 +282,11 @@ def trk_track(b, lat, n_turns):
     _check(lib().trk_track(b.handle, lat.handle, n_turns))
 
 
+def trk_track_parts(parts, lat, n_turns):
+    """Track one bunch held in several Bunch parts (see include/trk.h)."""
+    _check(lib().trk_track_parts(_handles(parts), len(parts), lat.handle, n_turns))
+
+
 def trk_moments(b, cap_turns=1 << 30):
     nt = c_int32()
     _check(lib().trk_moments(b.handle, None, 0, ctypes.byref(nt)))
@@ -451,6 +458,17 @@ def trk_mlp_forward(net, X, stream=None):
     out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
     _check(lib().trk_mlp_forward(net.handle, _dptr(X), X.shape[0], _dptr(out), _stream(X, stream)))
     return out
+
+
+def trk_mlp_forward_hidden(net, X, stream=None):
+    """X: float32 CUDA tensor (M, 8) -> (logits (M,) float32, hidden (4, M, 256)
+    int16 CUDA tensor holding each hidden layer's BF16 outputs bit for bit)."""
+    import torch
+    M = X.shape[0]
+    out = torch.empty(M, dtype=torch.float32, device=X.device)
+    hid = torch.empty((4, M, 256), dtype=torch.int16, device=X.device)
+    _check(lib().trk_mlp_forward_hidden(net.handle, _dptr(X), M, _dptr(out), _dptr(hid), _stream(X, stream)))
+    return out, hid
 
 
 def trk_mlp_grad(net, X, y, stream=None):

@@ -229,6 +229,33 @@ def gaussian_bunch(n, seed, tw, emit=EMIT, sigma_l=SIGMA_L, sigma_d=SIGMA_D,
     return z
 
 
+def gaussian_bunch_device(n, seed, tw, emit=EMIT, sigma_l=SIGMA_L, sigma_d=SIGMA_D, tail_frac=0.0,
+                          tail_half_width=0.0, device="cuda"):
+    """The distribution of gaussian_bunch drawn on the device (torch's own
+    generator, so not the same particles as the host draw): a (6, n) float64
+    CUDA tensor, for throughput runs whose bunch would be slow to make and
+    copy from the host."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    u = torch.randn((6, n), dtype=torch.float64, device=device, generator=g)
+    z = torch.empty((6, n), dtype=torch.float64, device=device)
+    for p, (beta, alpha) in enumerate(tw):
+        z[2 * p] = math.sqrt(emit * beta) * u[2 * p]
+        z[2 * p + 1] = math.sqrt(emit / beta) * (u[2 * p + 1] - alpha * u[2 * p])
+    z[4] = sigma_l * u[4]
+    z[5] = sigma_d * u[5]
+    if tail_frac > 0.0:
+        nt = int(round(tail_frac * n))
+        z[4, n - nt:] = (torch.rand(nt, dtype=torch.float64, device=device, generator=g) * 2.0 - 1.0) * tail_half_width
+    return z
+
+
+def c3_bunch_device(n, seed=3):
+    """The config-3 bunch distribution (95 % Gaussian, 5 % uniform tail) drawn on the device."""
+    return gaussian_bunch_device(n, seed, twiss("c3"), sigma_l=C3_SIGMA_L, tail_frac=0.05,
+                                 tail_half_width=6 * C3_SIGMA_L)
+
+
 def bunch(name, n=None, seed=None):
     """Standard bunch of a workload (n and seed may be overridden)."""
     if name == "c1":

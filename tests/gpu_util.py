@@ -14,6 +14,12 @@ TOL_MOM = 1e-12
 MARGIN = 1e-9
 
 
+def tol_turns(n):
+    """Coordinate tolerance after n turns between the two stated points: the
+    power law through 1e-12 at one pass and 1e-9 at 100 turns, TOL_PASS n^1.5."""
+    return TOL_PASS * float(n) ** 1.5
+
+
 def gpu_track(lat, z, n_turns, schedule=None, moments=True, calls=None):
     L = trk.trk_create_lattice(lat, moments=moments)
     coords, ids = trk.upload(z)

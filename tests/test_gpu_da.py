@@ -145,3 +145,114 @@ def test_lane_scan_rejects_kick_drift_lattice():
     # the general entry point falls back to the batched tracker
     s = trk.trk_da_survival(L, x0, y0, [0, 16], 5).cpu().numpy()
     assert np.all((s >= 1) & (s <= 6))
+
+
+def test_survival_scan_keeps_rows_that_feed_back():
+    """Survival scans skip the map rows no aperture test depends on (for the DA
+    lattices, the path-length row).  A lattice whose x' row reads l, and whose
+    l row reads x, must keep l: its scan equals full tracking of the same points
+    (loss turns of trk_track), in the batched and in the lane-parallel kernel;
+    and the unmodified lattice's pruned scan equals its full tracking too."""
+    n, turns = 20, 120
+    x0, y0, z = grid_points(n)
+    base = syn.lattice_c5(0)
+    els = []
+    for e in base["elements"]:
+        if e["type"] == "MAP" and e["map"]["order"] >= 1 and not els:
+            m = {k: np.array(v, dtype=np.float64, copy=True) for k, v in e["map"].items() if k != "order"}
+            m["order"] = e["map"]["order"]
+            R = m["R"].reshape(6, 6)
+            R[1, 4] += 5.0         # x' += 5 l
+            R[4, 0] += 1e-2        # l += 0.01 x
+            m["R"] = R.ravel()
+            els.append({"type": "MAP", "map": m})
+        else:
+            els.append(e)
+    lat = {**base, "elements": els}
+    L = trk.trk_create_lattice(lat, moments=False)
+    coords, ids = trk.upload(z)
+    b = trk.trk_bunch_wrap(coords, ids)
+    trk.trk_track(b, L, turns)
+    lid, lturn, _ = trk.trk_lost(b)
+    want = np.full(n * n, turns + 1)
+    want[lid] = lturn + 1
+    got = trk.trk_da_survival([L], x0, y0, [0, n * n], turns, schedule={"block": 128, "per_thread": 2,
+                                                                         "chunk_turns": 1, "growth": 2})
+    assert np.array_equal(got.cpu().numpy(), want)
+    lanes = trk.trk_da_survival_lanes([L], x0, y0, [0, n * n], turns)
+    assert np.array_equal(lanes.cpu().numpy(), want)
+    # the feedback matters: without it the survival differs somewhere
+    L0 = trk.trk_create_lattice(base, moments=False)
+    plain = trk.trk_da_survival_lanes([L0], x0, y0, [0, n * n], turns).cpu().numpy()
+    assert not np.array_equal(plain, want)
+    # the unmodified lattice (l pruned in the scan) against its full tracking
+    coords, ids = trk.upload(z)
+    b0 = trk.trk_bunch_wrap(coords, ids)
+    trk.trk_track(b0, L0, turns)
+    lid, lturn, _ = trk.trk_lost(b0)
+    want0 = np.full(n * n, turns + 1)
+    want0[lid] = lturn + 1
+    assert np.array_equal(plain, want0)
+    batched0 = trk.trk_da_survival([L0], x0, y0, [0, n * n], turns, schedule={"block": 128, "per_thread": 2,
+                                                                               "chunk_turns": 1, "growth": 2})
+    assert np.array_equal(batched0.cpu().numpy(), want0)
+
+
+def test_what_the_trained_network_gains():
+    """What the trained surrogate adds to the triage, measured on 4 variants of
+    a 96^2 grid (300 turns).  After trk_da_triage has trained the network in
+    place on the coarse cells, its prediction of every cell that is not known
+    before the prediction (neither a coarse nor a sentinel cell) is compared
+    with the exhaustive scan:
+    - against predicting without any model (each variant's majority label of
+      its coarse cells) the network must cut the wrong cells to a quarter or
+      less: it has learned the aperture;
+    - against the nearest known exact cell (the non-learned arm's predictor,
+      which sees the sentinel cells as well) it is not required to win: on this
+      workload the variants' apertures differ too much for one smooth function
+      of 8 inputs to beat a local interpolation of denser exact labels.  The
+      counts are printed; both triaged masks keep the one-cell boundary."""
+    nv, n, turns, stride = 4, 96, 300, 4
+    L = [trk.trk_create_lattice(syn.lattice_c5(v), moments=False) for v in range(nv)]
+    params_np = syn.c5_params()[:nv].astype(np.float32)
+    params = torch.from_numpy(params_np).cuda()
+    x0, y0, _ = grid_points(n)
+    exh = (trk.trk_da_survival(L, torch.cat([x0] * nv), torch.cat([y0] * nv), [k * n * n for k in range(nv + 1)],
+                               turns).cpu().numpy().reshape(nv, n, n) == turns + 1)
+    g = np.random.Generator(np.random.Philox(key=17))
+    opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
+            "band_radius": 2, "use_mlp": 1, "epochs": 60, "batch": 256, "lr": 2e-3, "sentinel_stride": 5,
+            "expand_radius": 0}
+    ncoarse = nv * ((n - stride // 2 + stride - 1) // stride) ** 2
+    perm = torch.from_numpy(np.stack([g.permutation(ncoarse) for _ in range(60)]).astype(np.int32)).cuda()
+    net = trk.trk_mlp_create(syn.mlp_init(7))
+    mask_s, _, st_s = trk.trk_da_triage(L, params, opts, net=net, perm=perm)
+    mask_n, _, st_n = trk.trk_da_triage(L, params, {**opts, "use_mlp": 0})
+    # the trained network's raw prediction of every cell
+    w = syn.DA_HALF_WIDTH
+    cc = (syn.da_grid(n, w) / w).astype(np.float32)
+    gx, gy = np.meshgrid(cc, cc)
+    X = np.concatenate([np.stack([np.tile(gx.ravel(), nv), np.tile(gy.ravel(), nv)], -1),
+                        np.repeat(params_np, n * n, axis=0)], -1).astype(np.float32)
+    pred = (trk.trk_mlp_forward(net, torch.from_numpy(X).cuda()).cpu().numpy() > 0).reshape(nv, n, n)
+    ci = otri.coarse_index(n, stride)
+    coarse = np.zeros((n, n), bool)
+    coarse[np.ix_(ci, ci)] = True
+    sa = otri.sentinel_axis(n, 5)
+    known = coarse.copy()
+    known[np.ix_(sa, sa)] = True
+    unknown = np.broadcast_to(~known, exh.shape)
+    wrong_net = int(np.sum((pred != exh) & unknown))
+    majority = np.array([exh[v][coarse].mean() > 0.5 for v in range(nv)])
+    wrong_const = int(np.sum((majority[:, None, None] != exh) & unknown))
+    from scipy import ndimage
+    _, (iy, ix) = ndimage.distance_transform_edt(~known, return_indices=True)
+    wrong_nk = int(sum(np.sum((exh[v][iy, ix] != exh[v]) & ~known) for v in range(nv)))
+    print("cells unknown before prediction %d: wrong with the network %d, with no model %d, with the nearest "
+          "known cell %d; band-tracked cells surrogate %d, non-learned %d"
+          % (int(unknown.sum()), wrong_net, wrong_const, wrong_nk, st_s["n_tracked"], st_n["n_tracked"]))
+    assert wrong_const > 0
+    assert wrong_net * 4 <= wrong_const
+    for v in range(nv):
+        assert dm.boundary_difference(mask_s.cpu().numpy()[v], exh[v])[0]
+        assert dm.boundary_difference(mask_n.cpu().numpy()[v], exh[v])[0]

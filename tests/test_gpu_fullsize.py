@@ -12,7 +12,7 @@ import synthetic as syn
 from oracle import oracle as orc
 from paper_1710_07350_gb300 import trk
 
-from gpu_util import MARGIN, TOL_100, reduction_check
+from gpu_util import MARGIN, TOL_100, TOL_PASS, compare_moments, compare_tracking, gpu_track, reduction_check
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -136,3 +136,21 @@ def test_c5_full_da_grid_bench_scan():
             keep &= oracle_survival(lat, zp, turns)[0] == want
         assert keep.sum() >= len(idx) // 3
         assert np.array_equal(s[idx][keep], want[keep])
+
+
+def test_c3_full_bunch_bench_launch():
+    """The wake linac at its full size in the bench's launch configuration: the
+    whole 1e7-particle bunch (95 % Gaussian, 5 % uniform tail), 4096-bin wakes,
+    block 128 x 2 particles per thread, through the first three periods (RF
+    cavity, wake, drift, quadrupole).  The wakes couple every particle, so the
+    oracle tracks the whole bunch and every particle is compared; after one pass
+    the tolerance is the one-pass 1e-12, and the per-element moments follow."""
+    lat = syn.lattice_c3(periods=3)
+    z = syn.bunch("c3")
+    assert z.shape[0] == 10_000_000
+    g = gpu_track(lat, z, 1, schedule={"block": 128, "per_thread": 2})
+    o = orc.track(lat, z, 1)
+    assert g["p0c"] == o["p0c"]
+    assert g["n_alive"] == z.shape[0]                # no aperture in the linac
+    err = compare_tracking(g, o, TOL_PASS)
+    compare_moments(g["moments"], o["moments"], coord_err=err)

@@ -26,20 +26,47 @@ def data(n, seed=1):
     return X, y
 
 
+def bf16_bits_to_f64(t):
+    """int16 CUDA tensor of BF16 bit patterns -> float64 numpy values."""
+    return (t.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
 @pytest.mark.parametrize("M", [1, 63, 1000, 70000])
 def test_forward_matches_oracle(M):
+    """Layer by layer from the GPU's own BF16 activations: each hidden layer's
+    output equals the oracle's bf16(gelu(z)) on the same inputs, or -- where
+    the exact activation lies within the float32 evaluation error of a BF16
+    rounding midpoint -- the other neighbour (an admissible flip); the logit
+    follows from the GPU's last hidden layer to float32 rounding.  End to end,
+    every row the GPU rounded as the oracle matches the oracle's logit to 1e-5
+    relative, so every larger difference comes from such flips."""
     p = params64()
     net = trk.trk_mlp_create(p)
     X, _ = data(M)
-    got = trk.trk_mlp_forward(net, torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    got_t, hid = trk.trk_mlp_forward_hidden(net, torch.from_numpy(X).cuda())
+    got = got_t.cpu().numpy().astype(np.float64)
+    H = bf16_bits_to_f64(hid)
+    plain = trk.trk_mlp_forward(net, torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    assert np.array_equal(plain, got)
+    h = om.bf16(X.astype(np.float64))
+    flipped_row = np.zeros(M, bool)
+    for l in range(4):
+        W, b = p[l]
+        exact, lo, hi = om.hidden_layer_check(h, W, b)
+        g = H[l]
+        assert np.all((g >= lo) & (g <= hi)), "layer %d: activation outside the admissible BF16 roundings" % l
+        flip = g != exact
+        assert flip.mean() <= 1e-3, (l, flip.mean())
+        flipped_row |= flip.any(axis=1)
+        h = g
+    w5, b5 = p[4]
+    head = h @ om.bf16(w5).reshape(-1) + b5[0]
+    assert np.all(np.abs(got - head) <= om.head_delta(h, w5, head))
     want, _ = om.forward(p, X.astype(np.float64))
     scale = np.maximum(np.abs(want), 0.1 * np.max(np.abs(want)))
     rel = np.abs(got - want) / scale
-    # FP32 (GPU) and FP64 (oracle) sums can round an activation to neighbouring
-    # BF16 values (2^-8 apart); such flips move a few logits by up to ~1e-2.
+    assert np.all(rel[~flipped_row] <= 1e-5)
     assert np.median(rel) <= 1e-5
-    assert np.sum(rel > 1e-3) <= max(3, 0.02 * M)
-    assert np.max(rel) <= 3e-2
 
 
 @pytest.mark.parametrize("M", [1000, 4096])

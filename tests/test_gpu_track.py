@@ -8,7 +8,7 @@ import synthetic as syn
 from oracle import oracle as orc
 from paper_1710_07350_gb300 import trk
 
-from gpu_util import (MARGIN, TOL_100, TOL_PASS, by_id, compare_moments, compare_tracking, gpu_track,
+from gpu_util import (MARGIN, TOL_100, TOL_PASS, by_id, compare_moments, compare_tracking, gpu_track, tol_turns,
                       reduction_check)
 
 pytestmark = pytest.mark.gpu
@@ -149,13 +149,13 @@ def test_edge_cases_empty_single_nan():
     z[2, 2] = 1e-4
     g = gpu_track(lat, z, 2)
     o = orc.track(lat, z, 2)
-    compare_tracking(g, o, TOL_PASS * 100)
+    compare_tracking(g, o, tol_turns(2))
     k = list(g["lost"][0]).index(0)      # the NaN particle is lost at element 0 of turn 0
     assert g["lost"][1][k] == 0 and g["lost"][2][k] == 0
     one = syn.bunch("c1", n=1)
     g = gpu_track(lat, one, 3)
     o = orc.track(lat, one, 3)
-    compare_tracking(g, o, TOL_PASS * 10)
+    compare_tracking(g, o, tol_turns(3))
     compare_moments(g["moments"], o["moments"])
 
 
@@ -267,7 +267,7 @@ def test_sbend_zero_angle_is_the_exact_drift():
     z = syn.bend_ring_bunch(1000, seed=5)
     g = gpu_track(lat, z, 3)
     o = orc.track(lat, z, 3)
-    compare_tracking(g, o, TOL_PASS * 10)
+    compare_tracking(g, o, tol_turns(3))
 
 
 def test_sbend_particles_that_cannot_reach_the_exit_face_are_lost_alike():

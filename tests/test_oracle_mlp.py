@@ -79,3 +79,68 @@ def test_adam_constant_gradient_closed_form():
         p = mlp.adam_step(p, grads, st, lr=1e-3, eps=1e-8)
     assert np.allclose(p[0][0], -7 * 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
     assert np.allclose(p[0][1], -7 * 1e-3 * np.sign([1.0, -1.0]) * (1 / (1 + 1e-8)), rtol=1e-12, atol=0)
+
+
+def _tc_like_layer(h, W, b, chunk=16, bias_scale=1.0):
+    """A float32 evaluation of one hidden layer in the manner of a tensor core:
+    each 16-wide slice of the K products summed exactly and rounded to float32,
+    the slices accumulated one after another in float32, the bias added in
+    float32, GELU in float32, then BF16."""
+    Wb = mlp.bf16(W)
+    K = h.shape[1]
+    acc = np.zeros((h.shape[0], W.shape[0]), np.float32)
+    for k0 in range(0, K, chunk):
+        part = (h[:, k0:k0 + chunk] @ Wb[:, k0:k0 + chunk].T).astype(np.float32)
+        acc = (acc + part).astype(np.float32)
+    z = (acc + np.float32(1.0) * (b * bias_scale).astype(np.float32)).astype(np.float32)
+    c = np.float32(0.70710678118654752)
+    from scipy.special import erf
+    e = erf((z * c).astype(np.float32).astype(np.float64)).astype(np.float32)
+    g = (np.float32(0.5) * z * (np.float32(1.0) + e)).astype(np.float32)
+    return mlp.bf16(g.astype(np.float64))
+
+
+def test_rounding_interval_holds_a_float32_evaluation():
+    """Every activation of a float32 (tensor-core-like) evaluation lies in the
+    oracle's admissible BF16 interval, and the interval is a single BF16 value
+    for all but about 1 % of activations (near-zero activations, whose BF16
+    spacing is below the float32 sum's absolute error, span a few values)."""
+    rng = np.random.default_rng(11)
+    p = [(W.astype(np.float64), rng.normal(0, 0.05, W.shape[0])) for W, _ in syn.mlp_init(7)]
+    X = rng.uniform(-1, 1, size=(3000, 8))
+    h = mlp.bf16(X)
+    for l in range(4):
+        W, b = p[l]
+        ex, lo, hi = mlp.hidden_layer_check(h, W, b)
+        got = _tc_like_layer(h, W, b)
+        assert np.all((got >= lo) & (got <= hi)), l
+        assert np.all(lo <= ex) and np.all(ex <= hi)
+        wide = lo < hi
+        assert wide.mean() < 0.02, wide.mean()
+        # away from zero a wide interval spans exactly two BF16 values
+        big = wide & (np.abs(ex) > 0.05)
+        assert np.all(hi[big] == _bf16_next_up(lo[big]))
+        h = got
+
+
+def _bf16_next_up(x):
+    """The next BF16 value above each BF16 value x (finite, x != -0)."""
+    u = (np.asarray(x, np.float64).astype(np.float32).view(np.uint32) >> 16).astype(np.int64)
+    neg = (u & 0x8000) != 0
+    mag = u & 0x7FFF
+    zero = mag == 0
+    out = np.where(neg, u - 1, u + 1)
+    out = np.where(zero, 1, out)                     # +0 or -0 -> the smallest positive subnormal
+    out = np.where(neg & (mag == 1), 0, out)         # -min -> +0
+    return (out.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_rounding_interval_detects_a_dropped_bias():
+    """The interval is tight enough to catch an evaluation that drops the bias."""
+    rng = np.random.default_rng(12)
+    p = [(W.astype(np.float64), rng.normal(0, 0.05, W.shape[0])) for W, _ in syn.mlp_init(7)]
+    h = mlp.bf16(rng.uniform(-1, 1, size=(500, 8)))
+    W, b = p[0]
+    _, lo, hi = mlp.hidden_layer_check(h, W, b)
+    bad = _tc_like_layer(h, W, b, bias_scale=0.0)
+    assert np.mean((bad < lo) | (bad > hi)) > 0.5
