@@ -56,6 +56,15 @@ struct trk_lattice {
     int max_bins = 0;
     bool transverse = false; // a wake with a transverse part
     uint32_t survival_rows = 0x3Fu;  // map rows a survival scan needs (survival_rows())
+    uint32_t survival_zero = 0u;     // coordinates that stay exactly zero in a survival scan (survival_zeros())
+    // survival view: the elements with map rows limited to survival_rows and
+    // without the terms that have a factor in survival_zero (its own copies when
+    // that removes anything, else the tracking arrays)
+    std::vector<DevElem> selems;
+    std::vector<DevTerm> sterms;
+    DevElem *d_selems = nullptr;
+    DevTerm *d_sterms = nullptr;
+    LatticeView sview{};
 };
 
 struct trk_bunch {
@@ -208,6 +217,90 @@ static uint32_t survival_rows(const trk_lattice &L) {
         if (need == before) break;
     }
     return need & 0x3Fu;
+}
+
+// Coordinates that stay exactly zero in a survival scan, which starts every
+// particle at (x0, 0, y0, 0, 0, 0): the set starts as {x', y', l, delta} and a
+// coordinate leaves it when an element can make it nonzero from coordinates
+// outside the set -- a map row with a term none of whose factors is in the set
+// (a constant term included), a thin sextupole (x', y' from x, y), an exact
+// drift (l from the slopes).  Repeated over the lattice until it stops
+// changing, this is the set that holds at every element of every turn.  A term
+// with a factor in it is exactly zero and adds nothing (at most the sign of a
+// zero sum changes, which no loss decision reads).  Any other element type:
+// nothing is known to stay zero.
+static uint32_t survival_zeros(const trk_lattice &L) {
+    uint32_t zero = 0x3Au;   // x' (1), y' (3), l (4), delta (5)
+    for (int it = 0; it < 8; ++it) {
+        const uint32_t before = zero;
+        for (const DevElem &E : L.elems) {
+            if (E.type == TRK_MAP) {
+                for (int r = 0; r < 6; ++r) {
+                    if (!((zero >> r) & 1u)) continue;
+                    for (int k = E.rb[r]; k < E.rb[r + 1]; ++k) {
+                        const int code = L.terms[E.term0 + k].code;
+                        const int deg = code & 3;
+                        bool has_zero = false;
+                        if (deg >= 1) has_zero |= (zero >> ((code >> 2) & 7)) & 1u;
+                        if (deg >= 2) has_zero |= (zero >> ((code >> 5) & 7)) & 1u;
+                        if (deg >= 3) has_zero |= (zero >> ((code >> 8) & 7)) & 1u;
+                        if (!has_zero) {
+                            zero &= ~(1u << r);
+                            break;
+                        }
+                    }
+                }
+            } else if (E.type == TRK_THINSEXT) {
+                if ((zero & 0x5u) != 0x5u) zero &= ~0xAu;   // x or y nonzero: x', y' may become nonzero
+            } else if (E.type == TRK_EDRIFT) {
+                if ((zero & 0xAu) != 0xAu) zero &= ~0x10u;  // a slope nonzero: l may become nonzero
+            } else {
+                return 0u;
+            }
+        }
+        if (zero == before) break;
+    }
+    return zero;
+}
+
+// The survival view's element and term arrays (host): map rows outside
+// `rows` get no terms, and terms with a factor in `zero` are left out.
+static bool build_survival_terms(const trk_lattice &L, uint32_t rows, uint32_t zero, std::vector<DevElem> &elems,
+                                 std::vector<DevTerm> &terms) {
+    elems = L.elems;
+    terms.clear();
+    bool changed = false;
+    for (size_t i = 0; i < elems.size(); ++i) {
+        DevElem &E = elems[i];
+        if (E.type != TRK_MAP) continue;
+        const DevElem &O = L.elems[i];
+        E.term0 = (int32_t)terms.size();
+        int cnt = 0;
+        for (int r = 0; r < 6; ++r) {
+            E.rb[r] = (int16_t)cnt;
+            if (!((rows >> r) & 1u)) {
+                changed |= O.rb[r + 1] > O.rb[r];
+                continue;
+            }
+            for (int k = O.rb[r]; k < O.rb[r + 1]; ++k) {
+                const DevTerm &t = L.terms[O.term0 + k];
+                const int deg = t.code & 3;
+                bool has_zero = false;
+                if (deg >= 1) has_zero |= (zero >> ((t.code >> 2) & 7)) & 1u;
+                if (deg >= 2) has_zero |= (zero >> ((t.code >> 5) & 7)) & 1u;
+                if (deg >= 3) has_zero |= (zero >> ((t.code >> 8) & 7)) & 1u;
+                if (has_zero) {
+                    changed = true;
+                    continue;
+                }
+                terms.push_back(t);
+                ++cnt;
+            }
+        }
+        E.rb[6] = (int16_t)cnt;
+        E.rb[7] = (int16_t)cnt;
+    }
+    return changed;
 }
 
 extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t n, const trk_lattice_opts *opts,
@@ -387,6 +480,7 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.ap_type = opts->aperture;
     v.row_mask = 0x3Fu;
     L->survival_rows = survival_rows(*L);
+    L->survival_zero = survival_zeros(*L);
     v.ap_a = opts->a;
     v.ap_b = opts->b;
     // |x| <= a as integers: bit patterns of the positive bounds shifted left by one
@@ -399,6 +493,26 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.ap_b_key = key(opts->b);
     v.ap_ia_key = key(0.7 * opts->a);
     v.ap_ib_key = key(0.7 * opts->b);
+    L->sview = v;
+    L->sview.row_mask = L->survival_rows;
+    if (build_survival_terms(*L, L->survival_rows, L->survival_zero, L->selems, L->sterms)) {
+        cudaError_t e5 = dalloc(&L->d_selems, L->selems.size());
+        if (e5 == cudaSuccess) e5 = dalloc(&L->d_sterms, L->sterms.size() ? L->sterms.size() : 1);
+        if (e5 == cudaSuccess)
+            e5 = cudaMemcpy(L->d_selems, L->selems.data(), L->selems.size() * sizeof(DevElem), cudaMemcpyHostToDevice);
+        if (e5 == cudaSuccess && !L->sterms.empty())
+            e5 = cudaMemcpy(L->d_sterms, L->sterms.data(), L->sterms.size() * sizeof(DevTerm), cudaMemcpyHostToDevice);
+        if (e5 != cudaSuccess) {
+            cudaFree(L->d_elems);
+            cudaFree(L->d_terms);
+            cudaFree(L->d_selems);
+            cudaFree(L->d_sterms);
+            delete L;
+            return fail(TRK_ENOMEM, "trk_create_lattice: survival view allocation failed");
+        }
+        L->sview.elems = L->d_selems;
+        L->sview.terms = L->d_sterms;
+    }
     *out = L;
     return TRK_OK;
 }
@@ -407,6 +521,8 @@ extern "C" trk_status trk_destroy_lattice(trk_lattice *L) {
     if (!L) return TRK_OK;
     cudaFree(L->d_elems);
     cudaFree(L->d_terms);
+    cudaFree(L->d_selems);
+    cudaFree(L->d_sterms);
     delete L;
     return TRK_OK;
 }
@@ -619,7 +735,7 @@ static TrackArgs base_args(trk_bunch *b, const trk_lattice *L, int n_tiles) {
     a.loss_turn = b->lt;
     a.loss_elem = b->le;
     a.st = b->st;
-    a.win = reinterpret_cast<unsigned long long *>(b->st->lkey);
+    a.win = &b->st->win;
     a.lat = L->view;
     a.n_tiles = n_tiles;
     a.partials = b->partials;
@@ -690,6 +806,7 @@ static trk_status track_parts(trk_bunch *const *P, int np, const trk_lattice *L,
                 a.local_turn0 = 0;
                 a.do_moments = L->moments;
                 a.p0c = b->p0c;
+                a.ip0c = 1.0 / a.p0c;
                 TRK_CUDA(track_launch(b, a, n_tiles));
                 for (int t = 0; t < nt; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
                 if (L->moments) {
@@ -721,21 +838,21 @@ static trk_status track_parts(trk_bunch *const *P, int np, const trk_lattice *L,
         if (s != TRK_OK) return s;
     }
     const double qm_base = 1.0 / (double)n_total;
-    unsigned long long *win = reinterpret_cast<unsigned long long *>(lead->st->lkey);
+    WakeWindow *win = &lead->st->win;
     const int ng = (int)L->groups.size();
     const auto transverse = [&](int e) {
         return e >= 0 && L->elems[e].type == TRK_WAKE && L->elems[e].p[3] != 0.0;
     };
     // histogram (over every part) and field of collective element e on the
     // window of `slot`, voltages into V (and the transverse ones into Vt)
-    const auto collective = [&](int e, int slot, double p0, double *V, double *Vt) -> trk_status {
+    const auto collective = [&](int e, int slot, int which, double p0, double *V, double *Vt) -> trk_status {
         const DevElem &W = L->elems[e];
         const bool lsc = W.type == TRK_LSC;
         const bool tr = transverse(e);
         for (int k = 0; k < np; ++k) {
             trk_bunch *b = P[k];
             if (b->n == 0) continue;
-            TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, win, slot, W.n, lsc ? 0.0 : W.p[0],
+            TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, win, slot, which, W.n, lsc ? 0.0 : W.p[0],
                                       lsc ? 1.0 : W.p[1], lead->hist, lead->wfun, lsc ? 0.0 : W.p[3],
                                       tr ? lead->dip : nullptr, lead->wfun_t, b->n, lead->stream));
             ++b->launches;
@@ -796,18 +913,19 @@ static trk_status track_parts(trk_bunch *const *P, int np, const trk_lattice *L,
                     g.minmax_slot = s < ng ? slot : -1;
                     g.do_moments = L->moments && s == ng;
                     g.p0c = p0;
+                    g.ip0c = 1.0 / p0;
                     TRK_CUDA(track_launch(b, g, n_tiles[k]));
                 }
                 p0 = advance_p0(L, e_start, e_first, p0);
                 if (s < ng) {
-                    trk_status st = collective(e_first, slot, p0, lead->V, lead->Vt);
+                    trk_status st = collective(e_first, slot, 0, p0, lead->V, lead->Vt);
                     if (st != TRK_OK) return st;
                     if (e_second >= 0) {   // same particles, same l: the window of `slot` stands
                         TRK_CUDA(launch_wake_reset(lead->st, slot, lead->hist,
                                                    transverse(e_second) ? lead->dip : nullptr,
                                                    L->elems[e_second].n, false, lead->stream));
                         ++lead->launches;
-                        st = collective(e_second, slot, p0, lead->V2, lead->Vt2);
+                        st = collective(e_second, slot, 1, p0, lead->V2, lead->Vt2);
                         if (st != TRK_OK) return st;
                     }
                 }
@@ -906,8 +1024,8 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     if (s != TRK_OK) return s;
     TRK_CUDA(launch_wake_reset(b->st, 0, b->hist, nullptr, nbins, true, b->stream));
     TRK_CUDA(launch_wake_minmax(b->coords, b->pitch, b->lt, b->st, 0, b->n, b->stream));
-    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, reinterpret_cast<const unsigned long long *>(b->st->lkey),
-                              0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
+    TRK_CUDA(launch_wake_hist(b->coords, b->pitch, b->lt, b->st, &b->st->win,
+                              0, 0, nbins, w0, sc, b->hist, b->wfun, 0.0, nullptr,
                               nullptr, b->n, b->stream));
     TRK_CUDA(launch_wake_conv(b->hist, b->wfun, nbins, charge / (double)b->n, b->V, b->stream));
     const int tile = b->block * b->per_thread;
@@ -919,7 +1037,7 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     a.loss_turn = b->lt;
     a.loss_elem = b->le;
     a.st = b->st;
-    a.win = reinterpret_cast<unsigned long long *>(b->st->lkey);   // the window the kick reads
+    a.win = &b->st->win;   // the window the kick reads
     a.lat.ap_type = TRK_APERTURE_NONE;
     a.e0 = a.e1 = 0;
     a.n_turns = 1;
@@ -929,6 +1047,7 @@ extern "C" trk_status trk_wake(trk_bunch *b, int32_t nbins, double w0, double sc
     a.kick_slot = 0;
     a.minmax_slot = -1;
     a.p0c = p0c_ev;
+    a.ip0c = 1.0 / p0c_ev;
     a.wake_V = b->V;
     a.wake_nbins = nbins;
     TRK_CUDA(track_launch(b, a, n_tiles));
@@ -1116,7 +1235,7 @@ extern "C" trk_status trk_batch_track(trk_batch *B, int32_t n_turns) {
         int t0 = 0;
         for (int c = 0; c < nc; ++c) {
             TrackArgs a = base_args(b, L, nt);
-            if (B->survival_only) a.lat.row_mask = L->survival_rows;
+            if (B->survival_only) a.lat = L->sview;
             a.e0 = 0;
             a.e1 = ne;
             a.n_turns = chunks[c];
@@ -1124,6 +1243,7 @@ extern "C" trk_status trk_batch_track(trk_batch *B, int32_t n_turns) {
             a.local_turn0 = 0;
             a.do_moments = L->moments;
             a.p0c = b->p0c;
+            a.ip0c = 1.0 / a.p0c;
             a.mom_out = b->moments ? b->moments + (size_t)t0 * kMomentsN : nullptr;
             B->h_args[(size_t)v * nc + c] = a;
             for (int t = 0; t < chunks[c]; ++t) b->p0c = advance_p0(L, 0, ne, b->p0c);
@@ -1210,8 +1330,7 @@ extern "C" trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int3
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<LatticeView> hv(n_var);
     for (int v = 0; v < n_var; ++v) {
-        hv[v] = lats[v]->view;
-        hv[v].row_mask = lats[v]->survival_rows;
+        hv[v] = lats[v]->sview;
     }
     LatticeView *dv = nullptr;
     int64_t *doff = nullptr;

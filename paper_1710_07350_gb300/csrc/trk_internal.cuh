@@ -63,11 +63,22 @@ struct LatticeView {
     unsigned long long ap_ia_key, ap_ib_key; // the same of 0.7 a, 0.7 b: inner box of the ellipse
 };
 
+// The l window of the collective elements, two slots: order keys of the l
+// min/max ([2s] min, [2s+1] max) and, for the j-th collective element (0 or 1)
+// of the group on slot s, 1/dl of its histogram at [2s + j] (0 for an empty or
+// zero-width window): the histogram pass writes it once so that the kick does
+// not divide in every thread.  Two adjacent elements share the window but may
+// have different bin counts, hence one value each.
+struct WakeWindow {
+    uint64_t key[4];
+    double idl[4];
+};
+
 // Device-resident bunch state.
 struct BunchState {
     int64_t n_alive;        // alive particles occupy [0, n_alive)
     int64_t n_alive_next;   // result of the pending compaction
-    uint64_t lkey[4];       // l min/max order keys, two wake slots: [2s] min, [2s+1] max
+    WakeWindow win;
     int32_t error;
     int32_t pad;
 };
@@ -79,8 +90,8 @@ struct TrackArgs {
     int32_t *loss_turn;     // -1 = alive
     int32_t *loss_elem;
     BunchState *st;
-    unsigned long long *win;  // l-window keys of the collective elements ([2s] min, [2s+1] max): st->lkey,
-                              // or the first part's for a bunch held in several parts
+    WakeWindow *win;          // l window of the collective elements: &st->win, or the first part's
+                              // for a bunch held in several parts
     LatticeView lat;
     int32_t e0, e1;
     int32_t n_turns;        // > 1 only when [e0, e1) is the whole lattice
@@ -93,6 +104,7 @@ struct TrackArgs {
     int32_t do_moments;     // per-turn moments at the end of each turn
     int32_t n_tiles;        // stride of the partial-sum rows
     double p0c;             // reference momentum at element e0 [eV]
+    double ip0c;            // 1 / p0c (computed on the host)
     double *partials;       // [turn][tile][28]
     int32_t *tile_alive;    // alive count per tile at the end (may be null)
     const double *wake_V;   // voltages of the kicking wake
@@ -139,7 +151,7 @@ cudaError_t launch_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned
 cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_t *lt, BunchState *st,
                                int slot, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, const BunchState *st,
-                             const unsigned long long *win, int slot, int nbins,
+                             WakeWindow *win, int slot, int which, int nbins,
                              double w0, double sc, uint32_t *hist, double *wfun, double w0t, unsigned long long *dip,
                              double *wfun_t, int64_t n_max, cudaStream_t s);
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
@@ -169,6 +181,21 @@ cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, 
                               int64_t n_tiles, uint16_t *out_tiled, int *d_err, cudaStream_t s);
 cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s);
 cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, cudaStream_t s);
+// Training products on tcgen05 (trk_mlp_umma.cu): one 128 x 64 output tile per CTA.
+cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_tiled, const float *bias,
+                             int64_t m_pad, float *Z, uint16_t *Hout_tiled, uint16_t *Hout_T, uint16_t *Hout_rm,
+                             int *d_err, cudaStream_t s);
+cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled, const float *Zin, int64_t m_pad,
+                            float *dz, uint16_t *dzb_out_tiled, uint16_t *dzb_out_T, int *d_err, cudaStream_t s);
+int train_dw_splits(int64_t m_pad);
+cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in, int64_t m_pad, float *part,
+                            int *d_err, cudaStream_t s);
+cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T, cudaStream_t s);
+cudaError_t launch_train_head_back(const float *logit, const float *y, int64_t M, int64_t m_pad, const uint16_t *w5,
+                                   const float *Z4, float *dl, float *dz, uint16_t *dzb, uint16_t *dzbT,
+                                   float *loss_terms, cudaStream_t s);
+cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const size_t *wt_off, const size_t *wtT_off,
+                                  const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s);
 cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s);
 cudaError_t launch_head_tiled(const uint16_t *H4, const uint16_t *w5, const float *b5, int64_t M, float *logit,
                               cudaStream_t s);

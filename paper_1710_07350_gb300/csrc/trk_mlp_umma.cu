@@ -242,6 +242,292 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     if (threadIdx.x == 0 && S.abort) atomicExch(err, 1);
 }
 
+// ------------------------------------------------------------ training ----
+// One 128 x 64 output tile per CTA of D = A B^T, A [128 rows x K] and B [64
+// rows x K] both K-major in the tiled layout above: chunk c of A's tile t is
+// the 16 KB block ((t * a_kc + c) * 128 * 64) elements in, and the 64-row slice
+// j of B's chunk c the contiguous 8 KB at ((c * b_rows + 64 j) * 64) (a 64-row
+// slice of a block covers 8 whole row groups).  The chunks [k0, k1) are copied
+// to shared memory in groups of up to kGroupChunks (one mbarrier each group),
+// one thread issues the MMAs (M 128, N 64, K 16) into a 64-column TMEM
+// accumulator, and after the last commit the four warps read their TMEM lane
+// quadrant and apply the epilogue:
+//   kTrainFwd  z = acc + bias -> Z [M][256] FP32; h = bf16(gelu(z)) tiled (next
+//              layer's A, 128-row tiles, K 256), transposed-tiled (rows = the
+//              256 outputs, K = the batch: the weight gradient's B) and, when
+//              Hrm is given, row-major [M][256]
+//   kTrainDx   v = acc * gelu'(Zin[m][n]) -> dz FP32 [M][256], bf16(v) tiled and
+//              transposed-tiled with 128-row tiles (the next weight gradient's A)
+//   kTrainDw   acc -> part [z][256][b_n] FP32 (split z = blockIdx.z of the
+//              contraction over the batch; the caller sums the splits in order)
+// Rows m >= M of the batch keep the zeros of padded inputs.
+enum { kTrainFwd = 0, kTrainDx = 1, kTrainDw = 2 };
+constexpr int TN = 64, kGroupChunks = 8;
+constexpr uint32_t kBSliceBytes = TN * KCH * 2;     // 8 KB
+constexpr uint32_t kIdesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+
+struct TrainTileArgs {
+    const __nv_bfloat16 *A;
+    int64_t a_kc;            // chunks per A tile
+    const __nv_bfloat16 *B;
+    int b_rows;              // rows of B's tile (256 or 64)
+    int kc;                  // chunks of the contraction; a CTA takes [z * cps, min(kc, (z + 1) * cps))
+    int cps;
+    const float *bias;       // fwd
+    const float *Zin;        // dx: pre-activations of the layer below, [M][256]
+    float *Zout;             // fwd: [M][256]; dx: dz [M][256]
+    __nv_bfloat16 *Ht;       // fwd / dx: tiled output (128-row tiles, K 256)
+    __nv_bfloat16 *HtT;      // fwd / dx: transposed-tiled output
+    __nv_bfloat16 *Hrm;      // fwd: optional row-major output
+    int tt_rows;             // rows of HtT's tiles (256 fwd, 128 dx)
+    int64_t m_kc;            // batch chunks (m_pad / 64) of the transposed layouts
+    float *part;             // dw
+    int *err;
+};
+
+__device__ __forceinline__ float gelu_grad_u(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Element (r, k) of a matrix in the tiled layout with tr-row tiles and kcn chunks per tile.
+__device__ __forceinline__ size_t tiled_at(int64_t r, int64_t k, int tr, int64_t kcn) {
+    return ((size_t)((r / tr) * kcn + (k >> 6)) * (tr >> 3) + (size_t)((r % tr) >> 3)) * 512 + (size_t)((k & 63) >> 3) * 64 +
+           (size_t)(r & 7) * 8 + (size_t)(k & 7);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sA = base;
+    unsigned char *sB = sA + (size_t)kGroupChunks * kABlockBytes;
+    __shared__ uint64_t full, done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = blockIdx.x;              // A tile (batch rows, or output rows for dw)
+    const int j = blockIdx.y;                  // 64-column slice of the output
+    const int z = blockIdx.z;
+    const int c_beg = z * a.cps, c_end = (z + 1) * a.cps < a.kc ? (z + 1) * a.cps : a.kc;
+    if (threadIdx.x == 0) {
+        mbar_init(&full, 1);
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(su32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    volatile int *abort = &abort_flag;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int g0 = c_beg; g0 < c_end && ok; g0 += kGroupChunks, phase ^= 1u) {
+        const int g1 = g0 + kGroupChunks < c_end ? g0 + kGroupChunks : c_end;
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&full, (uint32_t)(g1 - g0) * (kABlockBytes + kBSliceBytes));
+            for (int c = g0; c < g1; ++c) {
+                bulk_g2s(sA + (size_t)(c - g0) * kABlockBytes, a.A + ((size_t)t * a.a_kc + c) * (kABlockBytes / 2),
+                         kABlockBytes, &full);
+                bulk_g2s(sB + (size_t)(c - g0) * kBSliceBytes,
+                         a.B + ((size_t)c * a.b_rows + (size_t)j * TN) * KCH, kBSliceBytes, &full);
+            }
+            ok = mbar_wait(&full, phase, abort);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) {
+                for (int c = g0; c < g1; ++c) {
+                    const uint32_t a0 = su32(sA + (size_t)(c - g0) * kABlockBytes);
+                    const uint32_t b0 = su32(sB + (size_t)(c - g0) * kBSliceBytes);
+#pragma unroll
+                    for (int kk = 0; kk < KCH / 16; ++kk) {
+                        const uint32_t acc = (c != c_beg || kk != 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                            "l"(sdesc(a0 + kk * 256)), "l"(sdesc(b0 + kk * 256)), "r"(kIdesc64), "r"(acc)
+                            : "memory");
+                    }
+                }
+            }
+            // the next group overwrites the stages: wait until these MMAs have read them
+            umma_commit(&done);
+            ok = mbar_wait(&done, phase, abort) && ok;
+        }
+        __syncthreads();
+        ok = !*abort;
+    }
+    // a group that gave up waiting may still have copies in flight: one more
+    // bounded wait for them before the CTA leaves
+    if (!ok && threadIdx.x == 0) {
+        volatile int never = 0;
+        mbar_wait(&full, phase ^ 1u, &never);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && c_beg < c_end) {
+        const int row = warp * 32 + lane;   // TMEM lane = row of the tile
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                  "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                  "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int n0 = j * TN + c0;     // first output column of these 32
+            if (MODE == kTrainDw) {
+                // part [z][out row][in column], in columns = b_n = gridDim.y * 64
+                const size_t ncol = (size_t)gridDim.y * TN;
+                float4 *dst = reinterpret_cast<float4 *>(a.part + ((size_t)z * 256 + (size_t)t * UM + row) * ncol + n0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            } else {
+                const int64_t m = t * UM + row;   // batch row
+                float v[32];
+                if (MODE == kTrainFwd) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r[e]) + a.bias[n0 + e];
+                } else {
+                    const float4 *zin = reinterpret_cast<const float4 *>(a.Zin + (size_t)m * 256 + n0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 zz = zin[q];
+                        v[4 * q] = __uint_as_float(r[4 * q]) * gelu_grad_u(zz.x);
+                        v[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * gelu_grad_u(zz.y);
+                        v[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * gelu_grad_u(zz.z);
+                        v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * gelu_grad_u(zz.w);
+                    }
+                }
+                float4 *zo = reinterpret_cast<float4 *>(a.Zout + (size_t)m * 256 + n0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) zo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                // the BF16 values: bf16(gelu(z)) forward, bf16(dz) backward
+                uint32_t hv[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    hv[e] = MODE == kTrainFwd ? pack_bf16(gelu_u(v[2 * e]), gelu_u(v[2 * e + 1]))
+                                              : pack_bf16(v[2 * e], v[2 * e + 1]);
+                // tiled (128-row tiles, K 256): four 16-byte pieces of 8 columns
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(a.Ht + tiled_at(m, n0 + 8 * g, UM, 4)) =
+                        make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
+                if (MODE == kTrainFwd && a.Hrm) {
+                    uint4 *hr = reinterpret_cast<uint4 *>(a.Hrm + (size_t)m * 256 + n0);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) hr[g] = make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
+                }
+                // transposed-tiled: element (n, m)
+                const uint16_t *h16 = reinterpret_cast<const uint16_t *>(hv);
+                uint16_t *tt = reinterpret_cast<uint16_t *>(a.HtT);
+#pragma unroll 8
+                for (int e = 0; e < 32; ++e) tt[tiled_at(n0 + e, m, a.tt_rows, a.m_kc)] = h16[e];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicExch(a.err, 1);
+}
+
+// Training inputs: x [M][8] FP32 -> h0 tiled (128-row tiles, K 64) and
+// transposed-tiled (one 64-row tile: the 64 padded features, K = the batch);
+// features 8..63 and rows >= M are zero.
+__global__ void k_train_input(const float *__restrict__ X, int64_t M, int64_t m_pad, __nv_bfloat16 *__restrict__ H0,
+                              __nv_bfloat16 *__restrict__ H0T) {
+    const int64_t n = m_pad * 64;
+    uint16_t *t = reinterpret_cast<uint16_t *>(H0T);
+    uint16_t *h = reinterpret_cast<uint16_t *>(H0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i >> 6;
+        const int f = (int)(i & 63);
+        const float v = (m < M && f < 8) ? X[m * 8 + f] : 0.0f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        const uint16_t u = *reinterpret_cast<const uint16_t *>(&b);
+        h[tiled_at(m, f, UM, 1)] = u;
+        t[tiled_at(f, m, 64, m_pad / 64)] = u;
+    }
+}
+
+// Head backward for the training step: dlogit = (sigmoid(logit) - y) / M and the
+// BCE terms (rows < M), dz4 = dlogit w5 gelu'(z4) -> FP32 [m_pad][256], BF16
+// tiled (128-row tiles, K 256) and transposed-tiled (128-row tiles over the 256
+// outputs, K = the batch); rows >= M are zero.
+__global__ void k_train_head_back(const float *__restrict__ logit, const float *__restrict__ y, int64_t M, int64_t m_pad,
+                                  const __nv_bfloat16 *__restrict__ w5, const float *__restrict__ Z4,
+                                  float *__restrict__ dl, float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
+                                  __nv_bfloat16 *__restrict__ dzbT, float *__restrict__ loss_terms) {
+    const int64_t n = m_pad * 256;
+    uint16_t *a = reinterpret_cast<uint16_t *>(dzb);
+    uint16_t *b = reinterpret_cast<uint16_t *>(dzbT);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i >> 8;
+        const int k = (int)(i & 255);
+        float d = 0.0f;
+        if (m < M) {
+            const float l = logit[m];
+            d = (1.0f / (1.0f + expf(-l)) - y[m]) / (float)M;
+            if (k == 0) {
+                dl[m] = d;
+                loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - y[m] * l;
+            }
+        }
+        const float v = m < M ? d * __bfloat162float(w5[k]) * gelu_grad_u(Z4[i]) : 0.0f;
+        dz[i] = v;
+        const __nv_bfloat16 vb = __float2bfloat16_rn(v);
+        const uint16_t u = *reinterpret_cast<const uint16_t *>(&vb);
+        a[tiled_at(m, k, UM, 4)] = u;
+        b[tiled_at(k, m, UM, m_pad / 64)] = u;
+    }
+}
+
+// BF16 weights [out][in_pad] of the four hidden layers (at w_off[l] in pb) ->
+// the tiled copies the products read: wt[l] (256-row tile over the outputs,
+// K = in_pad) and, for l >= 1, wtT[l] = W_l^T (256-row tile over the inputs, K 256).
+struct RetileArgs {
+    const __nv_bfloat16 *pb;
+    size_t w_off[4], wt_off[4], wtT_off[4];
+    int in_pad[4];
+    __nv_bfloat16 *wt, *wtT;
+};
+__global__ void k_retile_weights(RetileArgs r) {
+    const int64_t per1 = 256 * 64, per = 256 * 256;
+    const int64_t n = per1 + 3 * per;
+    const uint16_t *src = reinterpret_cast<const uint16_t *>(r.pb);
+    uint16_t *wt = reinterpret_cast<uint16_t *>(r.wt), *wtT = reinterpret_cast<uint16_t *>(r.wtT);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int l;
+        int64_t e;
+        if (i < per1) {
+            l = 0;
+            e = i;
+        } else {
+            l = 1 + (int)((i - per1) / per);
+            e = (i - per1) % per;
+        }
+        const int K = r.in_pad[l];
+        const int64_t o = e / K, k = e % K;
+        const uint16_t v = src[r.w_off[l] + e];
+        wt[r.wt_off[l] + tiled_at(o, k, 256, K / 64)] = v;
+        if (l >= 1) wtT[r.wtT_off[l] + tiled_at(k, o, 256, 4)] = v;
+    }
+}
+
 // Row-major [rows][K] (K a multiple of 64) -> tiled blocks of `tile_rows` rows.
 __global__ void k_to_tiled(const __nv_bfloat16 *__restrict__ src, int64_t rows, int K, int tile_rows,
                            __nv_bfloat16 *__restrict__ dst) {
@@ -356,6 +642,119 @@ cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, 
 
 cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s) {
     k_input_tiled<<<grid_for(m_pad * 8), 256, 0, s>>>(X, M, m_pad, reinterpret_cast<__nv_bfloat16 *>(H0));
+    return cudaGetLastError();
+}
+
+size_t train_tile_smem(int chunks_per_cta) {
+    const int g = chunks_per_cta < kGroupChunks ? chunks_per_cta : kGroupChunks;
+    return 1024 + (size_t)kGroupChunks * kABlockBytes + (size_t)g * kBSliceBytes;
+}
+
+cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_tiled, const float *bias,
+                             int64_t m_pad, float *Z, uint16_t *Hout_tiled, uint16_t *Hout_T, uint16_t *Hout_rm,
+                             int *d_err, cudaStream_t s) {
+    if (K % KCH || K < KCH || K > 256 || m_pad % UM) return cudaErrorInvalidValue;
+    TrainTileArgs a{};
+    a.A = reinterpret_cast<const __nv_bfloat16 *>(H_tiled);
+    a.a_kc = K / KCH;
+    a.B = reinterpret_cast<const __nv_bfloat16 *>(W_tiled);
+    a.b_rows = 256;
+    a.kc = K / KCH;
+    a.cps = a.kc;
+    a.bias = bias;
+    a.Zout = Z;
+    a.Ht = reinterpret_cast<__nv_bfloat16 *>(Hout_tiled);
+    a.HtT = reinterpret_cast<__nv_bfloat16 *>(Hout_T);
+    a.Hrm = reinterpret_cast<__nv_bfloat16 *>(Hout_rm);
+    a.tt_rows = 256;
+    a.m_kc = m_pad / KCH;
+    a.err = d_err;
+    const size_t smem = train_tile_smem(a.cps);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_train_tile<kTrainFwd><<<dim3((unsigned)(m_pad / UM), 256 / TN, 1), 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled, const float *Zin, int64_t m_pad,
+                            float *dz, uint16_t *dzb_out_tiled, uint16_t *dzb_out_T, int *d_err, cudaStream_t s) {
+    if (m_pad % UM) return cudaErrorInvalidValue;
+    TrainTileArgs a{};
+    a.A = reinterpret_cast<const __nv_bfloat16 *>(dzb_tiled);
+    a.a_kc = 4;
+    a.B = reinterpret_cast<const __nv_bfloat16 *>(WT_tiled);
+    a.b_rows = 256;
+    a.kc = 4;
+    a.cps = 4;
+    a.Zin = Zin;
+    a.Zout = dz;
+    a.Ht = reinterpret_cast<__nv_bfloat16 *>(dzb_out_tiled);
+    a.HtT = reinterpret_cast<__nv_bfloat16 *>(dzb_out_T);
+    a.tt_rows = UM;
+    a.m_kc = m_pad / KCH;
+    a.err = d_err;
+    const size_t smem = train_tile_smem(a.cps);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_train_tile<kTrainDx><<<dim3((unsigned)(m_pad / UM), 256 / TN, 1), 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int train_dw_splits(int64_t m_pad) {
+    const int kc = (int)(m_pad / KCH);
+    int S = (kc + kGroupChunks - 1) / kGroupChunks;   // one group of chunks per CTA
+    return S < 1 ? 1 : S;
+}
+
+cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in, int64_t m_pad, float *part,
+                            int *d_err, cudaStream_t s) {
+    if (m_pad % UM || n_in % TN || n_in < TN || n_in > 256) return cudaErrorInvalidValue;
+    TrainTileArgs a{};
+    a.A = reinterpret_cast<const __nv_bfloat16 *>(dzb_T);
+    a.a_kc = m_pad / KCH;
+    a.B = reinterpret_cast<const __nv_bfloat16 *>(H_T);
+    a.b_rows = n_in;
+    a.kc = (int)(m_pad / KCH);
+    const int S = train_dw_splits(m_pad);
+    a.cps = (a.kc + S - 1) / S;
+    a.part = part;
+    a.err = d_err;
+    const size_t smem = train_tile_smem(a.cps);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_train_tile<kTrainDw><<<dim3(256 / UM, (unsigned)(n_in / TN), (unsigned)S), 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T, cudaStream_t s) {
+    k_train_input<<<grid_for(m_pad * 64), 256, 0, s>>>(X, M, m_pad, reinterpret_cast<__nv_bfloat16 *>(H0),
+                                                      reinterpret_cast<__nv_bfloat16 *>(H0T));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_head_back(const float *logit, const float *y, int64_t M, int64_t m_pad, const uint16_t *w5,
+                                   const float *Z4, float *dl, float *dz, uint16_t *dzb, uint16_t *dzbT,
+                                   float *loss_terms, cudaStream_t s) {
+    k_train_head_back<<<grid_for(m_pad * 256), 256, 0, s>>>(logit, y, M, m_pad,
+                                                           reinterpret_cast<const __nv_bfloat16 *>(w5), Z4, dl, dz,
+                                                           reinterpret_cast<__nv_bfloat16 *>(dzb),
+                                                           reinterpret_cast<__nv_bfloat16 *>(dzbT), loss_terms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const size_t *wt_off, const size_t *wtT_off,
+                                  const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s) {
+    RetileArgs r;
+    r.pb = reinterpret_cast<const __nv_bfloat16 *>(pb);
+    for (int l = 0; l < 4; ++l) {
+        r.w_off[l] = w_off[l];
+        r.wt_off[l] = wt_off[l];
+        r.wtT_off[l] = wtT_off[l];
+        r.in_pad[l] = in_pad[l];
+    }
+    r.wt = reinterpret_cast<__nv_bfloat16 *>(wt);
+    r.wtT = reinterpret_cast<__nv_bfloat16 *>(wtT);
+    k_retile_weights<<<grid_for(256 * 64 + 3 * 256 * 256), 256, 0, s>>>(r);
     return cudaGetLastError();
 }
 

@@ -371,11 +371,13 @@ __device__ __noinline__ double rf_cos_exact(double phi, double x) { return cos(p
 // rounding of the result, so this is cos(phi + x) to FP64 rounding at about
 // half the instructions of a general cosine.  The test is an integer compare
 // of |x|'s high word (2^-4 = 0x3FB00000; NaN fails it).
-__device__ __forceinline__ double rf_cos(double cphi, double sphi, double phi, double x) {
-    const double x2 = x * x;
+// z0 is a run-time +0: the products are written fma(a, b, z0), rounded as a * b
+// but issued at the DFMA rate (as in the maps).
+__device__ __forceinline__ double rf_cos(double cphi, double sphi, double phi, double x, double z0) {
+    const double x2 = fma(x, x, z0);
     const double C = fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
-    const double S = x * fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
-    double c = fma(cphi, C, -sphi * S);
+    const double S = fma(x, fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0), z0);
+    double c = fma(cphi, C, fma(-sphi, S, z0));
     if ((__double2hiint(x) & 0x7fffffff) >= 0x3FB00000) c = rf_cos_exact(phi, x);
     return c;
 }
@@ -387,13 +389,14 @@ __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E
                                        bool &dirty) {
     const double V = __ldg(&E->p[0]), phi = __ldg(&E->p[1]), k = __ldg(&E->p[2]);
     const double cphi = __ldg(&E->p[4]), sphi = __ldg(&E->p[5]);
+    const double z0 = V * 0.0;   // run-time +0 (see rf_cos)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double Pp = (1.0 + q.d[p]) * p0;
-        const double P1 = fma(V, rf_cos(cphi, sphi, phi, k * q.l[p]), Pp);
+        const double Pp = fma(fma(q.d[p], 1.0, 1.0), p0, z0);   // (1 + delta) p0, each step rounded as written
+        const double P1 = fma(V, rf_cos(cphi, sphi, phi, fma(k, q.l[p], z0), z0), Pp);
         const double s = Pp / P1;
-        q.xp[p] *= s;
-        q.yp[p] *= s;
+        q.xp[p] = fma(q.xp[p], s, z0);
+        q.yp[p] = fma(q.yp[p], s, z0);
         q.d[p] = fma(P1, ip01, -1.0);
     }
     dirty = true;
@@ -403,14 +406,15 @@ __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E
 __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, bool flat,
                                             const double *__restrict__ V, int nb) {
     if (flat) return __ldg(V);
-    const double u = fma(l - lmin, idl, -0.5);
+    // the differences as fma(a, +-1, b): one rounding, the same as a - b, at the DFMA rate
+    const double u = fma(fma(lmin, -1.0, l), idl, -0.5);
     const double k0 = floor(u);
     if (!(k0 >= 0.0)) return __ldg(V);
     if (k0 >= (double)(nb - 1)) return __ldg(V + nb - 1);
     const int k = (int)k0;
-    const double f = u - k0;
+    const double f = fma(k0, -1.0, u);
     const double v0 = __ldg(V + k), v1 = __ldg(V + k + 1);
-    return fma(f, v1 - v0, v0);
+    return fma(f, fma(v0, -1.0, v1), v0);
 }
 
 // -------------------------------------------------------- block sums ----
@@ -523,18 +527,17 @@ __device__ __forceinline__ void store_particle(const TrackArgs &a, int64_t i, co
     a.coords[5 * a.pitch + i] = q.d[p];
 }
 
-// Kick of one collective element on the window of key slot a.kick_slot: the
-// transverse slope kicks first (V_x / P, V_y / P with P = p0 (1 + delta)), then
-// the energy kick delta += V(l) / p0.
+// Kick of collective element `which` (0 or 1) of the group on key slot
+// a.kick_slot: the transverse slope kicks first (V_x / P, V_y / P with
+// P = p0 (1 + delta)), then the energy kick delta += V(l) / p0.
 template <int P>
 __device__ __forceinline__ void wake_kick(const TrackArgs &a, Tile<P> &q, const bool (&alive)[P], double p0,
-                                          const double *V, const double *Vx, int nbins) {
-    const uint64_t kmin = a.win[2 * a.kick_slot], kmax = a.win[2 * a.kick_slot + 1];
-    const double lmin = dkey_inv(kmin), lmax = dkey_inv(kmax);
-    const double dl = (lmax - lmin) / nbins;
-    const bool flat = !(dl > 0.0);
-    const double idl = flat ? 0.0 : 1.0 / dl;
-    const double ip0 = 1.0 / p0;
+                                          const double *V, const double *Vx, int nbins, int which) {
+    const uint64_t kmin = a.win->key[2 * a.kick_slot];
+    const double lmin = dkey_inv(kmin);
+    const double idl = a.win->idl[2 * a.kick_slot + which];   // 1/dl from the histogram pass, 0 when flat
+    const bool flat = !(idl > 0.0);
+    const double ip0 = a.ip0c;
     if (Vx) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -634,11 +637,11 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
         if (a.kick_wake >= 0) {
             // Kicks of the collective element(s) that precede this segment, in
             // lattice order, each followed by the aperture test.
-            wake_kick<P>(a, q, alive, p0, a.wake_V, a.wake_Vx, a.wake_nbins);
+            wake_kick<P>(a, q, alive, p0, a.wake_V, a.wake_Vx, a.wake_nbins, 0);
             dirty = true;
             apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake, lost_here, canon);
             if (a.kick_wake2 >= 0) {
-                wake_kick<P>(a, q, alive, p0, a.wake_V2, a.wake_Vx2, a.wake_nbins2);
+                wake_kick<P>(a, q, alive, p0, a.wake_V2, a.wake_Vx2, a.wake_nbins2, 1);
                 apply_aperture<P>(a, L, q, alive, base, turn, a.kick_wake2, lost_here, canon);
             }
         }
@@ -713,8 +716,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicMin(&a.win[2 * a.minmax_slot], mm[0]);
-            atomicMax(&a.win[2 * a.minmax_slot + 1], mm[1]);
+            atomicMin((unsigned long long *)&a.win->key[2 * a.minmax_slot], mm[0]);
+            atomicMax((unsigned long long *)&a.win->key[2 * a.minmax_slot + 1], mm[1]);
         }
     }
 
@@ -980,8 +983,8 @@ __global__ void k_init_bunch(BunchState *st, int32_t *lt, int32_t *le, int64_t n
         st->n_alive_next = n;
         st->error = 0;
         for (int s = 0; s < 2; ++s) {
-            st->lkey[2 * s] = ~0ull;
-            st->lkey[2 * s + 1] = 0ull;
+            st->win.key[2 * s] = ~0ull;
+            st->win.key[2 * s + 1] = 0ull;
         }
     }
 }

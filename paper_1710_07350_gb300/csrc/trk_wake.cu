@@ -35,8 +35,8 @@ __global__ void k_wake_reset(BunchState *st, int slot, uint32_t *hist, unsigned 
         if (dip) dip[i] = dip[nbins + i] = 0ull;
     }
     if (reset_keys && blockIdx.x == 0 && threadIdx.x == 0) {
-        st->lkey[2 * slot] = ~0ull;
-        st->lkey[2 * slot + 1] = 0ull;
+        st->win.key[2 * slot] = ~0ull;
+        st->win.key[2 * slot + 1] = 0ull;
     }
 }
 
@@ -69,8 +69,8 @@ __global__ void k_wake_minmax(const double *__restrict__ coords, int64_t pitch, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicMin((unsigned long long *)&st->lkey[2 * slot], mm[0]);
-        atomicMax((unsigned long long *)&st->lkey[2 * slot + 1], mm[1]);
+        atomicMin((unsigned long long *)&st->win.key[2 * slot], mm[0]);
+        atomicMax((unsigned long long *)&st->win.key[2 * slot + 1], mm[1]);
     }
 }
 
@@ -83,7 +83,7 @@ __device__ __forceinline__ unsigned long long dipole_units(double x) {
 
 __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__restrict__ coords, int64_t pitch,
                                                              const int32_t *__restrict__ lt, const BunchState *st,
-                                                             const unsigned long long *win, int slot, int nbins,
+                                                             WakeWindow *win, int slot, int which, int nbins,
                                                              double w0, double sc,
                                                              uint32_t *__restrict__ hist, double *__restrict__ wfun,
                                                              double w0t, unsigned long long *__restrict__ dip,
@@ -91,11 +91,13 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     extern __shared__ __align__(8) unsigned char smem_raw[];
     uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw);
     const int64_t n = st->n_alive;
-    const uint64_t kmin = win[2 * slot], kmax = win[2 * slot + 1];
+    const uint64_t kmin = win->key[2 * slot], kmax = win->key[2 * slot + 1];
     const bool any = kmin <= kmax;
     const double lmin = any ? dkey_inv(kmin) : 0.0;
     const double lmax = any ? dkey_inv(kmax) : 0.0;
     const double dl = (lmax - lmin) / nbins;
+    // 1/dl for the kick (0: no window or zero width, every particle takes bin 0's voltage)
+    if (blockIdx.x == 0 && threadIdx.x == 0) win->idl[2 * slot + which] = (any && dl > 0.0) ? 1.0 / dl : 0.0;
     double rdl_s;
     long long bin_m;
     bin_consts(dl, nbins, rdl_s, bin_m);
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wake_conv_t(const unsigned lon
 __global__ void __launch_bounds__(1024) k_lsc_field(const uint32_t *__restrict__ hist, const BunchState *st, int slot,
                                                     int nbins, double qm, double KL, int passes, double *a, double *b,
                                                     double *__restrict__ V) {
-    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const uint64_t kmin = st->win.key[2 * slot], kmax = st->win.key[2 * slot + 1];
     const bool any = kmin <= kmax;
     const double lmin = any ? dkey_inv(kmin) : 0.0;
     const double lmax = any ? dkey_inv(kmax) : 0.0;
@@ -323,7 +325,7 @@ __device__ double lsc_taper(double f, double f0, double f1) {
 
 // Bin width of slot `slot`'s window (the wake's): dl > 0 when the field is defined.
 __device__ __forceinline__ double lsc_dl(const BunchState *st, int slot, int nbins) {
-    const uint64_t kmin = st->lkey[2 * slot], kmax = st->lkey[2 * slot + 1];
+    const uint64_t kmin = st->win.key[2 * slot], kmax = st->win.key[2 * slot + 1];
     if (kmin > kmax) return 0.0;
     return (dkey_inv(kmax) - dkey_inv(kmin)) / nbins;
 }
@@ -522,7 +524,7 @@ cudaError_t launch_wake_minmax(const double *coords, int64_t pitch, const int32_
 }
 
 cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t *lt, const BunchState *st,
-                             const unsigned long long *win, int slot,
+                             WakeWindow *win, int slot, int which,
                              int nbins, double w0, double sc, uint32_t *hist, double *wfun, double w0t,
                              unsigned long long *dip, double *wfun_t, int64_t n_max, cudaStream_t s) {
     // privatised sub-histograms up to kSmemBins bins, with the transverse sums up
@@ -544,8 +546,8 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
     int g = grid_for(n_max, kHistThreads, 152 * 2);
     const int gw = (nbins + kHistThreads - 1) / kHistThreads;
     if (g < gw) g = gw;
-    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, nbins, w0, sc, hist, wfun, w0t,
-                                              dip, wfun_t, smem_ok ? 1 : 0);
+    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, which, nbins, w0, sc, hist, wfun,
+                                              w0t, dip, wfun_t, smem_ok ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -208,10 +208,15 @@ def test_what_the_trained_network_gains():
       its coarse cells) the network must cut the wrong cells to a quarter or
       less: it has learned the aperture;
     - against the nearest known exact cell (the non-learned arm's predictor,
-      which sees the sentinel cells as well) it is not required to win: on this
-      workload the variants' apertures differ too much for one smooth function
-      of 8 inputs to beat a local interpolation of denser exact labels.  The
-      counts are printed; both triaged masks keep the one-cell boundary."""
+      which sees the sentinel cells as well): on this grid of 96^2 cells over
+      +-25 mm, where the aperture is smooth at the scale of a cell, the network
+      mislabels fewer of those cells and its triage band-tracks fewer cells than
+      the non-learned arm at equal inputs (measured 334 against 513 wrong cells,
+      4344 against 4540 tracked).  On the 512^2 grid the aperture's fringe is
+      finer than the known cells' spacing and the nearest known cell wins
+      instead (0.37 % against 0.41 % wrong), which is why the full-size scan's
+      non-learned arm is the faster one.
+    Both triaged masks keep the one-cell boundary."""
     nv, n, turns, stride = 4, 96, 300, 4
     L = [trk.trk_create_lattice(syn.lattice_c5(v), moments=False) for v in range(nv)]
     params_np = syn.c5_params()[:nv].astype(np.float32)
@@ -253,6 +258,8 @@ def test_what_the_trained_network_gains():
           % (int(unknown.sum()), wrong_net, wrong_const, wrong_nk, st_s["n_tracked"], st_n["n_tracked"]))
     assert wrong_const > 0
     assert wrong_net * 4 <= wrong_const
+    assert wrong_net < wrong_nk
+    assert st_s["n_tracked"] < st_n["n_tracked"]
     for v in range(nv):
         assert dm.boundary_difference(mask_s.cpu().numpy()[v], exh[v])[0]
         assert dm.boundary_difference(mask_n.cpu().numpy()[v], exh[v])[0]
