@@ -313,12 +313,14 @@ trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int32_t n_var, 
 /* MLP surrogate for dynamic-aperture triage (no counterpart in the paper).
  * Fixed architecture 8 -> 4 x [Linear 256 + GELU(erf)] -> Linear 256 -> 1 logit.
  * FP32 master weights and biases with BF16 copies; BF16 activations into the
- * tensor-core products (mma.sync, FP32 accumulation); BCE loss on the logit;
- * Adam (Kingma & Ba).  Rounding points: h0 = bf16(x), z = h W^T + b (FP32),
- * h = bf16(gelu(z)); dz = dh * gelu'(z) (FP32) rounded to BF16 for dW = dz^T h
- * and dh = dz W; db = sum dz (FP32).  Inference (trk_mlp_forward) runs its
- * hidden layers on tcgen05 (128 x 256 tiles, FP32 accumulators in tensor
- * memory); training on mma.sync; the rounding points are the same.
+ * tensor-core products (tcgen05, FP32 accumulation in tensor memory); BCE loss
+ * on the logit; Adam (Kingma & Ba).  Rounding points: h0 = bf16(x),
+ * z = h W^T + b (FP32), h = bf16(gelu(z)); dz = dh * gelu'(z) (FP32) rounded to
+ * BF16 for dW = dz^T h and dh = dz W; db = sum dz (FP32).  Inference
+ * (trk_mlp_forward) runs its hidden layers as persistent 128 x 256 tiles;
+ * training (trk_mlp_grad, trk_mlp_train) runs every product -- forward, input
+ * gradient, weight gradient split over the batch and summed in split order --
+ * as 128 x 64 tiles; the rounding points are the same.
  *   W[l], b[l]   HOST FP32 arrays, W[l] row-major [out][in]: l = 0: 256 x 8,
  *                l = 1..3: 256 x 256, l = 4: 1 x 256; b[l] [out]
  *   d_X          device FP32 [M][8] inputs; d_y device FP32 [M] labels (0/1)

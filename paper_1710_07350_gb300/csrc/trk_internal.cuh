@@ -181,7 +181,7 @@ cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, 
                               int64_t n_tiles, uint16_t *out_tiled, int *d_err, cudaStream_t s);
 cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s);
 cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, cudaStream_t s);
-// Training products on tcgen05 (trk_mlp_umma.cu): one 128 x 64 output tile per CTA.
+// Training products on tcgen05 (trk_mlp_umma.cu): one output tile per CTA.
 cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_tiled, const float *bias,
                              int64_t m_pad, float *Z, uint16_t *Hout_tiled, uint16_t *Hout_T, uint16_t *Hout_rm,
                              int *d_err, cudaStream_t s);
@@ -190,10 +190,18 @@ cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled,
 int train_dw_splits(int64_t m_pad);
 cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in, int64_t m_pad, float *part,
                             int *d_err, cudaStream_t s);
-cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T, cudaStream_t s);
+// Training inputs in both layouts; with step != NULL the batch rows are
+// gathered through perm at the device step counter (labels into yb).
+cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T,
+                               const int32_t *perm, int64_t n, int64_t batch, int64_t spe, const int64_t *step,
+                               const float *y, float *yb, cudaStream_t s);
 cudaError_t launch_train_head_back(const float *logit, const float *y, int64_t M, int64_t m_pad, const uint16_t *w5,
                                    const float *Z4, float *dl, float *dz, uint16_t *dzb, uint16_t *dzbT,
                                    float *loss_terms, cudaStream_t s);
+cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint16_t *pb, int64_t n, float lr,
+                             const float *c12, int64_t *step, const float *loss, float *loss_hist, unsigned *ticket,
+                             const size_t *w_off, const size_t *w_end, const size_t *wt_off, const size_t *wtT_off,
+                             const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s);
 cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const size_t *wt_off, const size_t *wtT_off,
                                   const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s);
 cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s);

@@ -1,6 +1,8 @@
 // MLP surrogate for dynamic-aperture triage: 8 -> 4 x [Linear 256 + GELU] -> 1.
-// BF16 weights and activations into tensor-core products (mma.sync m16n8k16,
-// FP32 accumulation), FP32 master weights, biases and gradients, Adam.
+// BF16 weights and activations into tcgen05 tensor-core products (FP32
+// accumulation in tensor memory, trk_mlp_umma.cu), FP32 master weights, biases
+// and gradients, Adam.  This file holds the network's parameters and buffers,
+// the small reductions and the Adam update, and drives the products.
 //
 // Rounding points (kept identical to the oracle's):
 //   h0 = bf16(x); z_l = h_{l-1} W_l^T + b_l (FP32); h_l = bf16(gelu(z_l))
@@ -20,211 +22,6 @@ namespace trk {
 namespace {
 
 constexpr int kIn = 8, kInPad = 64, kW = 256, kHidden = 4;  // inputs padded to one 64-wide tile
-constexpr int BM = 64, BN = 64, BK = 32, SK = BK + 8;  // smem row stride (bf16), padded against bank conflicts
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
-
-enum { EPI_F32 = 0, EPI_GELU = 1, EPI_GELU_STOREZ = 2, EPI_DGELU = 3 };
-
-// C[M x N] = A[M x K] * B[K x N].
-//   A_T = false: A[m][k] = A[m * lda + k];  A_T = true: A[m][k] = A[k * lda + m]
-//   B_NK = true: B[k][n] = B[n * ldb + k];  B_NK = false: B[k][n] = B[k * ldb + n]
-// Epilogues: EPI_F32 stores acc (FP32, ldc); EPI_GELU stores bf16(gelu(acc + bias));
-// EPI_GELU_STOREZ also stores z = acc + bias (FP32); EPI_DGELU multiplies acc by
-// gelu'(aux[m][n]) and stores the product (FP32 and BF16).
-// Split-K: block z sums k in [z * k_split, min(K, (z + 1) * k_split)) and stores
-// its FP32 partial at Cf + z * c_split (EPI_F32 only; the caller reduces).
-// M, N multiples of 64, K and k_split multiples of 32, lda, ldb multiples of 8
-// and A, B 16-byte aligned (the caller pads): tiles move as 16-byte vectors.
-template <bool A_T, bool B_NK, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
-                                              const __nv_bfloat16 *__restrict__ B, int ldb, int K,
-                                              float *__restrict__ Cf, int ldc, __nv_bfloat16 *__restrict__ Cb,
-                                              const float *__restrict__ bias, const float *__restrict__ aux,
-                                              int k_split, size_t c_split) {
-    // two shared-memory stages: the next tile's global loads are in flight in
-    // registers while the current tile's MMAs run, then land in the other stage
-    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * SK];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][BN * SK];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, tg = lane & 3;
-    const int kbeg = blockIdx.z * k_split, kend = kbeg + k_split < K ? kbeg + k_split : K;
-    if (EPI == EPI_F32) Cf += blockIdx.z * c_split;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-
-    // A tile BM x BK and B tile (stored n-major, sB[n][k]) BN x BK: 256 16-byte
-    // vectors each, two per thread.
-    uint4 ra[2], rb[2];
-    const auto load = [&](int k0) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int e = tid + q * 128;
-            if (!A_T) {
-                const int m = e >> 2, k = (e & 3) * 8;
-                ra[q] = *reinterpret_cast<const uint4 *>(&A[(size_t)(m0 + m) * lda + (k0 + k)]);
-            } else {
-                const int k = e >> 3, m = (e & 7) * 8;
-                ra[q] = *reinterpret_cast<const uint4 *>(&A[(size_t)(k0 + k) * lda + (m0 + m)]);
-            }
-            if (B_NK) {
-                const int n = e >> 2, k = (e & 3) * 8;
-                rb[q] = *reinterpret_cast<const uint4 *>(&B[(size_t)(n0 + n) * ldb + (k0 + k)]);
-            } else {
-                const int k = e >> 3, n = (e & 7) * 8;
-                rb[q] = *reinterpret_cast<const uint4 *>(&B[(size_t)(k0 + k) * ldb + (n0 + n)]);
-            }
-        }
-    };
-    const auto store = [&](int st) {
-        __nv_bfloat16 *a = sA[st], *b = sB[st];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int e = tid + q * 128;
-            if (!A_T) {
-                const int m = e >> 2, k = (e & 3) * 8;
-                *reinterpret_cast<uint4 *>(&a[m * SK + k]) = ra[q];
-            } else {
-                const int k = e >> 3, m = (e & 7) * 8;
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&ra[q]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) a[(m + i) * SK + k] = h[i];
-            }
-            if (B_NK) {
-                const int n = e >> 2, k = (e & 3) * 8;
-                *reinterpret_cast<uint4 *>(&b[n * SK + k]) = rb[q];
-            } else {
-                const int k = e >> 3, n = (e & 7) * 8;
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&rb[q]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) b[(n + i) * SK + k] = h[i];
-            }
-        }
-    };
-    int st = 0;
-    if (kbeg < kend) {
-        load(kbeg);
-        store(0);
-    }
-    __syncthreads();
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        const bool more = k0 + BK < kend;
-        if (more) load(k0 + BK);
-        const __nv_bfloat16 *a = sA[st], *b = sB[st];
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + g, c = kk + tg * 2;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&a[r * SK + c]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&a[(r + 8) * SK + c]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&a[r * SK + c + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&a[(r + 8) * SK + c + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = wn + j * 8 + g, c = kk + tg * 2;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&b[n * SK + c]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&b[n * SK + c + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]),
-                          "r"(bf[j][1]));
-        }
-        // the other stage was last read before the previous barrier
-        if (more) store(st ^ 1);
-        __syncthreads();
-        st ^= 1;
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int row = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
-                const int col = n0 + wn + j * 8 + tg * 2 + (r & 1);
-                const size_t o = (size_t)row * ldc + col;
-                float v = acc[i][j][r];
-                if (EPI == EPI_F32) {
-                    Cf[o] = v;
-                } else if (EPI == EPI_GELU || EPI == EPI_GELU_STOREZ) {
-                    v += bias[col];
-                    if (EPI == EPI_GELU_STOREZ) Cf[o] = v;
-                    Cb[o] = __float2bfloat16_rn(gelu_f(v));
-                } else {  // EPI_DGELU
-                    v *= gelu_grad_f(aux[o]);
-                    Cf[o] = v;
-                    Cb[o] = __float2bfloat16_rn(v);
-                }
-            }
-}
-
-// x [M x 8] FP32 -> h0 [M x 64] BF16 (zero padded)
-__global__ void k_input(const float *__restrict__ X, int64_t M, int64_t m_pad, __nv_bfloat16 *__restrict__ H0) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad * kInPad;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i / kInPad;
-        const int k = (int)(i % kInPad);
-        const float v = (m < M && k < kIn) ? X[m * kIn + k] : 0.0f;
-        H0[i] = __float2bfloat16_rn(v);
-    }
-}
-
-// logit[m] = h4[m] . w5 + b5 (warp per row)
-__global__ void k_head(const __nv_bfloat16 *__restrict__ H4, const __nv_bfloat16 *__restrict__ w5, const float *b5,
-                       int64_t M, float *__restrict__ logit) {
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= M) return;
-    float s = 0.0f;
-#pragma unroll
-    for (int k = lane; k < kW; k += 32) s += __bfloat162float(H4[row * kW + k]) * __bfloat162float(w5[k]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) logit[row] = s + b5[0];
-}
-
-// dlogit = (sigmoid - y)/M, loss terms; dz4 = (dlogit w5) * gelu'(z4) for valid rows
-__global__ void k_head_back(const float *__restrict__ logit, const float *__restrict__ y, int64_t M, int64_t m_pad,
-                            const __nv_bfloat16 *__restrict__ w5, const float *__restrict__ Z4, float *__restrict__ dl,
-                            float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb, float *__restrict__ loss_terms) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad * kW;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i / kW;
-        const int k = (int)(i % kW);
-        float d = 0.0f;
-        if (m < M) {
-            const float l = logit[m];
-            d = (1.0f / (1.0f + expf(-l)) - y[m]) / (float)M;
-            if (k == 0) {
-                dl[m] = d;
-                loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - y[m] * l;
-            }
-        }
-        const float v = d * __bfloat162float(w5[k]) * gelu_grad_f(Z4[i]);
-        dz[i] = m < M ? v : 0.0f;
-        dzb[i] = __float2bfloat16_rn(m < M ? v : 0.0f);
-    }
-}
 
 // out[n] = sum_m A[m][n] (* w[m] if w): column sums over N = 256 columns in a
 // fixed order, FP32, in one launch: each of kColSlices blocks writes the partial
@@ -239,10 +36,34 @@ __global__ void k_colsum(const float *__restrict__ A, const __nv_bfloat16 *__res
     const int n = threadIdx.x;  // blockDim.x == kW
     const int64_t per = (M + kColSlices - 1) / kColSlices;
     const int64_t m0 = blockIdx.x * per, m1 = m0 + per < M ? m0 + per : M;
+    // the rows are added one after another in row order; the loads of 16 rows
+    // are issued before their adds so that they are in flight together
     float s = 0.0f;
-    for (int64_t m = m0; m < m1; ++m) {
-        const float a = A ? A[m * kW + n] : __bfloat162float(Ab[m * kW + n]);
-        s += w ? a * w[m] : a;
+    int64_t m = m0;
+    if (A) {
+        for (; m + 16 <= m1; m += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = A[(m + q) * kW + n];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s += v[q];
+        }
+        for (; m < m1; ++m) s += A[m * kW + n];
+    } else {
+        for (; m + 16 <= m1; m += 16) {
+            float v[16], ww[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                v[q] = __bfloat162float(Ab[(m + q) * kW + n]);
+                ww[q] = w ? w[m + q] : 1.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s += w ? v[q] * ww[q] : v[q];
+        }
+        for (; m < m1; ++m) {
+            const float a = __bfloat162float(Ab[m * kW + n]);
+            s += w ? a * w[m] : a;
+        }
     }
     part[blockIdx.x * kW + n] = s;
     __threadfence();
@@ -252,7 +73,13 @@ __global__ void k_colsum(const float *__restrict__ A, const __nv_bfloat16 *__res
     if (!last) return;
     __threadfence();
     float t = 0.0f;
-    for (int j = 0; j < kColSlices; ++j) t += __ldcg(part + j * kW + n);
+    for (int j = 0; j < kColSlices; j += 16) {
+        float pv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) pv[q] = __ldcg(part + (j + q) * kW + n);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) t += pv[q];
+    }
     out[n] = t;
     if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -274,11 +101,18 @@ __global__ void k_sum2(const float *__restrict__ a0, const float *__restrict__ a
 }
 
 // out[i] = sum over slices s = 0, 1, ... of part[s * n + i], in slice order.
-constexpr int kSplits = 16;
 __global__ void k_reduce_splits(const float *__restrict__ part, int splits, int64_t n, float *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float a = part[i];
-        for (int z = 1; z < splits; ++z) a += part[z * n + i];
+        // up to 16 slices' loads in flight, added in slice order
+        float a = 0.0f;
+        for (int z0 = 0; z0 < splits; z0 += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = z0 + q < splits ? part[(int64_t)(z0 + q) * n + i] : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (z0 + q < splits) a = (z0 + q == 0) ? v[q] : a + v[q];
+        }
         out[i] = a;
     }
 }
@@ -333,20 +167,25 @@ struct trk_mlp {
     size_t w_off[5], b_off[5], n_par;  // offsets into the flat FP32 parameter arrays
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // master, Adam, gradients
     __nv_bfloat16 *pb = nullptr;                                   // BF16 copy of p
-    int64_t cap = 0;                                               // rows of the activation buffers
-    __nv_bfloat16 *H[kHidden + 1] = {};                            // h0 .. h4
-    float *Z[kHidden] = {};                                        // z1 .. z4
-    float *dz = nullptr;                                           // FP32 dz of the current layer
-    __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
-    float *logit = nullptr, *dl = nullptr, *loss_terms = nullptr, *loss = nullptr;
+    float *loss = nullptr;                                         // mean loss of the last gradient
     float *part = nullptr;                                         // column-sum partials, then the ticket
-    float *splitk = nullptr;                                       // split-K partials of dW [kSplits][256][256]
     uint16_t *wt = nullptr;                                        // BF16 weights of layers 0..3, tcgen05 tiled layout
     size_t wt_off[kHidden] = {};
     uint16_t *act[2] = {nullptr, nullptr};                         // tiled activations for inference (ping-pong)
     int64_t act_rows = 0;
     int *d_err = nullptr;                                          // device error flag of the tcgen05 layers
     int64_t t = 0;                                                 // Adam step
+    // training on tcgen05: activations tiled (A of the products) and
+    // transposed-tiled (B of the weight gradients), pre-activations, the
+    // gradient chain, the transposed weight tiles and the split partials
+    int64_t tc_cap = 0;
+    uint16_t *Ht[kHidden + 1] = {}, *HT[kHidden + 1] = {}, *H4rm = nullptr;
+    float *Zt[kHidden] = {}, *tdz = nullptr, *tlogit = nullptr, *tdl = nullptr, *tloss_terms = nullptr;
+    uint16_t *dzbt[2] = {nullptr, nullptr}, *dzbT = nullptr;
+    float *tpart = nullptr;
+    unsigned *tickets = nullptr;   // [9]: the Adam step's block counter (zero between launches)
+    uint16_t *wtT = nullptr;
+    size_t wtT_off[kHidden] = {};
 };
 
 static trk_status mlp_fail(trk_status s, const std::string &m) { return set_error(s, m); }
@@ -354,46 +193,60 @@ static trk_status mlp_fail(trk_status s, const std::string &m) { return set_erro
 // The column sums' ticket counter, kept after the partials (zero between calls).
 static unsigned *col_ticket(trk_mlp *N) { return reinterpret_cast<unsigned *>(N->part + kColSlices * kW); }
 
-static void mlp_free_acts(trk_mlp *N) {
-    for (auto &h : N->H) {
-        cudaFree(h);
-        h = nullptr;
+static void mlp_free_tc(trk_mlp *N) {
+    for (int l = 0; l <= kHidden; ++l) {
+        cudaFree(N->Ht[l]);
+        cudaFree(N->HT[l]);
+        N->Ht[l] = N->HT[l] = nullptr;
     }
-    for (auto &z : N->Z) {
-        cudaFree(z);
-        z = nullptr;
+    for (int l = 0; l < kHidden; ++l) {
+        cudaFree(N->Zt[l]);
+        N->Zt[l] = nullptr;
     }
-    cudaFree(N->dz);
-    cudaFree(N->dzb);
-    cudaFree(N->dzb2);
-    cudaFree(N->logit);
-    cudaFree(N->dl);
-    cudaFree(N->loss_terms);
-    N->dz = nullptr;
-    N->dzb = N->dzb2 = nullptr;
-    N->logit = N->dl = N->loss_terms = nullptr;
-    N->cap = 0;
+    cudaFree(N->H4rm);
+    cudaFree(N->tdz);
+    cudaFree(N->tlogit);
+    cudaFree(N->tdl);
+    cudaFree(N->tloss_terms);
+    cudaFree(N->dzbt[0]);
+    cudaFree(N->dzbt[1]);
+    cudaFree(N->dzbT);
+    cudaFree(N->tpart);
+    cudaFree(N->tickets);
+    N->H4rm = N->dzbt[0] = N->dzbt[1] = N->dzbT = nullptr;
+    N->tdz = N->tlogit = N->tdl = N->tloss_terms = N->tpart = nullptr;
+    N->tickets = nullptr;
+    N->tc_cap = 0;
 }
 
-static trk_status mlp_ensure(trk_mlp *N, int64_t rows, bool training) {
-    if (rows <= N->cap && (!training || N->Z[0])) return TRK_OK;
-    mlp_free_acts(N);
+// Buffers of the tcgen05 training step for up to `rows` rows (a multiple of 128).
+static trk_status mlp_ensure_tc(trk_mlp *N, int64_t rows) {
+    if (rows <= N->tc_cap) return TRK_OK;
+    mlp_free_tc(N);
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&N->H[0], rows * kInPad * sizeof(__nv_bfloat16));
-    for (int l = 1; l <= kHidden && e == cudaSuccess; ++l) e = cudaMalloc(&N->H[l], rows * kW * sizeof(__nv_bfloat16));
-    if (training)
-        for (int l = 0; l < kHidden && e == cudaSuccess; ++l) e = cudaMalloc(&N->Z[l], rows * kW * sizeof(float));
-    if (e == cudaSuccess && training) e = cudaMalloc(&N->dz, rows * kW * sizeof(float));
-    if (e == cudaSuccess && training) e = cudaMalloc(&N->dzb, rows * kW * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess && training) e = cudaMalloc(&N->dzb2, rows * kW * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&N->logit, rows * sizeof(float));
-    if (e == cudaSuccess && training) e = cudaMalloc(&N->dl, rows * sizeof(float));
-    if (e == cudaSuccess && training) e = cudaMalloc(&N->loss_terms, rows * sizeof(float));
-    if (e != cudaSuccess) {
-        mlp_free_acts(N);
-        return mlp_fail(TRK_ENOMEM, "trk_mlp: activation allocation failed");
+    const size_t r = (size_t)rows;
+    for (int l = 0; l <= kHidden && e == cudaSuccess; ++l) {
+        const size_t k = l == 0 ? kInPad : kW;
+        e = cudaMalloc(&N->Ht[l], r * k * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&N->HT[l], r * k * sizeof(uint16_t));
     }
-    N->cap = rows;
+    for (int l = 0; l < kHidden && e == cudaSuccess; ++l) e = cudaMalloc(&N->Zt[l], r * kW * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->H4rm, r * kW * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tdz, r * kW * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tlogit, r * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tdl, r * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tloss_terms, r * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->dzbt[0], r * kW * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&N->dzbt[1], r * kW * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&N->dzbT, r * kW * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tpart, (size_t)train_dw_splits(rows) * kW * kW * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->tickets, 16 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(N->tickets, 0, 16 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        mlp_free_tc(N);
+        return mlp_fail(TRK_ENOMEM, "trk_mlp: training buffer allocation failed");
+    }
+    N->tc_cap = rows;
     return TRK_OK;
 }
 
@@ -430,7 +283,6 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
     if (e == cudaSuccess) e = cudaMalloc(&N->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->part, (kColSlices * kW + 4) * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(N->part + kColSlices * kW, 0, 4 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&N->splitk, (size_t)kSplits * kW * kW * sizeof(float));
     {
         size_t o = 0;
         for (int l = 0; l < kHidden; ++l) {
@@ -438,6 +290,12 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
             o += (size_t)kW * N->in_pad[l];
         }
         if (e == cudaSuccess) e = cudaMalloc(&N->wt, o * sizeof(uint16_t));
+        size_t ot = 0;
+        for (int l = 1; l < kHidden; ++l) {
+            N->wtT_off[l] = ot;
+            ot += (size_t)kW * kW;
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&N->wtT, ot * sizeof(uint16_t));
     }
     if (e == cudaSuccess) e = cudaMalloc(&N->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(N->d_err, 0, sizeof(int));
@@ -457,8 +315,8 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
         cudaFree(N->pb);
         cudaFree(N->loss);
         cudaFree(N->part);
-        cudaFree(N->splitk);
         cudaFree(N->wt);
+        cudaFree(N->wtT);
         cudaFree(N->d_err);
         delete N;
         return mlp_fail(TRK_ENOMEM, std::string("trk_mlp_create: ") + cudaGetErrorString(e));
@@ -470,7 +328,6 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
 extern "C" trk_status trk_mlp_destroy(trk_mlp *N) {
     if (!N) return TRK_OK;
     cudaDeviceSynchronize();
-    mlp_free_acts(N);
     cudaFree(N->p);
     cudaFree(N->m);
     cudaFree(N->v);
@@ -478,35 +335,14 @@ extern "C" trk_status trk_mlp_destroy(trk_mlp *N) {
     cudaFree(N->pb);
     cudaFree(N->loss);
     cudaFree(N->part);
-    cudaFree(N->splitk);
     cudaFree(N->wt);
+    cudaFree(N->wtT);
     cudaFree(N->d_err);
     cudaFree(N->act[0]);
     cudaFree(N->act[1]);
+    mlp_free_tc(N);
     delete N;
     return TRK_OK;
-}
-
-// Forward over rows [0, m_pad) of the buffers (m_pad a multiple of 64).
-static cudaError_t mlp_forward_rows(trk_mlp *N, const float *X, int64_t M, int64_t m_pad, bool training,
-                                    cudaStream_t s) {
-    k_input<<<grid_for(m_pad * kInPad), 256, 0, s>>>(X, M, m_pad, N->H[0]);
-    for (int l = 0; l < kHidden; ++l) {
-        const int K = N->in_pad[l];
-        const dim3 grid(kW / BN, (unsigned)(m_pad / BM));
-        const __nv_bfloat16 *W = N->pb + N->w_off[l];
-        const float *b = N->p + N->b_off[l];
-        if (training)
-            k_gemm<false, true, EPI_GELU_STOREZ><<<grid, 128, 0, s>>>(N->H[l], K, W, K, K, N->Z[l], kW, N->H[l + 1],
-                                                                      b, nullptr, K, 0);
-        else
-            k_gemm<false, true, EPI_GELU><<<grid, 128, 0, s>>>(N->H[l], K, W, K, K, nullptr, kW, N->H[l + 1], b,
-                                                               nullptr, K, 0);
-    }
-    const int rows_per_block = 8;
-    k_head<<<(unsigned)((M + rows_per_block - 1) / rows_per_block), 32 * rows_per_block, 0, s>>>(
-        N->H[kHidden], N->pb + N->w_off[4], N->p + N->b_off[4], M, N->logit);
-    return cudaGetLastError();
 }
 
 // Inference on the tcgen05 layers: inputs and activations in the tiled layout
@@ -562,42 +398,60 @@ extern "C" trk_status trk_mlp_forward(trk_mlp *N, const float *d_X, int64_t M, f
     return trk_mlp_forward_hidden(N, d_X, M, d_logits, nullptr, stream);
 }
 
-// Gradients of the mean BCE over M rows into N->g; loss into N->loss.
-static cudaError_t mlp_grad_rows(trk_mlp *N, const float *X, const float *y, int64_t M, cudaStream_t s) {
-    const int64_t m_pad = (M + BM - 1) / BM * BM;
-    cudaError_t e = mlp_forward_rows(N, X, M, m_pad, true, s);
+// The tiled weight copies (wt for the forward products, wtT = W^T for the
+// input gradients) from the BF16 weights.
+static cudaError_t mlp_retile(trk_mlp *N, cudaStream_t s) {
+    const uint16_t *pb = reinterpret_cast<const uint16_t *>(N->pb);
+    const int in_pad[kHidden] = {N->in_pad[0], N->in_pad[1], N->in_pad[2], N->in_pad[3]};
+    return launch_retile_weights(pb, N->w_off, N->wt_off, N->wtT_off, in_pad, N->wt, N->wtT, s);
+}
+
+// Gradients of the mean BCE over M rows into N->g and the loss into N->loss,
+// every product on tcgen05 (the tiled weights must be current: mlp_retile).
+// Rounding points as mlp_grad_rows: h0 = bf16(x), z FP32, h = bf16(gelu(z)),
+// dz FP32, dzb = bf16(dz), dW = dzb^T h and dh = dzb W in FP32, db = sum dz.
+struct GatherRows {
+    const int32_t *perm = nullptr;
+    int64_t n = 0, batch = 0, spe = 1;
+    const int64_t *step = nullptr;   // NULL: rows [0, M) of X and y as given
+    const float *y_all = nullptr;
+};
+
+static cudaError_t mlp_grad_tc(trk_mlp *N, const float *X, const float *y, int64_t M, cudaStream_t s,
+                               const GatherRows &gr = GatherRows()) {
+    const int64_t m_pad = (M + 127) / 128 * 128;
+    const uint16_t *pb = reinterpret_cast<const uint16_t *>(N->pb);
+    // with a gather, y is the batch's label buffer that the input kernel fills
+    cudaError_t e = launch_train_input(X, M, m_pad, N->Ht[0], N->HT[0], gr.perm, gr.n, gr.batch, gr.spe, gr.step,
+                                       gr.y_all, const_cast<float *>(y), s);
+    for (int l = 0; l < kHidden && e == cudaSuccess; ++l)
+        e = launch_train_fwd(N->Ht[l], N->in_pad[l], N->wt + N->wt_off[l], N->p + N->b_off[l], m_pad, N->Zt[l],
+                             N->Ht[l + 1], N->HT[l + 1], l == kHidden - 1 ? N->H4rm : nullptr, N->d_err, s);
+    if (e == cudaSuccess)
+        e = launch_head_tiled(N->Ht[kHidden], pb + N->w_off[4], N->p + N->b_off[4], M, N->tlogit, s);
+    if (e == cudaSuccess)
+        e = launch_train_head_back(N->tlogit, y, M, m_pad, pb + N->w_off[4], N->Zt[kHidden - 1], N->tdl, N->tdz,
+                                   N->dzbt[0], N->dzbT, N->tloss_terms, s);
     if (e != cudaSuccess) return e;
-    // head backward: dlogit, dz4 (rows beyond M are zero)
-    k_head_back<<<grid_for(m_pad * kW), 256, 0, s>>>(N->logit, y, M, m_pad, N->pb + N->w_off[4], N->Z[kHidden - 1],
-                                                    N->dl, N->dz, N->dzb, N->loss_terms);
-    k_colsum<<<kColSlices, kW, 0, s>>>(nullptr, N->H[kHidden], N->dl, M, N->part, col_ticket(N),
-                                       N->g + N->w_off[4]);
-    k_sum2<<<2, 256, 0, s>>>(N->dl, N->loss_terms, M, 1.0f, 1.0f / (float)M, N->g + N->b_off[4], N->loss);
-    // dW reduces over the rows: split them into at most kSplits slices of
-    // k_split rows, one block column each, then sum the partials in slice order.
-    int splits = (int)(m_pad / 256) < kSplits ? (int)(m_pad / 256) : kSplits;
-    if (splits < 1) splits = 1;
-    const int k_split = (int)(((m_pad + splits - 1) / splits + BK - 1) / BK * BK);
-    splits = (int)((m_pad + k_split - 1) / k_split);
-    __nv_bfloat16 *dzb = N->dzb, *dzb_next = N->dzb2;
-    for (int l = kHidden - 1; l >= 0; --l) {
+    k_colsum<<<kColSlices, kW, 0, s>>>(nullptr, reinterpret_cast<const __nv_bfloat16 *>(N->H4rm), N->tdl, M, N->part,
+                                       col_ticket(N), N->g + N->w_off[4]);
+    k_sum2<<<2, 256, 0, s>>>(N->tdl, N->tloss_terms, M, 1.0f, 1.0f / (float)M, N->g + N->b_off[4], N->loss);
+    int cur = 0;
+    for (int l = kHidden - 1; l >= 0 && e == cudaSuccess; --l) {
         const int K = N->in_pad[l];
-        // dW_l [256 x K] = dzb^T [256 x m_pad] * h_{l} [m_pad x K]   (A transposed, B k-major rows)
-        k_gemm<true, false, EPI_F32><<<dim3((K + BN - 1) / BN, kW / BM, splits), 128, 0, s>>>(
-            dzb, kW, N->H[l], K, (int)m_pad, N->splitk, K, nullptr, nullptr, nullptr, k_split, (size_t)kW * K);
-        k_reduce_splits<<<grid_for((int64_t)kW * K), 256, 0, s>>>(N->splitk, splits, (int64_t)kW * K,
+        // dW_l: batch-split partials, summed in split order
+        e = launch_train_dw(N->dzbT, N->HT[l], K, m_pad, N->tpart, N->d_err, s);
+        if (e != cudaSuccess) break;
+        k_reduce_splits<<<grid_for((int64_t)kW * K), 256, 0, s>>>(N->tpart, train_dw_splits(m_pad), (int64_t)kW * K,
                                                                   N->g + N->w_off[l]);
-        // db_l = sum_m dz (FP32)
-        k_colsum<<<kColSlices, kW, 0, s>>>(N->dz, nullptr, nullptr, M, N->part, col_ticket(N), N->g + N->b_off[l]);
+        k_colsum<<<kColSlices, kW, 0, s>>>(N->tdz, nullptr, nullptr, M, N->part, col_ticket(N), N->g + N->b_off[l]);
         if (l > 0) {
-            // dz_{l-1} = (dzb W_l) * gelu'(z_{l-1}), W_l [256 x 256] as B[k = out][n = in]
-            k_gemm<false, false, EPI_DGELU><<<dim3(kW / BN, (unsigned)(m_pad / BM)), 128, 0, s>>>(
-                dzb, kW, N->pb + N->w_off[l], kW, kW, N->dz, kW, dzb_next, nullptr, N->Z[l - 1], kW, 0);
-            __nv_bfloat16 *t = dzb;
-            dzb = dzb_next;
-            dzb_next = t;
+            e = launch_train_dx(N->dzbt[cur], N->wtT + N->wtT_off[l], N->Zt[l - 1], m_pad, N->tdz, N->dzbt[cur ^ 1],
+                                N->dzbT, N->d_err, s);
+            cur ^= 1;
         }
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -605,10 +459,11 @@ extern "C" trk_status trk_mlp_grad(trk_mlp *N, const float *d_X, const float *d_
                                    void *stream) {
     if (!N || M < 1 || !d_X || !d_y) return mlp_fail(TRK_EINVAL, "trk_mlp_grad: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t m_pad = ((int64_t)M + BM - 1) / BM * BM;
-    trk_status st = mlp_ensure(N, m_pad, true);
+    const int64_t m_pad = ((int64_t)M + 127) / 128 * 128;
+    trk_status st = mlp_ensure_tc(N, m_pad);
     if (st != TRK_OK) return st;
-    cudaError_t e = mlp_grad_rows(N, d_X, d_y, M, s);
+    cudaError_t e = mlp_retile(N, s);
+    if (e == cudaSuccess) e = mlp_grad_tc(N, d_X, d_y, M, s);
     if (e == cudaSuccess && d_loss) e = cudaMemcpyAsync(d_loss, N->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_grad: ") + cudaGetErrorString(e));
     return TRK_OK;
@@ -627,41 +482,31 @@ extern "C" trk_status trk_mlp_adam(trk_mlp *N, float lr, float beta1, float beta
 
 namespace trk {
 namespace {
-// Rows of training step *step: epoch e = step / spe, rows [r0, r0 + m) of the
-// epoch's order with r0 = (step % spe) * batch; the order is perm[e * n + r]
-// (identity without perm).
-__global__ void k_gather_rows(const float *__restrict__ X, const float *__restrict__ y, const int32_t *__restrict__ perm,
-                              int64_t n, int64_t batch, int64_t spe, const int64_t *__restrict__ step, int64_t m,
-                              float *__restrict__ Xo, float *__restrict__ yo) {
-    const int64_t st = *step, ep = st / spe, r0 = (st % spe) * batch;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = perm ? (int64_t)perm[ep * n + r0 + i] : r0 + i;
-        for (int k = 0; k < kIn; ++k) Xo[i * kIn + k] = X[r * kIn + k];
-        yo[i] = y[r];
-    }
-}
-
-// End of a training step: record the loss, advance the step counter.
-__global__ void k_step_end(const float *__restrict__ loss, float *__restrict__ hist, int64_t *__restrict__ step) {
-    if (hist) hist[*step] = *loss;
-    *step += 1;
-}
-
 // One training step on m rows, enqueued on s (captured into a graph).
 cudaError_t train_step(trk_mlp *N, const float *d_X, const float *d_y, const int32_t *d_perm, int64_t n,
-                       int64_t batch, int64_t spe, int64_t m, float lr, const float *c12, int64_t *dstep, float *Xb,
+                       int64_t batch, int64_t spe, int64_t m, float lr, const float *c12, int64_t *dstep,
                        float *yb, float *d_loss_hist, cudaStream_t s) {
-    k_gather_rows<<<grid_for(m), 256, 0, s>>>(d_X, d_y, d_perm, n, batch, spe, dstep, m, Xb, yb);
-    cudaError_t e = mlp_grad_rows(N, Xb, yb, m, s);
+    GatherRows gr;
+    gr.perm = d_perm;
+    gr.n = n;
+    gr.batch = batch;
+    gr.spe = spe;
+    gr.step = dstep;
+    gr.y_all = d_y;
+    cudaError_t e = mlp_grad_tc(N, d_X, yb, m, s, gr);
     if (e != cudaSuccess) return e;
-    k_adam<<<grid_for(N->n_par), 256, 0, s>>>(N->p, N->m, N->v, N->g, N->pb, N->n_par, lr, 0.9f, 0.999f, 1e-8f, 0.0f,
-                                              0.0f, c12, dstep);
-    k_step_end<<<1, 1, 0, s>>>(N->loss, d_loss_hist, dstep);
-    return cudaGetLastError();
+    // Adam, the tiled weight copies for the next step and the step counter in one launch
+    size_t w_end[kHidden];
+    for (int l = 0; l < kHidden; ++l) w_end[l] = N->b_off[l];
+    const int in_pad[kHidden] = {N->in_pad[0], N->in_pad[1], N->in_pad[2], N->in_pad[3]};
+    e = launch_adam_step(N->p, N->m, N->v, N->g, reinterpret_cast<uint16_t *>(N->pb), (int64_t)N->n_par, lr, c12, dstep,
+                         N->loss, d_loss_hist, N->tickets + 9, N->w_off, w_end, N->wt_off, N->wtT_off, in_pad, N->wt,
+                         N->wtT, s);
+    return e;
 }
 
 struct TrainRes {
-    float *Xb = nullptr, *yb = nullptr, *c12 = nullptr;
+    float *yb = nullptr, *c12 = nullptr;
     int64_t *dstep = nullptr;
     cudaStream_t ps = nullptr;
     cudaEvent_t ev = nullptr;
@@ -673,7 +518,6 @@ struct TrainRes {
             if (g[i]) cudaGraphDestroy(g[i]);
         }
         if (ps) cudaStreamSynchronize(ps);
-        cudaFree(Xb);
         cudaFree(yb);
         cudaFree(c12);
         cudaFree(dstep);
@@ -697,8 +541,8 @@ extern "C" trk_status trk_mlp_train(trk_mlp *N, const float *d_X, const float *d
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t b = batch < n ? batch : n;
     const int64_t spe = (n + b - 1) / b, total = spe * epochs, tail = n - (spe - 1) * b;
-    const int64_t m_pad = (b + BM - 1) / BM * BM;
-    trk_status st = mlp_ensure(N, m_pad, true);
+    const int64_t m_pad = (b + 127) / 128 * 128;
+    trk_status st = mlp_ensure_tc(N, m_pad);
     if (st != TRK_OK) return st;
     TrainRes R;
     std::vector<float> c12(2 * total);
@@ -707,8 +551,7 @@ extern "C" trk_status trk_mlp_train(trk_mlp *N, const float *d_X, const float *d
         c12[2 * k] = 1.0f - powf(0.9f, t);
         c12[2 * k + 1] = 1.0f - powf(0.999f, t);
     }
-    cudaError_t e = cudaMalloc(&R.Xb, (size_t)b * kIn * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&R.yb, (size_t)b * sizeof(float));
+    cudaError_t e = cudaMalloc(&R.yb, (size_t)b * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&R.c12, c12.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&R.dstep, sizeof(int64_t));
     if (e != cudaSuccess) return mlp_fail(TRK_ENOMEM, "trk_mlp_train: allocation failed");
@@ -717,13 +560,14 @@ extern "C" trk_status trk_mlp_train(trk_mlp *N, const float *d_X, const float *d
     // order the private stream after the caller's work
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.c12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(R.dstep, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess) e = mlp_retile(N, s);   // the first step's products read the current weights
     if (e == cudaSuccess) e = cudaEventRecord(R.ev, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(R.ps, R.ev, 0);
     const int n_graphs = tail == b ? 1 : 2;
     for (int k = 0; k < n_graphs && e == cudaSuccess; ++k) {
         e = cudaStreamBeginCapture(R.ps, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) break;
-        cudaError_t ec = train_step(N, d_X, d_y, d_perm, n, b, spe, k == 0 ? b : tail, lr, R.c12, R.dstep, R.Xb,
+        cudaError_t ec = train_step(N, d_X, d_y, d_perm, n, b, spe, k == 0 ? b : tail, lr, R.c12, R.dstep,
                                     R.yb, d_loss_hist, R.ps);
         e = cudaStreamEndCapture(R.ps, &R.g[k]);
         if (ec != cudaSuccess) e = ec;
@@ -736,6 +580,13 @@ extern "C" trk_status trk_mlp_train(trk_mlp *N, const float *d_X, const float *d
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return mlp_fail(TRK_ECUDA, std::string("trk_mlp_train: ") + cudaGetErrorString(e));
     N->t += total;
+    int herr = 0;
+    if (cudaMemcpy(&herr, N->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return mlp_fail(TRK_ECUDA, "trk_mlp_train: error flag read failed");
+    if (herr) {
+        cudaMemset(N->d_err, 0, sizeof(int));
+        return mlp_fail(TRK_ETIMEOUT, "trk_mlp_train: a tensor-core product gave up waiting on a barrier");
+    }
     return TRK_OK;
 }
 

@@ -2,8 +2,9 @@
 //
 // One hidden layer is Out[M x 256] = bf16(gelu(A[M x K] W^T + b)) with BF16
 // A and W, FP32 accumulation in tensor memory (TMEM) and FP32 bias / GELU in
-// the epilogue: the same rounding points as the mma.sync layers, a different
-// FP32 summation order inside the products.
+// the epilogue: the rounding points of the oracle, with the tensor core's own
+// FP32 summation order inside the products.  The training products (forward,
+// input and weight gradients) are below, after the inference layer.
 //
 // Layout.  Activations and weights live in global memory in the layout the
 // MMA reads from shared memory (K-major, no swizzle): a matrix with R rows is
@@ -243,15 +244,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 }
 
 // ------------------------------------------------------------ training ----
-// One 128 x 64 output tile per CTA of D = A B^T, A [128 rows x K] and B [64
+// One 128 x TN output tile per CTA of D = A B^T, A [128 rows x K] and B [TN
 // rows x K] both K-major in the tiled layout above: chunk c of A's tile t is
-// the 16 KB block ((t * a_kc + c) * 128 * 64) elements in, and the 64-row slice
-// j of B's chunk c the contiguous 8 KB at ((c * b_rows + 64 j) * 64) (a 64-row
-// slice of a block covers 8 whole row groups).  The chunks [k0, k1) are copied
+// the 16 KB block ((t * a_kc + c) * 128 * 64) elements in, and the TN-row slice
+// j of B's chunk c the contiguous TN * 128 bytes at ((c * b_rows + TN j) * 64)
+// (a slice of a block covers TN / 8 whole row groups).  The chunks [k0, k1) are copied
 // to shared memory in groups of up to kGroupChunks (one mbarrier each group),
-// one thread issues the MMAs (M 128, N 64, K 16) into a 64-column TMEM
-// accumulator, and after the last commit the four warps read their TMEM lane
-// quadrant and apply the epilogue:
+// one thread issues the MMAs (M 128, N TN, K 16) into a TN-column TMEM
+// accumulator, and after the last commit eight warps (two per TMEM lane
+// quadrant, TN / 2 columns each) read the accumulator and apply the epilogue:
 //   kTrainFwd  z = acc + bias -> Z [M][256] FP32; h = bf16(gelu(z)) tiled (next
 //              layer's A, 128-row tiles, K 256), transposed-tiled (rows = the
 //              256 outputs, K = the batch: the weight gradient's B) and, when
@@ -260,11 +261,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 //              transposed-tiled with 128-row tiles (the next weight gradient's A)
 //   kTrainDw   acc -> part [z][256][b_n] FP32 (split z = blockIdx.z of the
 //              contraction over the batch; the caller sums the splits in order)
+// The forward and input-gradient products use 32-column tiles (256 CTAs for a
+// 4096-row batch), the weight gradients 64-column tiles over 8 batch splits.
 // Rows m >= M of the batch keep the zeros of padded inputs.
 enum { kTrainFwd = 0, kTrainDx = 1, kTrainDw = 2 };
-constexpr int TN = 64, kGroupChunks = 8;
-constexpr uint32_t kBSliceBytes = TN * KCH * 2;     // 8 KB
-constexpr uint32_t kIdesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+constexpr int kGroupChunks = 8;
+// instruction descriptor, kind::f16: D FP32, A and B BF16 K-major, N = n, M 128
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
 
 struct TrainTileArgs {
     const __nv_bfloat16 *A;
@@ -281,8 +286,9 @@ struct TrainTileArgs {
     __nv_bfloat16 *Hrm;      // fwd: optional row-major output
     int tt_rows;             // rows of HtT's tiles (256 fwd, 128 dx)
     int64_t m_kc;            // batch chunks (m_pad / 64) of the transposed layouts
-    float *part;             // dw
+    float *part;             // dw: split partials [z][256][b_n], summed in split order by the caller
     int *err;
+    int group;               // chunks per shared-memory group: min(cps, kGroupChunks)
 };
 
 __device__ __forceinline__ float gelu_grad_u(float z) {
@@ -294,13 +300,23 @@ __device__ __forceinline__ size_t tiled_at(int64_t r, int64_t k, int tr, int64_t
     return ((size_t)((r / tr) * kcn + (k >> 6)) * (tr >> 3) + (size_t)((r % tr) >> 3)) * 512 + (size_t)((k & 63) >> 3) * 64 +
            (size_t)(r & 7) * 8 + (size_t)(k & 7);
 }
+// The same for tiles of 2^tr_log2 rows given at run time (no integer division).
+__device__ __forceinline__ size_t tiled_at_pow2(int64_t r, int64_t k, int tr_log2, int64_t kcn) {
+    const int64_t tr = (int64_t)1 << tr_log2;
+    return ((size_t)((r >> tr_log2) * kcn + (k >> 6)) * (size_t)(tr >> 3) + (size_t)((r & (tr - 1)) >> 3)) * 512 +
+           (size_t)((k & 63) >> 3) * 64 + (size_t)(r & 7) * 8 + (size_t)(k & 7);
+}
 
-template <int MODE>
-__global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
+constexpr int kTrainThreads = 256;   // 8 warps: two per TMEM lane quadrant, 32 output columns each
+
+template <int MODE, int TN>
+__global__ void __launch_bounds__(kTrainThreads) k_train_tile(TrainTileArgs a) {
+    constexpr uint32_t kBSliceBytes = TN * KCH * 2;
+    constexpr int kCols = TN / 2;   // columns per warp (two warps per lane quadrant)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sA = base;
-    unsigned char *sB = sA + (size_t)kGroupChunks * kABlockBytes;
+    unsigned char *sB = sA + (size_t)a.group * kABlockBytes;
     __shared__ uint64_t full, done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -316,7 +332,8 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(su32(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "n"(TN < 32 ? 32 : TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -326,8 +343,8 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
     volatile int *abort = &abort_flag;
     bool ok = true;
     uint32_t phase = 0;
-    for (int g0 = c_beg; g0 < c_end && ok; g0 += kGroupChunks, phase ^= 1u) {
-        const int g1 = g0 + kGroupChunks < c_end ? g0 + kGroupChunks : c_end;
+    for (int g0 = c_beg; g0 < c_end && ok; g0 += a.group, phase ^= 1u) {
+        const int g1 = g0 + a.group < c_end ? g0 + a.group : c_end;
         if (threadIdx.x == 0) {
             mbar_expect_tx(&full, (uint32_t)(g1 - g0) * (kABlockBytes + kBSliceBytes));
             for (int c = g0; c < g1; ++c) {
@@ -348,7 +365,7 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
                         asm volatile(
                             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                            "l"(sdesc(a0 + kk * 256)), "l"(sdesc(b0 + kk * 256)), "r"(kIdesc64), "r"(acc)
+                            "l"(sdesc(a0 + kk * 256)), "l"(sdesc(b0 + kk * 256)), "r"(idesc_n(TN)), "r"(acc)
                             : "memory");
                     }
                 }
@@ -367,12 +384,19 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
         mbar_wait(&full, phase ^ 1u, &never);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (MODE == kTrainDw && !(c_beg < c_end)) {
+        // an empty split contributes zeros
+        const size_t ncol = (size_t)gridDim.y * TN;
+        for (int e = threadIdx.x; e < UM * TN; e += blockDim.x)
+            a.part[((size_t)z * 256 + (size_t)t * UM + e / TN) * ncol + (size_t)j * TN + e % TN] = 0.0f;
+    }
     if (ok && c_beg < c_end) {
-        const int row = warp * 32 + lane;   // TMEM lane = row of the tile
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const int quad = warp & 3;          // TMEM lane quadrant of this warp
+        const int row = quad * 32 + lane;   // TMEM lane = row of the tile
+        const int c0 = (warp >> 2) * kCols;   // this warp's kCols of the TN columns
+        uint32_t r[kCols];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
+        if constexpr (kCols == 32) {
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -382,65 +406,80 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int n0 = j * TN + c0;     // first output column of these 32
-            if (MODE == kTrainDw) {
-                // part [z][out row][in column], in columns = b_n = gridDim.y * 64
-                const size_t ncol = (size_t)gridDim.y * TN;
-                float4 *dst = reinterpret_cast<float4 *>(a.part + ((size_t)z * 256 + (size_t)t * UM + row) * ncol + n0);
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15])
+                : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int n0 = j * TN + c0;     // first output column of this warp's columns
+        if (MODE == kTrainDw) {
+            // part [z][out row][in column], in columns = b_n = gridDim.y * TN
+            const size_t ncol = (size_t)gridDim.y * TN;
+            float4 *dst = reinterpret_cast<float4 *>(a.part + ((size_t)z * 256 + (size_t)t * UM + row) * ncol + n0);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            for (int q = 0; q < kCols / 4; ++q)
+                dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                     __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        } else {
+            const int64_t m = t * UM + row;   // batch row
+            float v[kCols];
+            if (MODE == kTrainFwd) {
+                const float4 *bb = reinterpret_cast<const float4 *>(a.bias + n0);
+#pragma unroll
+                for (int q = 0; q < kCols / 4; ++q) {
+                    const float4 b4 = __ldg(bb + q);
+                    v[4 * q] = __uint_as_float(r[4 * q]) + b4.x;
+                    v[4 * q + 1] = __uint_as_float(r[4 * q + 1]) + b4.y;
+                    v[4 * q + 2] = __uint_as_float(r[4 * q + 2]) + b4.z;
+                    v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) + b4.w;
+                }
             } else {
-                const int64_t m = t * UM + row;   // batch row
-                float v[32];
-                if (MODE == kTrainFwd) {
+                const float4 *zin = reinterpret_cast<const float4 *>(a.Zin + (size_t)m * 256 + n0);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r[e]) + a.bias[n0 + e];
-                } else {
-                    const float4 *zin = reinterpret_cast<const float4 *>(a.Zin + (size_t)m * 256 + n0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 zz = zin[q];
-                        v[4 * q] = __uint_as_float(r[4 * q]) * gelu_grad_u(zz.x);
-                        v[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * gelu_grad_u(zz.y);
-                        v[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * gelu_grad_u(zz.z);
-                        v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * gelu_grad_u(zz.w);
-                    }
+                for (int q = 0; q < kCols / 4; ++q) {
+                    const float4 zz = zin[q];
+                    v[4 * q] = __uint_as_float(r[4 * q]) * gelu_grad_u(zz.x);
+                    v[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * gelu_grad_u(zz.y);
+                    v[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * gelu_grad_u(zz.z);
+                    v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * gelu_grad_u(zz.w);
                 }
-                float4 *zo = reinterpret_cast<float4 *>(a.Zout + (size_t)m * 256 + n0);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) zo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                // the BF16 values: bf16(gelu(z)) forward, bf16(dz) backward
-                uint32_t hv[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    hv[e] = MODE == kTrainFwd ? pack_bf16(gelu_u(v[2 * e]), gelu_u(v[2 * e + 1]))
-                                              : pack_bf16(v[2 * e], v[2 * e + 1]);
-                // tiled (128-row tiles, K 256): four 16-byte pieces of 8 columns
-#pragma unroll
-                for (int g = 0; g < 4; ++g)
-                    *reinterpret_cast<uint4 *>(a.Ht + tiled_at(m, n0 + 8 * g, UM, 4)) =
-                        make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
-                if (MODE == kTrainFwd && a.Hrm) {
-                    uint4 *hr = reinterpret_cast<uint4 *>(a.Hrm + (size_t)m * 256 + n0);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) hr[g] = make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
-                }
-                // transposed-tiled: element (n, m)
-                const uint16_t *h16 = reinterpret_cast<const uint16_t *>(hv);
-                uint16_t *tt = reinterpret_cast<uint16_t *>(a.HtT);
-#pragma unroll 8
-                for (int e = 0; e < 32; ++e) tt[tiled_at(n0 + e, m, a.tt_rows, a.m_kc)] = h16[e];
             }
+            float4 *zo = reinterpret_cast<float4 *>(a.Zout + (size_t)m * 256 + n0);
+#pragma unroll
+            for (int q = 0; q < kCols / 4; ++q) zo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            // the BF16 values: bf16(gelu(z)) forward, bf16(dz) backward
+            uint32_t hv[kCols / 2];
+#pragma unroll
+            for (int e = 0; e < kCols / 2; ++e)
+                hv[e] = MODE == kTrainFwd ? pack_bf16(gelu_u(v[2 * e]), gelu_u(v[2 * e + 1]))
+                                          : pack_bf16(v[2 * e], v[2 * e + 1]);
+            // tiled (128-row tiles, K 256): 16-byte pieces of 8 columns
+#pragma unroll
+            for (int g = 0; g < kCols / 8; ++g)
+                *reinterpret_cast<uint4 *>(a.Ht + tiled_at(m, n0 + 8 * g, UM, 4)) =
+                    make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
+            if (MODE == kTrainFwd && a.Hrm) {
+                uint4 *hr = reinterpret_cast<uint4 *>(a.Hrm + (size_t)m * 256 + n0);
+#pragma unroll
+                for (int g = 0; g < kCols / 8; ++g) hr[g] = make_uint4(hv[4 * g], hv[4 * g + 1], hv[4 * g + 2], hv[4 * g + 3]);
+            }
+            // transposed-tiled: element (n, m)
+            const uint16_t *h16 = reinterpret_cast<const uint16_t *>(hv);
+            uint16_t *tt = reinterpret_cast<uint16_t *>(a.HtT);
+            const int trl = a.tt_rows == 256 ? 8 : 7;
+#pragma unroll
+            for (int e = 0; e < kCols; ++e) tt[tiled_at_pow2(n0 + e, m, trl, a.m_kc)] = h16[e];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TN < 32 ? 32 : TN));
     }
     if (threadIdx.x == 0 && abort_flag) atomicExch(a.err, 1);
 }
@@ -448,15 +487,35 @@ __global__ void __launch_bounds__(128, 1) k_train_tile(TrainTileArgs a) {
 // Training inputs: x [M][8] FP32 -> h0 tiled (128-row tiles, K 64) and
 // transposed-tiled (one 64-row tile: the 64 padded features, K = the batch);
 // features 8..63 and rows >= M are zero.
+// With `step`, batch row m is row perm[e n + r0 + m] of X (identity without
+// perm), e = step / spe, r0 = (step % spe) batch, and its label goes to yb.
+struct TrainGather {
+    const int32_t *perm;
+    int64_t n, batch, spe;
+    const int64_t *step;
+    const float *y;
+    float *yb;
+};
 __global__ void k_train_input(const float *__restrict__ X, int64_t M, int64_t m_pad, __nv_bfloat16 *__restrict__ H0,
-                              __nv_bfloat16 *__restrict__ H0T) {
+                              __nv_bfloat16 *__restrict__ H0T, TrainGather gth) {
     const int64_t n = m_pad * 64;
     uint16_t *t = reinterpret_cast<uint16_t *>(H0T);
     uint16_t *h = reinterpret_cast<uint16_t *>(H0);
+    int64_t ep = 0, r0 = 0;
+    if (gth.step) {
+        const int64_t st = *gth.step;
+        ep = st / gth.spe;
+        r0 = (st % gth.spe) * gth.batch;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = i >> 6;
         const int f = (int)(i & 63);
-        const float v = (m < M && f < 8) ? X[m * 8 + f] : 0.0f;
+        int64_t row = m;
+        if (gth.step && m < M) {
+            row = gth.perm ? (int64_t)gth.perm[ep * gth.n + r0 + m] : r0 + m;
+            if (f == 0) gth.yb[m] = gth.y[row];
+        }
+        const float v = (m < M && f < 8) ? X[row * 8 + f] : 0.0f;
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
         const uint16_t u = *reinterpret_cast<const uint16_t *>(&b);
         h[tiled_at(m, f, UM, 1)] = u;
@@ -525,6 +584,61 @@ __global__ void k_retile_weights(RetileArgs r) {
         const uint16_t v = src[r.w_off[l] + e];
         wt[r.wt_off[l] + tiled_at(o, k, 256, K / 64)] = v;
         if (l >= 1) wtT[r.wtT_off[l] + tiled_at(k, o, 256, 4)] = v;
+    }
+}
+
+// One Adam step of the training graph on FP32 master weights (Kingma & Ba; the
+// bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t from the table c12 at
+// the device step counter), writing the BF16 copy and, for the hidden layers'
+// weights, their tiled copies (wt, and wtT = W^T for l >= 1); the last block
+// records the step's loss and advances the step counter.
+struct AdamStepArgs {
+    float *p, *m, *v;
+    const float *g;
+    __nv_bfloat16 *pb;
+    int64_t n;
+    float lr, b1, b2, eps;
+    const float *c12;
+    int64_t *step;
+    const float *loss;
+    float *loss_hist;
+    unsigned *ticket;
+    RetileArgs r;
+    size_t w_end[4];   // the weights of layer l are [w_off[l], w_end[l]) of the parameter array
+};
+__global__ void k_adam_step(AdamStepArgs a) {
+    __shared__ bool last;
+    const int64_t st = *a.step;
+    const float c1 = a.c12[2 * st], c2 = a.c12[2 * st + 1];
+    uint16_t *wt = reinterpret_cast<uint16_t *>(a.r.wt), *wtT = reinterpret_cast<uint16_t *>(a.r.wtT);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = a.g[i];
+        const float mi = a.b1 * a.m[i] + (1.0f - a.b1) * gi;
+        const float vi = a.b2 * a.v[i] + (1.0f - a.b2) * gi * gi;
+        a.m[i] = mi;
+        a.v[i] = vi;
+        const float w = a.p[i] - a.lr * (mi / c1) / (sqrtf(vi / c2) + a.eps);
+        a.p[i] = w;
+        const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+        a.pb[i] = wb;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if ((size_t)i >= a.r.w_off[l] && (size_t)i < a.w_end[l]) {
+                const int K = a.r.in_pad[l];
+                const int64_t e = (int64_t)((size_t)i - a.r.w_off[l]), o = e / K, k = e % K;
+                const uint16_t u = *reinterpret_cast<const uint16_t *>(&wb);
+                wt[a.r.wt_off[l] + tiled_at(o, k, 256, K / 64)] = u;
+                if (l >= 1) wtT[a.r.wtT_off[l] + tiled_at(k, o, 256, 4)] = u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        if (a.loss_hist) a.loss_hist[st] = *a.loss;
+        *a.step = st + 1;
+        *a.ticket = 0u;
     }
 }
 
@@ -645,9 +759,14 @@ cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_
     return cudaGetLastError();
 }
 
-size_t train_tile_smem(int chunks_per_cta) {
-    const int g = chunks_per_cta < kGroupChunks ? chunks_per_cta : kGroupChunks;
-    return 1024 + (size_t)kGroupChunks * kABlockBytes + (size_t)g * kBSliceBytes;
+constexpr int kTnAct = 32;   // output columns per CTA of the forward and input-gradient products
+constexpr int kTnDw = 64;    // the same of the weight gradients
+
+int train_group(int chunks_per_cta) { return chunks_per_cta < kGroupChunks ? chunks_per_cta : kGroupChunks; }
+
+size_t train_tile_smem(int chunks_per_cta, int tn) {
+    const int g = train_group(chunks_per_cta);
+    return 1024 + (size_t)g * (kABlockBytes + (size_t)tn * KCH * 2);
 }
 
 cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_tiled, const float *bias,
@@ -669,10 +788,12 @@ cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_t
     a.tt_rows = 256;
     a.m_kc = m_pad / KCH;
     a.err = d_err;
-    const size_t smem = train_tile_smem(a.cps);
-    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    a.group = train_group(a.cps);
+    const size_t smem = train_tile_smem(a.cps, kTnAct);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainFwd, kTnAct>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainFwd><<<dim3((unsigned)(m_pad / UM), 256 / TN, 1), 128, smem, s>>>(a);
+    k_train_tile<kTrainFwd, kTnAct><<<dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1), kTrainThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -693,10 +814,12 @@ cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled,
     a.tt_rows = UM;
     a.m_kc = m_pad / KCH;
     a.err = d_err;
-    const size_t smem = train_tile_smem(a.cps);
-    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    a.group = train_group(a.cps);
+    const size_t smem = train_tile_smem(a.cps, kTnAct);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDx, kTnAct>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainDx><<<dim3((unsigned)(m_pad / UM), 256 / TN, 1), 128, smem, s>>>(a);
+    k_train_tile<kTrainDx, kTnAct><<<dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1), kTrainThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -708,7 +831,7 @@ int train_dw_splits(int64_t m_pad) {
 
 cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in, int64_t m_pad, float *part,
                             int *d_err, cudaStream_t s) {
-    if (m_pad % UM || n_in % TN || n_in < TN || n_in > 256) return cudaErrorInvalidValue;
+    if (m_pad % UM || n_in % kTnDw || n_in < kTnDw || n_in > 256) return cudaErrorInvalidValue;
     TrainTileArgs a{};
     a.A = reinterpret_cast<const __nv_bfloat16 *>(dzb_T);
     a.a_kc = m_pad / KCH;
@@ -719,16 +842,21 @@ cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in
     a.cps = (a.kc + S - 1) / S;
     a.part = part;
     a.err = d_err;
-    const size_t smem = train_tile_smem(a.cps);
-    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    a.group = train_group(a.cps);
+    const size_t smem = train_tile_smem(a.cps, kTnDw);
+    cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDw, kTnDw>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainDw><<<dim3(256 / UM, (unsigned)(n_in / TN), (unsigned)S), 128, smem, s>>>(a);
+    k_train_tile<kTrainDw, kTnDw><<<dim3(256 / UM, (unsigned)(n_in / kTnDw), (unsigned)S), kTrainThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T, cudaStream_t s) {
+cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T,
+                               const int32_t *perm, int64_t n, int64_t batch, int64_t spe, const int64_t *step,
+                               const float *y, float *yb, cudaStream_t s) {
+    TrainGather g{perm, n, batch, spe, step, y, yb};
     k_train_input<<<grid_for(m_pad * 64), 256, 0, s>>>(X, M, m_pad, reinterpret_cast<__nv_bfloat16 *>(H0),
-                                                      reinterpret_cast<__nv_bfloat16 *>(H0T));
+                                                      reinterpret_cast<__nv_bfloat16 *>(H0T), g);
     return cudaGetLastError();
 }
 
@@ -755,6 +883,40 @@ cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const
     r.wt = reinterpret_cast<__nv_bfloat16 *>(wt);
     r.wtT = reinterpret_cast<__nv_bfloat16 *>(wtT);
     k_retile_weights<<<grid_for(256 * 64 + 3 * 256 * 256), 256, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint16_t *pb, int64_t n, float lr,
+                             const float *c12, int64_t *step, const float *loss, float *loss_hist, unsigned *ticket,
+                             const size_t *w_off, const size_t *w_end, const size_t *wt_off, const size_t *wtT_off,
+                             const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s) {
+    AdamStepArgs a;
+    a.p = p;
+    a.m = m;
+    a.v = v;
+    a.g = g;
+    a.pb = reinterpret_cast<__nv_bfloat16 *>(pb);
+    a.n = n;
+    a.lr = lr;
+    a.b1 = 0.9f;
+    a.b2 = 0.999f;
+    a.eps = 1e-8f;
+    a.c12 = c12;
+    a.step = step;
+    a.loss = loss;
+    a.loss_hist = loss_hist;
+    a.ticket = ticket;
+    a.r.pb = a.pb;
+    for (int l = 0; l < 4; ++l) {
+        a.r.w_off[l] = w_off[l];
+        a.w_end[l] = w_end[l];
+        a.r.wt_off[l] = wt_off[l];
+        a.r.wtT_off[l] = wtT_off[l];
+        a.r.in_pad[l] = in_pad[l];
+    }
+    a.r.wt = reinterpret_cast<__nv_bfloat16 *>(wt);
+    a.r.wtT = reinterpret_cast<__nv_bfloat16 *>(wtT);
+    k_adam_step<<<grid_for(n), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
