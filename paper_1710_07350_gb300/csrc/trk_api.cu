@@ -914,6 +914,15 @@ static trk_status track_parts(trk_bunch *const *P, int np, const trk_lattice *L,
                     g.do_moments = L->moments && s == ng;
                     g.p0c = p0;
                     g.ip0c = 1.0 / p0;
+                    {   // 1 / p0' after the segment's first RF cavities, as the kernel's p0 runs
+                        double pr = p0;
+                        g.n_rf_ip = 0;
+                        for (int e = e_start; e < e_first && g.n_rf_ip < 4; ++e)
+                            if (L->elems[e].type == TRK_RFCA) {
+                                pr = pr + L->elems[e].p[3];
+                                g.rf_ip[g.n_rf_ip++] = 1.0 / pr;
+                            }
+                    }
                     TRK_CUDA(track_launch(b, g, n_tiles[k]));
                 }
                 p0 = advance_p0(L, e_start, e_first, p0);

@@ -45,5 +45,93 @@ __device__ __forceinline__ void bin_consts(double dl, int nbins, double &rdl_s, 
     m = rdl_s < INFINITY ? (long long)((nbins + 2 + 31) / 32) + 1 : (1ll << 62);
 }
 
+// Integer estimate of the bin, for windows whose l values fit a 64-bit fixed
+// point: L = trunc(l 2^F) from l's bit pattern (|L| < 2^62 for every l of the
+// window, F = 62 - e with max(|lmin|, |lmax|) < 2^e), D = L - Lmin and
+// Q = D R / 2^P with R = 2^(44 - F + P) / dl truncated to a 64-bit integer in
+// [2^62, 2^63): Q estimates (l - lmin) / dl in units of 2^-44 of a bin.  In those
+// units the two truncations of L cost below 2 r (r = 2^(44 - F) / dl), R's
+// truncation below 1/2 (Q < 2^61) and the final shift below 1; the oracle's
+// rounded difference and quotient are within 2^-52 relative of the exact
+// quotient, below 2^8 units for up to 2^16 bins.  So where Q's fraction is more
+// than m = 2 r + 2^9 + 65 units from 0 and from 1, floor(Q 2^-44) is the
+// oracle's bin.  Only integer operations per particle.
+struct BinFast {
+    int F, P;
+    long long lmin_fix;
+    unsigned long long R, m;
+    bool on;
+};
+
+// trunc(l 2^F) from the bit pattern; `ok` false for inf/NaN or a value that
+// does not fit (never for l inside the window the constants were made for).
+__device__ __forceinline__ long long fix_of(double l, int F, bool &ok) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(l);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    ok = ex != 0x7FF;
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    int e = ex - 1075;                        // l = mant 2^e (with the hidden bit)
+    if (ex) mant |= 1ull << 52;
+    else e = -1074;
+    const int sh = e + F;
+    long long v;
+    if (sh >= 0) {
+        if (sh > 9) ok = false;               // 53 + 9 bits: no room left below 2^62
+        v = (long long)(mant << (sh > 9 ? 0 : sh));
+    } else {
+        v = sh <= -64 ? 0 : (long long)(mant >> -sh);
+    }
+    return (b >> 63) ? -v : v;
+}
+
+__device__ __forceinline__ BinFast bin_fast_consts(double lmin, double lmax, double dl, int nbins) {
+    BinFast c;
+    c.on = false;
+    c.F = 0;
+    c.P = 0;
+    c.lmin_fix = 0;
+    c.R = 0;
+    c.m = 0;
+    if (!(dl > 0.0) || nbins > 65536) return c;
+    const double big = fmax(fabs(lmin), fabs(lmax));
+    if (!(big > 0.0) || !isfinite(big)) return c;
+    int eb;
+    frexp(big, &eb);                          // big < 2^eb
+    c.F = 62 - eb;                            // |l| 2^F < 2^62
+    const double r = ldexp(1.0, 44 - c.F) / dl;
+    int er;
+    const double fr = frexp(r, &er);          // r = fr 2^er, fr in [0.5, 1)
+    c.P = 63 - er;                            // R = fr 2^63 in [2^62, 2^63)
+    if (c.P < 1 || c.P > 120 || !(r < 1e12)) return c;
+    c.R = (unsigned long long)ldexp(fr, 63);
+    bool ok;
+    c.lmin_fix = fix_of(lmin, c.F, ok);
+    if (!ok) return c;
+    c.m = (unsigned long long)(2.0 * r) + 512 + 64 + 1;
+    c.on = true;
+    return c;
+}
+
+// The oracle's bin of l: the integer estimate where it decides, else bin_of.
+__device__ __forceinline__ int bin_of_fast(double l, const BinFast &c, double lmin, double dl, double rdl_s,
+                                           long long m_exact, int nbins) {
+    if (c.on) {
+        bool ok;
+        const long long L = fix_of(l, c.F, ok);
+        const long long D = L - c.lmin_fix;
+        if (ok && D >= 0) {
+            const unsigned long long ud = (unsigned long long)D;
+            const unsigned long long hi = __umul64hi(ud, c.R), lo = ud * c.R;
+            const unsigned long long Q = c.P >= 64 ? (hi >> (c.P - 64)) : ((hi << (64 - c.P)) | (lo >> c.P));
+            const unsigned long long fr = Q & ((1ull << kBinFracBits) - 1);
+            const unsigned long long k = Q >> kBinFracBits;
+            if ((c.P < 64 ? (hi >> c.P) == 0 : true) && k < (unsigned long long)nbins && fr > c.m &&
+                fr < (1ull << kBinFracBits) - c.m)
+                return (int)k;
+        }
+    }
+    return bin_of(l, lmin, dl, rdl_s, m_exact, nbins);
+}
+
 }  // namespace
 }  // namespace trk

@@ -105,6 +105,11 @@ struct TrackArgs {
     int32_t n_tiles;        // stride of the partial-sum rows
     double p0c;             // reference momentum at element e0 [eV]
     double ip0c;            // 1 / p0c (computed on the host)
+    // n_turns == 1: 1 / p0' after the first n_rf_ip RF cavities of [e0, e1), in
+    // order, computed on the host from the same sums as the kernel's p0
+    double rf_ip[4];
+    int32_t n_rf_ip;
+    int32_t pad_rf;
     double *partials;       // [turn][tile][28]
     int32_t *tile_alive;    // alive count per tile at the end (may be null)
     const double *wake_V;   // voltages of the kicking wake
@@ -181,6 +186,29 @@ cudaError_t launch_umma_layer(const uint16_t *A_tiled, const uint16_t *W_tiled, 
                               int64_t n_tiles, uint16_t *out_tiled, int *d_err, cudaStream_t s);
 cudaError_t launch_to_tiled(const uint16_t *src, int64_t rows, int K, int tile_rows, uint16_t *dst, cudaStream_t s);
 cudaError_t launch_from_tiled(const uint16_t *src, int64_t rows, uint16_t *dst, cudaStream_t s);
+// Programmatic dependent launch for the training step's chain of small
+// kernels: a kernel launched by pdl_launch may be scheduled while the kernel
+// before it in the stream finishes; it must call pdl_wait() before it reads or
+// writes global memory that an earlier kernel of the stream uses, and it calls
+// pdl_trigger() to let the next kernel be scheduled in turn.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... Exp, typename... Act>
+cudaError_t pdl_launch(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Act &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Act &&>(args)...);
+}
+#endif
 // Training products on tcgen05 (trk_mlp_umma.cu): one output tile per CTA.
 cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_tiled, const float *bias,
                              int64_t m_pad, float *Z, uint16_t *Hout_tiled, uint16_t *Hout_T, uint16_t *Hout_rm,
@@ -195,9 +223,12 @@ cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in
 cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T,
                                const int32_t *perm, int64_t n, int64_t batch, int64_t spe, const int64_t *step,
                                const float *y, float *yb, cudaStream_t s);
-cudaError_t launch_train_head_back(const float *logit, const float *y, int64_t M, int64_t m_pad, const uint16_t *w5,
-                                   const float *Z4, float *dl, float *dz, uint16_t *dzb, uint16_t *dzbT,
-                                   float *loss_terms, cudaStream_t s);
+// Logits of the tiled last hidden layer and the head's backward step in one
+// launch (dlogit, dz_4 FP32 and its BF16 copy tiled and transposed-tiled,
+// the loss terms); rows [M, m_pad) get zeros.
+cudaError_t launch_train_head(const uint16_t *H4_tiled, const uint16_t *w5, const float *b5, const float *y,
+                              int64_t M, int64_t m_pad, const float *Z4, float *logit, float *dl, float *dz,
+                              uint16_t *dzb, uint16_t *dzbT, float *loss_terms, cudaStream_t s);
 cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint16_t *pb, int64_t n, float lr,
                              const float *c12, int64_t *step, const float *loss, float *loss_hist, unsigned *ticket,
                              const size_t *w_off, const size_t *w_end, const size_t *wt_off, const size_t *wtT_off,

@@ -22,6 +22,9 @@ namespace trk {
 namespace {
 
 constexpr int kIn = 8, kInPad = 64, kW = 256, kHidden = 4;  // inputs padded to one 64-wide tile
+// the backward pass's concurrent branches: the head's sums and each layer's
+// bias sums (kColSlots column sums in flight), each layer's weight gradient
+constexpr int kColSlots = kHidden + 1, kSide = 3, kEvents = 2 * kHidden + 4;
 
 // out[n] = sum_m A[m][n] (* w[m] if w): column sums over N = 256 columns in a
 // fixed order, FP32, in one launch: each of kColSlices blocks writes the partial
@@ -29,10 +32,13 @@ constexpr int kIn = 8, kInPad = 64, kW = 256, kHidden = 4;  // inputs padded to 
 // the next call) adds the partials in slice order, so the result does not
 // depend on which block came last.
 constexpr int kColSlices = 64;
+constexpr size_t kColSlot = kColSlices * kW + 4;   // partials and the ticket of one column sum
 __global__ void k_colsum(const float *__restrict__ A, const __nv_bfloat16 *__restrict__ Ab,
                          const float *__restrict__ w, int64_t M, float *part, unsigned *ticket,
                          float *__restrict__ out) {
     __shared__ bool last;
+    pdl_wait();
+    pdl_trigger();
     const int n = threadIdx.x;  // blockDim.x == kW
     const int64_t per = (M + kColSlices - 1) / kColSlices;
     const int64_t m0 = blockIdx.x * per, m1 = m0 + per < M ? m0 + per : M;
@@ -88,6 +94,8 @@ __global__ void k_colsum(const float *__restrict__ A, const __nv_bfloat16 *__res
 __global__ void k_sum2(const float *__restrict__ a0, const float *__restrict__ a1, int64_t n, float scale0,
                        float scale1, float *__restrict__ out0, float *__restrict__ out1) {
     __shared__ float sh[256];
+    pdl_wait();
+    pdl_trigger();
     const float *a = blockIdx.x ? a1 : a0;
     float s = 0.0f;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
@@ -102,6 +110,8 @@ __global__ void k_sum2(const float *__restrict__ a0, const float *__restrict__ a
 
 // out[i] = sum over slices s = 0, 1, ... of part[s * n + i], in slice order.
 __global__ void k_reduce_splits(const float *__restrict__ part, int splits, int64_t n, float *__restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         // up to 16 slices' loads in flight, added in slice order
         float a = 0.0f;
@@ -180,9 +190,14 @@ struct trk_mlp {
     // gradient chain, the transposed weight tiles and the split partials
     int64_t tc_cap = 0;
     uint16_t *Ht[kHidden + 1] = {}, *HT[kHidden + 1] = {}, *H4rm = nullptr;
-    float *Zt[kHidden] = {}, *tdz = nullptr, *tlogit = nullptr, *tdl = nullptr, *tloss_terms = nullptr;
-    uint16_t *dzbt[2] = {nullptr, nullptr}, *dzbT = nullptr;
-    float *tpart = nullptr;
+    // the gradient chain keeps one set per layer (dz FP32, its BF16 copy tiled
+    // and transposed-tiled, the weight-gradient split partials), so that each
+    // layer's weight and bias gradients run beside the next input gradient
+    float *Zt[kHidden] = {}, *tlogit = nullptr, *tdl = nullptr, *tloss_terms = nullptr;
+    float *tdz[kHidden] = {}, *tpart[kHidden] = {};
+    uint16_t *dzbt[kHidden] = {}, *dzbT[kHidden] = {};
+    cudaStream_t side[kSide] = {};  // the branches' streams (joined back before the step ends)
+    cudaEvent_t ev[kEvents] = {};
     unsigned *tickets = nullptr;   // [9]: the Adam step's block counter (zero between launches)
     uint16_t *wtT = nullptr;
     size_t wtT_off[kHidden] = {};
@@ -191,7 +206,11 @@ struct trk_mlp {
 static trk_status mlp_fail(trk_status s, const std::string &m) { return set_error(s, m); }
 
 // The column sums' ticket counter, kept after the partials (zero between calls).
-static unsigned *col_ticket(trk_mlp *N) { return reinterpret_cast<unsigned *>(N->part + kColSlices * kW); }
+// Column sums run concurrently, each with its own slot of partials and ticket.
+static float *col_part(trk_mlp *N, int slot) { return N->part + (size_t)slot * kColSlot; }
+static unsigned *col_ticket(trk_mlp *N, int slot) {
+    return reinterpret_cast<unsigned *>(col_part(N, slot) + kColSlices * kW);
+}
 
 static void mlp_free_tc(trk_mlp *N) {
     for (int l = 0; l <= kHidden; ++l) {
@@ -203,18 +222,21 @@ static void mlp_free_tc(trk_mlp *N) {
         cudaFree(N->Zt[l]);
         N->Zt[l] = nullptr;
     }
+    for (int l = 0; l < kHidden; ++l) {
+        cudaFree(N->tdz[l]);
+        cudaFree(N->tpart[l]);
+        cudaFree(N->dzbt[l]);
+        cudaFree(N->dzbT[l]);
+        N->tdz[l] = N->tpart[l] = nullptr;
+        N->dzbt[l] = N->dzbT[l] = nullptr;
+    }
     cudaFree(N->H4rm);
-    cudaFree(N->tdz);
     cudaFree(N->tlogit);
     cudaFree(N->tdl);
     cudaFree(N->tloss_terms);
-    cudaFree(N->dzbt[0]);
-    cudaFree(N->dzbt[1]);
-    cudaFree(N->dzbT);
-    cudaFree(N->tpart);
     cudaFree(N->tickets);
-    N->H4rm = N->dzbt[0] = N->dzbt[1] = N->dzbT = nullptr;
-    N->tdz = N->tlogit = N->tdl = N->tloss_terms = N->tpart = nullptr;
+    N->H4rm = nullptr;
+    N->tlogit = N->tdl = N->tloss_terms = nullptr;
     N->tickets = nullptr;
     N->tc_cap = 0;
 }
@@ -232,14 +254,16 @@ static trk_status mlp_ensure_tc(trk_mlp *N, int64_t rows) {
     }
     for (int l = 0; l < kHidden && e == cudaSuccess; ++l) e = cudaMalloc(&N->Zt[l], r * kW * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->H4rm, r * kW * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&N->tdz, r * kW * sizeof(float));
+    for (int l = 0; l < kHidden && e == cudaSuccess; ++l) {
+        e = cudaMalloc(&N->tdz[l], r * kW * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&N->dzbt[l], r * kW * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&N->dzbT[l], r * kW * sizeof(uint16_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&N->tpart[l], (size_t)train_dw_splits(rows) * kW * N->in_pad[l] * sizeof(float));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&N->tlogit, r * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->tdl, r * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->tloss_terms, r * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&N->dzbt[0], r * kW * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&N->dzbt[1], r * kW * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&N->dzbT, r * kW * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&N->tpart, (size_t)train_dw_splits(rows) * kW * kW * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->tickets, 16 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(N->tickets, 0, 16 * sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -281,8 +305,10 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
     if (e == cudaSuccess) e = cudaMalloc(&N->g, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&N->pb, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&N->loss, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&N->part, (kColSlices * kW + 4) * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(N->part + kColSlices * kW, 0, 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&N->part, kColSlots * kColSlot * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(N->part, 0, kColSlots * kColSlot * sizeof(float));
+    for (int k = 0; k < kSide && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&N->side[k], cudaStreamNonBlocking);
+    for (int k = 0; k < kEvents && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&N->ev[k], cudaEventDisableTiming);
     {
         size_t o = 0;
         for (int l = 0; l < kHidden; ++l) {
@@ -318,6 +344,10 @@ extern "C" trk_status trk_mlp_create(const float *const *host_W, const float *co
         cudaFree(N->wt);
         cudaFree(N->wtT);
         cudaFree(N->d_err);
+        for (int k = 0; k < kSide; ++k)
+            if (N->side[k]) cudaStreamDestroy(N->side[k]);
+        for (int k = 0; k < kEvents; ++k)
+            if (N->ev[k]) cudaEventDestroy(N->ev[k]);
         delete N;
         return mlp_fail(TRK_ENOMEM, std::string("trk_mlp_create: ") + cudaGetErrorString(e));
     }
@@ -341,6 +371,10 @@ extern "C" trk_status trk_mlp_destroy(trk_mlp *N) {
     cudaFree(N->act[0]);
     cudaFree(N->act[1]);
     mlp_free_tc(N);
+    for (int k = 0; k < kSide; ++k)
+        if (N->side[k]) cudaStreamDestroy(N->side[k]);
+    for (int k = 0; k < kEvents; ++k)
+        if (N->ev[k]) cudaEventDestroy(N->ev[k]);
     delete N;
     return TRK_OK;
 }
@@ -428,28 +462,58 @@ static cudaError_t mlp_grad_tc(trk_mlp *N, const float *X, const float *y, int64
         e = launch_train_fwd(N->Ht[l], N->in_pad[l], N->wt + N->wt_off[l], N->p + N->b_off[l], m_pad, N->Zt[l],
                              N->Ht[l + 1], N->HT[l + 1], l == kHidden - 1 ? N->H4rm : nullptr, N->d_err, s);
     if (e == cudaSuccess)
-        e = launch_head_tiled(N->Ht[kHidden], pb + N->w_off[4], N->p + N->b_off[4], M, N->tlogit, s);
-    if (e == cudaSuccess)
-        e = launch_train_head_back(N->tlogit, y, M, m_pad, pb + N->w_off[4], N->Zt[kHidden - 1], N->tdl, N->tdz,
-                                   N->dzbt[0], N->dzbT, N->tloss_terms, s);
-    if (e != cudaSuccess) return e;
-    k_colsum<<<kColSlices, kW, 0, s>>>(nullptr, reinterpret_cast<const __nv_bfloat16 *>(N->H4rm), N->tdl, M, N->part,
-                                       col_ticket(N), N->g + N->w_off[4]);
-    k_sum2<<<2, 256, 0, s>>>(N->tdl, N->tloss_terms, M, 1.0f, 1.0f / (float)M, N->g + N->b_off[4], N->loss);
-    int cur = 0;
+        e = launch_train_head(N->Ht[kHidden], pb + N->w_off[4], N->p + N->b_off[4], y, M, m_pad, N->Zt[kHidden - 1],
+                              N->tlogit, N->tdl, N->tdz[kHidden - 1], N->dzbt[kHidden - 1], N->dzbT[kHidden - 1],
+                              N->tloss_terms, s);
+    // The backward pass as a fork-join: the main stream runs the input
+    // gradients dx_3, dx_2, dx_1 (each writing its own layer's buffers); as soon
+    // as layer l's dz exists, side streams take its weight gradient (split
+    // products, then their sum in split order) and its bias column sums.  Each
+    // result has one writer and a fixed summation order, so the gradients are
+    // the same as in one stream.  Everything joins the main stream at the end.
+    int ev = 0;
+    auto fork = [&](cudaStream_t to) {
+        if (e == cudaSuccess) e = cudaEventRecord(N->ev[ev], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, N->ev[ev], 0);
+        ++ev;
+    };
+    cudaStream_t cs = N->side[0];   // column sums (head, then every layer's bias)
+    fork(cs);
+    if (e == cudaSuccess) {
+        e = pdl_launch(k_colsum, dim3(kColSlices), dim3(kW), 0, cs, (const float *)nullptr,
+                       reinterpret_cast<const __nv_bfloat16 *>(N->H4rm), (const float *)N->tdl, M,
+                       col_part(N, kHidden), col_ticket(N, kHidden), N->g + N->w_off[4]);
+        if (e == cudaSuccess)
+            e = pdl_launch(k_sum2, dim3(2), dim3(256), 0, cs, (const float *)N->tdl, (const float *)N->tloss_terms, M,
+                           1.0f, 1.0f / (float)M, N->g + N->b_off[4], N->loss);
+    }
     for (int l = kHidden - 1; l >= 0 && e == cudaSuccess; --l) {
         const int K = N->in_pad[l];
-        // dW_l: batch-split partials, summed in split order
-        e = launch_train_dw(N->dzbT, N->HT[l], K, m_pad, N->tpart, N->d_err, s);
+        // layer l's weight gradient on a side stream (layer 0's on the main
+        // stream, which has nothing else left); the fork's event marks dz_l as
+        // written, and the column-sum stream waits for it as well
+        cudaStream_t ws = l > 0 ? N->side[1 + (l & 1)] : s;
+        fork(l > 0 ? ws : cs);
+        if (l > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(cs, N->ev[ev - 1], 0);
         if (e != cudaSuccess) break;
-        k_reduce_splits<<<grid_for((int64_t)kW * K), 256, 0, s>>>(N->tpart, train_dw_splits(m_pad), (int64_t)kW * K,
-                                                                  N->g + N->w_off[l]);
-        k_colsum<<<kColSlices, kW, 0, s>>>(N->tdz, nullptr, nullptr, M, N->part, col_ticket(N), N->g + N->b_off[l]);
-        if (l > 0) {
-            e = launch_train_dx(N->dzbt[cur], N->wtT + N->wtT_off[l], N->Zt[l - 1], m_pad, N->tdz, N->dzbt[cur ^ 1],
-                                N->dzbT, N->d_err, s);
-            cur ^= 1;
-        }
+        e = launch_train_dw(N->dzbT[l], N->HT[l], K, m_pad, N->tpart[l], N->d_err, ws);
+        if (e != cudaSuccess) break;
+        e = pdl_launch(k_reduce_splits, dim3(grid_for((int64_t)kW * K)), dim3(256), 0, ws, (const float *)N->tpart[l],
+                       train_dw_splits(m_pad), (int64_t)kW * K, N->g + N->w_off[l]);
+        if (e == cudaSuccess)
+            e = pdl_launch(k_colsum, dim3(kColSlices), dim3(kW), 0, cs, (const float *)N->tdz[l],
+                           (const __nv_bfloat16 *)nullptr, (const float *)nullptr, M, col_part(N, l),
+                           col_ticket(N, l), N->g + N->b_off[l]);
+        if (e != cudaSuccess) break;
+        if (l > 0)
+            e = launch_train_dx(N->dzbt[l], N->wtT + N->wtT_off[l], N->Zt[l - 1], m_pad, N->tdz[l - 1],
+                                N->dzbt[l - 1], N->dzbT[l - 1], N->d_err, s);
+    }
+    // join: the main stream waits for every side stream
+    for (int k = 0; k < kSide; ++k) {
+        if (e == cudaSuccess) e = cudaEventRecord(N->ev[ev], N->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, N->ev[ev], 0);
+        ++ev;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -339,6 +339,10 @@ __global__ void __launch_bounds__(kTrainThreads) k_train_tile(TrainTileArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the set-up above overlaps the previous kernel of the stream; its outputs
+    // are read from here on
+    pdl_wait();
+    pdl_trigger();
     const uint32_t tmem = tmem_base;
     volatile int *abort = &abort_flag;
     bool ok = true;
@@ -498,6 +502,8 @@ struct TrainGather {
 };
 __global__ void k_train_input(const float *__restrict__ X, int64_t M, int64_t m_pad, __nv_bfloat16 *__restrict__ H0,
                               __nv_bfloat16 *__restrict__ H0T, TrainGather gth) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t n = m_pad * 64;
     uint16_t *t = reinterpret_cast<uint16_t *>(H0T);
     uint16_t *h = reinterpret_cast<uint16_t *>(H0);
@@ -523,36 +529,69 @@ __global__ void k_train_input(const float *__restrict__ X, int64_t M, int64_t m_
     }
 }
 
-// Head backward for the training step: dlogit = (sigmoid(logit) - y) / M and the
-// BCE terms (rows < M), dz4 = dlogit w5 gelu'(z4) -> FP32 [m_pad][256], BF16
-// tiled (128-row tiles, K 256) and transposed-tiled (128-row tiles over the 256
-// outputs, K = the batch); rows >= M are zero.
-__global__ void k_train_head_back(const float *__restrict__ logit, const float *__restrict__ y, int64_t M, int64_t m_pad,
-                                  const __nv_bfloat16 *__restrict__ w5, const float *__restrict__ Z4,
-                                  float *__restrict__ dl, float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
-                                  __nv_bfloat16 *__restrict__ dzbT, float *__restrict__ loss_terms) {
-    const int64_t n = m_pad * 256;
-    uint16_t *a = reinterpret_cast<uint16_t *>(dzb);
-    uint16_t *b = reinterpret_cast<uint16_t *>(dzbT);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i >> 8;
-        const int k = (int)(i & 255);
-        float d = 0.0f;
-        if (m < M) {
-            const float l = logit[m];
-            d = (1.0f / (1.0f + expf(-l)) - y[m]) / (float)M;
-            if (k == 0) {
-                dl[m] = d;
-                loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - y[m] * l;
-            }
+// The head and its backward step, a warp per row m < m_pad: lane l holds
+// the 8 columns k = 64 (l / 8) + 8 (l % 8) + e of the tiled h4 row; the logit
+// h4 . w5 + b5 is lane 0's sum after the xor butterfly (as k_head_tiled),
+// broadcast to the warp; dlogit = (sigmoid(logit) - y) / M; each lane then
+// writes dz = dlogit w5[k] gelu'(z4) for its columns (FP32, BF16 tiled as one
+// 16-byte store, BF16 transposed-tiled).  Rows m >= M take dz = 0.
+__global__ void k_train_head(const __nv_bfloat16 *__restrict__ H4, const __nv_bfloat16 *__restrict__ w5,
+                             const float *__restrict__ b5, const float *__restrict__ y, int64_t M, int64_t m_pad,
+                             const float *__restrict__ Z4, float *__restrict__ logit, float *__restrict__ dl,
+                             float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
+                             __nv_bfloat16 *__restrict__ dzbT, float *__restrict__ loss_terms) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (m >= m_pad) return;
+    const int c = lane >> 3, kg = lane & 7;
+    const int k0 = c * 64 + kg * 8;
+    const uint4 wv = *reinterpret_cast<const uint4 *>(w5 + k0);
+    const __nv_bfloat16 *w = reinterpret_cast<const __nv_bfloat16 *>(&wv);
+    float d = 0.0f;
+    if (m < M) {
+        const int64_t t = m / UM;
+        const int rr = (int)(m % UM);
+        const uint4 hv = *reinterpret_cast<const uint4 *>(H4 + (((size_t)t * 4 + c) * 16 + (rr >> 3)) * 8 * 64 +
+                                                          (size_t)kg * 64 + (rr & 7) * 8);
+        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&hv);
+        float s = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s += __bfloat162float(h[e]) * __bfloat162float(w[e]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float l = __shfl_sync(0xffffffffu, s, 0) + b5[0];
+        const float ym = y[m];
+        d = (1.0f / (1.0f + expf(-l)) - ym) / (float)M;
+        if (lane == 0) {
+            logit[m] = l;
+            dl[m] = d;
+            loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - ym * l;
         }
-        const float v = m < M ? d * __bfloat162float(w5[k]) * gelu_grad_u(Z4[i]) : 0.0f;
-        dz[i] = v;
-        const __nv_bfloat16 vb = __float2bfloat16_rn(v);
-        const uint16_t u = *reinterpret_cast<const uint16_t *>(&vb);
-        a[tiled_at(m, k, UM, 4)] = u;
-        b[tiled_at(k, m, UM, m_pad / 64)] = u;
     }
+    const float4 z0 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0);
+    const float4 z1 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0 + 4);
+    const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+    float v[8];
+    uint16_t u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        v[e] = m < M ? d * __bfloat162float(w[e]) * gelu_grad_u(z[e]) : 0.0f;
+        const __nv_bfloat16 vb = __float2bfloat16_rn(v[e]);
+        u[e] = *reinterpret_cast<const uint16_t *>(&vb);
+    }
+    *reinterpret_cast<float4 *>(dz + m * 256 + k0) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(dz + m * 256 + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    uint4 pk;
+    pk.x = (uint32_t)u[0] | ((uint32_t)u[1] << 16);
+    pk.y = (uint32_t)u[2] | ((uint32_t)u[3] << 16);
+    pk.z = (uint32_t)u[4] | ((uint32_t)u[5] << 16);
+    pk.w = (uint32_t)u[6] | ((uint32_t)u[7] << 16);
+    *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(dzb) + tiled_at(m, k0, UM, 4)) = pk;
+    uint16_t *b = reinterpret_cast<uint16_t *>(dzbT);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) b[tiled_at_pow2(k0 + e, m, 7, m_pad / 64)] = u[e];
 }
 
 // BF16 weights [out][in_pad] of the four hidden layers (at w_off[l] in pb) ->
@@ -608,6 +647,8 @@ struct AdamStepArgs {
 };
 __global__ void k_adam_step(AdamStepArgs a) {
     __shared__ bool last;
+    pdl_wait();
+    pdl_trigger();
     const int64_t st = *a.step;
     const float c1 = a.c12[2 * st], c2 = a.c12[2 * st + 1];
     uint16_t *wt = reinterpret_cast<uint16_t *>(a.r.wt), *wtT = reinterpret_cast<uint16_t *>(a.r.wtT);
@@ -793,8 +834,8 @@ cudaError_t launch_train_fwd(const uint16_t *H_tiled, int K, const uint16_t *W_t
     cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainFwd, kTnAct>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainFwd, kTnAct><<<dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1), kTrainThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_train_tile<kTrainFwd, kTnAct>, dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1),
+                      dim3(kTrainThreads), smem, s, a);
 }
 
 cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled, const float *Zin, int64_t m_pad,
@@ -819,8 +860,8 @@ cudaError_t launch_train_dx(const uint16_t *dzb_tiled, const uint16_t *WT_tiled,
     cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDx, kTnAct>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainDx, kTnAct><<<dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1), kTrainThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_train_tile<kTrainDx, kTnAct>, dim3((unsigned)(m_pad / UM), 256 / kTnAct, 1),
+                      dim3(kTrainThreads), smem, s, a);
 }
 
 int train_dw_splits(int64_t m_pad) {
@@ -847,27 +888,26 @@ cudaError_t launch_train_dw(const uint16_t *dzb_T, const uint16_t *H_T, int n_in
     cudaError_t e = cudaFuncSetAttribute(k_train_tile<kTrainDw, kTnDw>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_train_tile<kTrainDw, kTnDw><<<dim3(256 / UM, (unsigned)(n_in / kTnDw), (unsigned)S), kTrainThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_train_tile<kTrainDw, kTnDw>, dim3(256 / UM, (unsigned)(n_in / kTnDw), (unsigned)S),
+                      dim3(kTrainThreads), smem, s, a);
 }
 
 cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, uint16_t *H0T,
                                const int32_t *perm, int64_t n, int64_t batch, int64_t spe, const int64_t *step,
                                const float *y, float *yb, cudaStream_t s) {
     TrainGather g{perm, n, batch, spe, step, y, yb};
-    k_train_input<<<grid_for(m_pad * 64), 256, 0, s>>>(X, M, m_pad, reinterpret_cast<__nv_bfloat16 *>(H0),
-                                                      reinterpret_cast<__nv_bfloat16 *>(H0T), g);
-    return cudaGetLastError();
+    return pdl_launch(k_train_input, dim3(grid_for(m_pad * 64)), dim3(256), 0, s, X, M, m_pad,
+                      reinterpret_cast<__nv_bfloat16 *>(H0), reinterpret_cast<__nv_bfloat16 *>(H0T), g);
 }
 
-cudaError_t launch_train_head_back(const float *logit, const float *y, int64_t M, int64_t m_pad, const uint16_t *w5,
-                                   const float *Z4, float *dl, float *dz, uint16_t *dzb, uint16_t *dzbT,
-                                   float *loss_terms, cudaStream_t s) {
-    k_train_head_back<<<grid_for(m_pad * 256), 256, 0, s>>>(logit, y, M, m_pad,
-                                                           reinterpret_cast<const __nv_bfloat16 *>(w5), Z4, dl, dz,
-                                                           reinterpret_cast<__nv_bfloat16 *>(dzb),
-                                                           reinterpret_cast<__nv_bfloat16 *>(dzbT), loss_terms);
-    return cudaGetLastError();
+cudaError_t launch_train_head(const uint16_t *H4_tiled, const uint16_t *w5, const float *b5, const float *y,
+                              int64_t M, int64_t m_pad, const float *Z4, float *logit, float *dl, float *dz,
+                              uint16_t *dzb, uint16_t *dzbT, float *loss_terms, cudaStream_t s) {
+    const int rows_per_block = 8;
+    return pdl_launch(k_train_head, dim3((unsigned)((m_pad + rows_per_block - 1) / rows_per_block)),
+                      dim3(32 * rows_per_block), 0, s, reinterpret_cast<const __nv_bfloat16 *>(H4_tiled),
+                      reinterpret_cast<const __nv_bfloat16 *>(w5), b5, y, M, m_pad, Z4, logit, dl, dz,
+                      reinterpret_cast<__nv_bfloat16 *>(dzb), reinterpret_cast<__nv_bfloat16 *>(dzbT), loss_terms);
 }
 
 cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const size_t *wt_off, const size_t *wtT_off,
@@ -916,8 +956,7 @@ cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint1
     }
     a.r.wt = reinterpret_cast<__nv_bfloat16 *>(wt);
     a.r.wtT = reinterpret_cast<__nv_bfloat16 *>(wtT);
-    k_adam_step<<<grid_for(n), 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_adam_step, dim3(grid_for(n)), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_head_tiled(const uint16_t *H4, const uint16_t *w5, const float *b5, int64_t M, float *logit,

@@ -632,6 +632,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
     // element, the moments, loss records and the final store.
     bool canon = false;
     double p0 = a.p0c;  // reference momentum, identical in every thread
+    int n_rf = 0;       // RF cavities passed (for the host's reciprocals)
     for (int t = 0; t < a.n_turns; ++t) {
         const int turn = a.turn_abs0 + t;
         if (a.kick_wake >= 0) {
@@ -671,7 +672,10 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
             case TRK_SBEND: v_sbend<P>(q, E); break;
             case TRK_RFCA: {
                 const double p01 = p0 + __ldg(&E->p[3]);
-                v_rfca<P>(q, E, p0, 1.0 / p01, dirty);
+                // the host's reciprocal when it has one for this cavity (single-turn segments)
+                const double ip01 = n_rf < a.n_rf_ip ? a.rf_ip[n_rf] : 1.0 / p01;
+                ++n_rf;
+                v_rfca<P>(q, E, p0, ip01, dirty);
                 p0 = p01;
                 break;
             }

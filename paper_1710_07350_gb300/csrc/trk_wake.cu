@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kHistThreads = 512;
 constexpr int kSmemBins = 8192;      // sub-histograms in shared memory up to this many bins
+constexpr int kHistUnroll = 4;      // particles per thread and step of the histogram
 constexpr int kSubHists = 2;         // per block (one per half of the warps)
 constexpr int kConvOut = 16;         // outputs per convolution block
 constexpr int kConvThreads = 256;
@@ -74,14 +75,15 @@ __global__ void k_wake_minmax(const double *__restrict__ coords, int64_t pitch, 
     }
 }
 
-// Bin index exactly as floor((l - lmin) / dl) in IEEE double, clamped.
 // A finite offset in fixed point (round to nearest); a non-finite one carries no
 // dipole moment.
 __device__ __forceinline__ unsigned long long dipole_units(double x) {
     return isfinite(x) ? (unsigned long long)__double2ll_rn(x * kDipoleScale) : 0ull;
 }
 
-__global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__restrict__ coords, int64_t pitch,
+// kDip: the transverse sums are taken (dip != NULL).
+template <bool kDip>
+__global__ void __launch_bounds__(kHistThreads, 2) k_wake_hist(const double *__restrict__ coords, int64_t pitch,
                                                              const int32_t *__restrict__ lt, const BunchState *st,
                                                              WakeWindow *win, int slot, int which, int nbins,
                                                              double w0, double sc,
@@ -101,12 +103,13 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     double rdl_s;
     long long bin_m;
     bin_consts(dl, nbins, rdl_s, bin_m);
+    const BinFast bf = bin_fast_consts(lmin, lmax, dl, nbins);
     // wake function samples W(m dl) = w0 / sqrt(max(m dl, s_c))
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nbins; m += gridDim.x * blockDim.x) {
         const double s = (double)m * dl;
         const double r = sqrt(s > sc ? s : sc);
         wfun[m] = w0 / r;
-        if (dip) wfun_t[m] = w0t / r;
+        if (kDip) wfun_t[m] = w0t / r;
     }
     if (!any) return;
     const bool smem = use_smem != 0;
@@ -115,20 +118,19 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
     unsigned long long *shd = reinterpret_cast<unsigned long long *>(smem_raw + kSubHists * nbins * sizeof(uint32_t));
     if (smem) {
         for (int i = threadIdx.x; i < kSubHists * nbins; i += blockDim.x) sh[i] = 0u;
-        if (dip)
+        if (kDip)
             for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x) shd[i] = 0ull;
         __syncthreads();
     }
     uint32_t *mine = sh + ((threadIdx.x >> 5) % kSubHists) * nbins;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (lt[i] >= 0) continue;
-        const int b = bin_of(coords[4 * pitch + i], lmin, dl, rdl_s, bin_m, nbins);
+    auto add = [&](double l, double x, double y) {
+        const int b = bin_of_fast(l, bf, lmin, dl, rdl_s, bin_m, nbins);
         if (smem)
             atomicAdd(mine + b, 1u);
         else
             atomicAdd(hist + b, 1u);
-        if (dip) {
-            const unsigned long long ux = dipole_units(coords[i]), uy = dipole_units(coords[2 * pitch + i]);
+        if (kDip) {
+            const unsigned long long ux = dipole_units(x), uy = dipole_units(y);
             if (smem) {
                 atomicAdd(shd + b, ux);
                 atomicAdd(shd + nbins + b, uy);
@@ -137,7 +139,28 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
                 atomicAdd(dip + nbins + b, uy);
             }
         }
+    };
+    // U particles per thread and step, their loads issued together (the
+    // counts are integers: the order of the additions does not matter)
+    constexpr int U = kDip ? kHistUnroll / 2 : kHistUnroll;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < n; i += U * stride) {
+        int32_t lv[U];
+        double l[U], x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            lv[u] = lt[i + u * stride];
+            l[u] = coords[4 * pitch + i + u * stride];
+            x[u] = kDip ? coords[i + u * stride] : 0.0;
+            y[u] = kDip ? coords[2 * pitch + i + u * stride] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (lv[u] < 0) add(l[u], x[u], y[u]);
     }
+    for (; i < n; i += stride)
+        if (lt[i] < 0) add(coords[4 * pitch + i], kDip ? coords[i] : 0.0, kDip ? coords[2 * pitch + i] : 0.0);
     if (smem) {
         __syncthreads();
         for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
@@ -146,7 +169,7 @@ __global__ void __launch_bounds__(kHistThreads) k_wake_hist(const double *__rest
             for (int s = 0; s < kSubHists; ++s) c += sh[s * nbins + b];
             if (c) {
                 atomicAdd(hist + b, c);
-                if (dip) {
+                if (kDip) {
                     atomicAdd(dip + b, shd[b]);
                     atomicAdd(dip + nbins + b, shd[nbins + b]);
                 }
@@ -174,57 +197,77 @@ __device__ __forceinline__ double conv_block_sum(const double (&acc)[kConvOut], 
     return s;
 }
 
-// V_k = -q_m sum_{j <= k} h_j W((k - j) dl); a block owns kConvOut outputs and
-// its threads split the source bins.
+// Output chunk c (kConvOut outputs) costs in proportion to c + 1, so block b
+// takes chunks b and C - 1 - b (C chunks): every block does the same work.
+__device__ __forceinline__ int conv_chunk(int pass, int nbins) {
+    const int C = (nbins + kConvOut - 1) / kConvOut;
+    const int c = pass == 0 ? (int)blockIdx.x : C - 1 - (int)blockIdx.x;
+    return pass == 1 && c <= (int)blockIdx.x ? -1 : c;   // -1: no second chunk
+}
+
+int conv_blocks(int nbins) { return ((nbins + kConvOut - 1) / kConvOut + 1) / 2; }
+
+// V_k = -q_m sum_{j <= k} h_j W((k - j) dl); a chunk of kConvOut outputs per
+// pass, its source bins split over the block's threads.
 __global__ void __launch_bounds__(kConvThreads) k_wake_conv(const uint32_t *__restrict__ hist,
                                                              const double *__restrict__ wfun, int nbins, double qm,
                                                              double *__restrict__ V) {
     __shared__ double red[kConvThreads * kConvOut];
-    const int k0 = blockIdx.x * kConvOut;
-    const int kend = min(k0 + kConvOut, nbins);
-    double acc[kConvOut];
+    for (int pass = 0; pass < 2; ++pass) {
+        const int c = conv_chunk(pass, nbins);
+        if (c < 0) break;
+        const int k0 = c * kConvOut;
+        const int kend = min(k0 + kConvOut, nbins);
+        double acc[kConvOut];
 #pragma unroll
-    for (int i = 0; i < kConvOut; ++i) acc[i] = 0.0;
-    for (int j = threadIdx.x; j < kend; j += blockDim.x) {
-        const uint32_t hj = __ldg(hist + j);
-        if (hj == 0u) continue;
-        const double h = (double)hj;
+        for (int i = 0; i < kConvOut; ++i) acc[i] = 0.0;
+        for (int j = threadIdx.x; j < kend; j += blockDim.x) {
+            const uint32_t hj = __ldg(hist + j);
+            if (hj == 0u) continue;
+            const double h = (double)hj;
 #pragma unroll
-        for (int i = 0; i < kConvOut; ++i) {
-            const int k = k0 + i;
-            if (k >= j && k < kend) acc[i] = fma(h, __ldg(wfun + (k - j)), acc[i]);
+            for (int i = 0; i < kConvOut; ++i) {
+                const int k = k0 + i;
+                if (k >= j && k < kend) acc[i] = fma(h, __ldg(wfun + (k - j)), acc[i]);
+            }
         }
+        const double s = conv_block_sum(acc, red);
+        const int o = threadIdx.x >> 4;
+        if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[k0 + o] = -qm * s;
+        __syncthreads();   // red is reused by the second chunk
     }
-    const double s = conv_block_sum(acc, red);
-    const int o = threadIdx.x >> 4;
-    if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[k0 + o] = -qm * s;
 }
 
-// V_c[k] = q_m sum_{j <= k} D_c[j] W_T((k - j) dl), D in fixed point; blocks of
-// kConvOut outputs per coordinate (blockIdx.y = coordinate).
+// V_c[k] = q_m sum_{j <= k} D_c[j] W_T((k - j) dl), D in fixed point; chunks
+// as k_wake_conv per coordinate (blockIdx.y = coordinate).
 __global__ void __launch_bounds__(kConvThreads) k_wake_conv_t(const unsigned long long *__restrict__ dip,
                                                                const double *__restrict__ wfun_t, int nbins,
                                                                double qm, double *__restrict__ V) {
     __shared__ double red[kConvThreads * kConvOut];
     const unsigned long long *D = dip + (size_t)blockIdx.y * nbins;
-    const int k0 = blockIdx.x * kConvOut;
-    const int kend = min(k0 + kConvOut, nbins);
-    double acc[kConvOut];
+    for (int pass = 0; pass < 2; ++pass) {
+        const int c = conv_chunk(pass, nbins);
+        if (c < 0) break;
+        const int k0 = c * kConvOut;
+        const int kend = min(k0 + kConvOut, nbins);
+        double acc[kConvOut];
 #pragma unroll
-    for (int i = 0; i < kConvOut; ++i) acc[i] = 0.0;
-    for (int j = threadIdx.x; j < kend; j += blockDim.x) {
-        const long long dj = (long long)__ldg(D + j);
-        if (dj == 0) continue;
-        const double d = (double)dj * (1.0 / kDipoleScale);
+        for (int i = 0; i < kConvOut; ++i) acc[i] = 0.0;
+        for (int j = threadIdx.x; j < kend; j += blockDim.x) {
+            const long long dj = (long long)__ldg(D + j);
+            if (dj == 0) continue;
+            const double d = (double)dj * (1.0 / kDipoleScale);
 #pragma unroll
-        for (int i = 0; i < kConvOut; ++i) {
-            const int k = k0 + i;
-            if (k >= j && k < kend) acc[i] = fma(d, __ldg(wfun_t + (k - j)), acc[i]);
+            for (int i = 0; i < kConvOut; ++i) {
+                const int k = k0 + i;
+                if (k >= j && k < kend) acc[i] = fma(d, __ldg(wfun_t + (k - j)), acc[i]);
+            }
         }
+        const double s = conv_block_sum(acc, red);
+        const int o = threadIdx.x >> 4;
+        if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[(size_t)blockIdx.y * nbins + k0 + o] = qm * s;
+        __syncthreads();
     }
-    const double s = conv_block_sum(acc, red);
-    const int o = threadIdx.x >> 4;
-    if ((threadIdx.x & 15) == 0 && k0 + o < kend) V[(size_t)blockIdx.y * nbins + k0 + o] = qm * s;
 }
 
 // One block: line density, `passes` 1-2-1 smoothing passes, central
@@ -538,16 +581,23 @@ cudaError_t launch_wake_hist(const double *coords, int64_t pitch, const int32_t 
         const int most = kSubHists * (kSmemBins / 2) * (int)sizeof(uint32_t) +
                          2 * (kSmemBins / 2) * (int)sizeof(unsigned long long);
         const int plain = kSubHists * kSmemBins * (int)sizeof(uint32_t);
-        cudaError_t e = cudaFuncSetAttribute(k_wake_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_wake_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              most > plain ? most : plain);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_wake_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     most > plain ? most : plain);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     int g = grid_for(n_max, kHistThreads, 152 * 2);
     const int gw = (nbins + kHistThreads - 1) / kHistThreads;
     if (g < gw) g = gw;
-    k_wake_hist<<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, which, nbins, w0, sc, hist, wfun,
-                                              w0t, dip, wfun_t, smem_ok ? 1 : 0);
+    if (dip)
+        k_wake_hist<true><<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, which, nbins, w0, sc, hist,
+                                                        wfun, w0t, dip, wfun_t, smem_ok ? 1 : 0);
+    else
+        k_wake_hist<false><<<g, kHistThreads, smem, s>>>(coords, pitch, lt, st, win, slot, which, nbins, w0, sc, hist,
+                                                         wfun, w0t, dip, wfun_t, smem_ok ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -600,13 +650,13 @@ cudaError_t launch_lsc_imp(const uint32_t *hist, const BunchState *st, int slot,
 
 cudaError_t launch_wake_conv_t(const unsigned long long *dip, const double *wfun_t, int nbins, double qm, double *V,
                                cudaStream_t s) {
-    k_wake_conv_t<<<dim3((nbins + kConvOut - 1) / kConvOut, 2), kConvThreads, 0, s>>>(dip, wfun_t, nbins, qm, V);
+    k_wake_conv_t<<<dim3(conv_blocks(nbins), 2), kConvThreads, 0, s>>>(dip, wfun_t, nbins, qm, V);
     return cudaGetLastError();
 }
 
 cudaError_t launch_wake_conv(const uint32_t *hist, const double *wfun, int nbins, double qm, double *V,
                              cudaStream_t s) {
-    k_wake_conv<<<(nbins + kConvOut - 1) / kConvOut, kConvThreads, 0, s>>>(hist, wfun, nbins, qm, V);
+    k_wake_conv<<<conv_blocks(nbins), kConvThreads, 0, s>>>(hist, wfun, nbins, qm, V);
     return cudaGetLastError();
 }
 

@@ -180,14 +180,25 @@ def test_space_charge_impedance_rejects_bad_parameters(bad):
         trk.trk_create_lattice({"elements": [sc], "aperture": None, "p0c": 1e8})
 
 
-def test_wake_histogram_on_and_next_to_bin_edges():
-    """Particles placed on the bin edges and one ulp either side (where the
-    division-free bin index defers to the division): counts bit-exact."""
-    nb = 1000
-    lmin, lmax = -1.234e-4, 3.21e-4
+@pytest.mark.parametrize("lmin,lmax,nb", [
+    (-1.234e-4, 3.21e-4, 1000),      # a window about zero
+    (0.75, 0.75 + 2.5e-5, 4096),     # a narrow window far from zero (fixed point set by |l| ~ 1)
+    (-3.0e2, -2.9999e2, 777),        # negative, far from zero, odd bin count
+    (1e-300, 7e-300, 64),            # tiny magnitudes
+    (-5e-3, 5e-3, 65536),            # the largest bin count of the integer path
+    (1e6, 1e6 + 1e-3, 4096),         # bins about 2000 units of rounding of l wide
+    (2.0, 2.0 + 2.0 ** -40, 16),     # bins a few units of rounding wide
+])
+def test_wake_histogram_on_and_next_to_bin_edges(lmin, lmax, nb):
+    """Particles placed on the bin edges and one ulp either side (where both
+    division-free bin indices defer to the division), plus uniform particles:
+    counts bit-exact for windows near and far from zero, tiny and wide."""
     dl = (lmax - lmin) / nb
-    edges = lmin + np.arange(nb + 1) * dl
-    l = np.concatenate([edges, np.nextafter(edges, np.inf), np.nextafter(edges, -np.inf), [lmin, lmax]])
+    k = np.arange(nb + 1) if nb <= 5000 else np.random.default_rng(3).integers(0, nb + 1, 5000)
+    edges = lmin + k * dl
+    rng = np.random.default_rng(nb)
+    l = np.concatenate([edges, np.nextafter(edges, np.inf), np.nextafter(edges, -np.inf),
+                        rng.uniform(lmin, lmax, 20000), [lmin, lmax]])
     z = np.zeros((l.size, 6))
     z[:, 4] = np.clip(l, lmin, lmax)
     g, gh, gV = gpu_wake(z, nb, syn.C3_W0, syn.C3_SC, syn.C3_CHARGE, 2.0e9)
