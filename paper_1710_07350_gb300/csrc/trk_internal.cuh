@@ -229,10 +229,14 @@ cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_
 cudaError_t launch_train_head(const uint16_t *H4_tiled, const uint16_t *w5, const float *b5, const float *y,
                               int64_t M, int64_t m_pad, const float *Z4, float *logit, float *dl, float *dz,
                               uint16_t *dzb, uint16_t *dzbT, float *loss_terms, cudaStream_t s);
-cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint16_t *pb, int64_t n, float lr,
+// Adam on the FP32 master weights with the BF16 and tiled weight copies and
+// the device step counter; with wpart, the hidden layers' weight gradients are
+// summed from their batch-split partials (in split order) and stored to g.
+cudaError_t launch_adam_step(float *p, float *m, float *v, float *g, uint16_t *pb, int64_t n, float lr,
                              const float *c12, int64_t *step, const float *loss, float *loss_hist, unsigned *ticket,
                              const size_t *w_off, const size_t *w_end, const size_t *wt_off, const size_t *wtT_off,
-                             const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s);
+                             const int *in_pad, uint16_t *wt, uint16_t *wtT, const float *const *wpart, int splits,
+                             cudaStream_t s);
 cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const size_t *wt_off, const size_t *wtT_off,
                                   const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s);
 cudaError_t launch_input_tiled(const float *X, int64_t M, int64_t m_pad, uint16_t *H0, cudaStream_t s);

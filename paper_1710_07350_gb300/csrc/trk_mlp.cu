@@ -451,8 +451,11 @@ struct GatherRows {
     const float *y_all = nullptr;
 };
 
+// With sums_in_adam the first layer's weight gradient stays as split partials
+// (N->tpart[0]) for the Adam step to sum: its product is the last of the
+// backward pass, so its sum would otherwise be one more launch before Adam.
 static cudaError_t mlp_grad_tc(trk_mlp *N, const float *X, const float *y, int64_t M, cudaStream_t s,
-                               const GatherRows &gr = GatherRows()) {
+                               const GatherRows &gr = GatherRows(), bool sums_in_adam = false) {
     const int64_t m_pad = (M + 127) / 128 * 128;
     const uint16_t *pb = reinterpret_cast<const uint16_t *>(N->pb);
     // with a gather, y is the batch's label buffer that the input kernel fills
@@ -498,8 +501,9 @@ static cudaError_t mlp_grad_tc(trk_mlp *N, const float *X, const float *y, int64
         if (e != cudaSuccess) break;
         e = launch_train_dw(N->dzbT[l], N->HT[l], K, m_pad, N->tpart[l], N->d_err, ws);
         if (e != cudaSuccess) break;
-        e = pdl_launch(k_reduce_splits, dim3(grid_for((int64_t)kW * K)), dim3(256), 0, ws, (const float *)N->tpart[l],
-                       train_dw_splits(m_pad), (int64_t)kW * K, N->g + N->w_off[l]);
+        if (!(sums_in_adam && l == 0))
+            e = pdl_launch(k_reduce_splits, dim3(grid_for((int64_t)kW * K)), dim3(256), 0, ws,
+                           (const float *)N->tpart[l], train_dw_splits(m_pad), (int64_t)kW * K, N->g + N->w_off[l]);
         if (e == cudaSuccess)
             e = pdl_launch(k_colsum, dim3(kColSlices), dim3(kW), 0, cs, (const float *)N->tdz[l],
                            (const __nv_bfloat16 *)nullptr, (const float *)nullptr, M, col_part(N, l),
@@ -557,15 +561,16 @@ cudaError_t train_step(trk_mlp *N, const float *d_X, const float *d_y, const int
     gr.spe = spe;
     gr.step = dstep;
     gr.y_all = d_y;
-    cudaError_t e = mlp_grad_tc(N, d_X, yb, m, s, gr);
+    cudaError_t e = mlp_grad_tc(N, d_X, yb, m, s, gr, true);
     if (e != cudaSuccess) return e;
     // Adam, the tiled weight copies for the next step and the step counter in one launch
     size_t w_end[kHidden];
     for (int l = 0; l < kHidden; ++l) w_end[l] = N->b_off[l];
     const int in_pad[kHidden] = {N->in_pad[0], N->in_pad[1], N->in_pad[2], N->in_pad[3]};
+    const float *first_part[kHidden] = {N->tpart[0], nullptr, nullptr, nullptr};
     e = launch_adam_step(N->p, N->m, N->v, N->g, reinterpret_cast<uint16_t *>(N->pb), (int64_t)N->n_par, lr, c12, dstep,
                          N->loss, d_loss_hist, N->tickets + 9, N->w_off, w_end, N->wt_off, N->wtT_off, in_pad, N->wt,
-                         N->wtT, s);
+                         N->wtT, first_part, train_dw_splits((m + 127) / 128 * 128), s);
     return e;
 }
 

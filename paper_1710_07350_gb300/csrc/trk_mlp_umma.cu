@@ -529,69 +529,98 @@ __global__ void k_train_input(const float *__restrict__ X, int64_t M, int64_t m_
     }
 }
 
-// The head and its backward step, a warp per row m < m_pad: lane l holds
-// the 8 columns k = 64 (l / 8) + 8 (l % 8) + e of the tiled h4 row; the logit
-// h4 . w5 + b5 is lane 0's sum after the xor butterfly (as k_head_tiled),
-// broadcast to the warp; dlogit = (sigmoid(logit) - y) / M; each lane then
-// writes dz = dlogit w5[k] gelu'(z4) for its columns (FP32, BF16 tiled as one
-// 16-byte store, BF16 transposed-tiled).  Rows m >= M take dz = 0.
-__global__ void k_train_head(const __nv_bfloat16 *__restrict__ H4, const __nv_bfloat16 *__restrict__ w5,
-                             const float *__restrict__ b5, const float *__restrict__ y, int64_t M, int64_t m_pad,
-                             const float *__restrict__ Z4, float *__restrict__ logit, float *__restrict__ dl,
-                             float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
-                             __nv_bfloat16 *__restrict__ dzbT, float *__restrict__ loss_terms) {
+// The head and its backward step, 16 rows per block (8 warps, 2 rows each):
+// for row m, lane l holds the 8 columns k = 64 (l / 8) + 8 (l % 8) + e of the
+// tiled h4 row; the logit h4 . w5 + b5 is lane 0's sum after the xor butterfly
+// (as k_head_tiled), broadcast to the warp; dlogit = (sigmoid(logit) - y) / M;
+// dz = dlogit w5[k] gelu'(z4) goes out as FP32 and BF16 tiled, and the BF16
+// values through shared memory to the transposed-tiled copy as 16-byte
+// pieces of 8 rows of one column (8 consecutive threads write 128 B).
+// Rows m >= M take dz = 0.
+constexpr int kHeadRows = 16;
+constexpr int kHeadLd = 264;   // shared row length in BF16 (528 B: 8 rows of one column fall in distinct banks)
+__global__ void __launch_bounds__(256) k_train_head(const __nv_bfloat16 *__restrict__ H4,
+                                                    const __nv_bfloat16 *__restrict__ w5,
+                                                    const float *__restrict__ b5, const float *__restrict__ y,
+                                                    int64_t M, int64_t m_pad, const float *__restrict__ Z4,
+                                                    float *__restrict__ logit, float *__restrict__ dl,
+                                                    float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
+                                                    __nv_bfloat16 *__restrict__ dzbT, float *__restrict__ loss_terms) {
+    __shared__ __align__(16) uint16_t S[kHeadRows * kHeadLd];
     pdl_wait();
     pdl_trigger();
-    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (m >= m_pad) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * kHeadRows;
     const int c = lane >> 3, kg = lane & 7;
     const int k0 = c * 64 + kg * 8;
     const uint4 wv = *reinterpret_cast<const uint4 *>(w5 + k0);
     const __nv_bfloat16 *w = reinterpret_cast<const __nv_bfloat16 *>(&wv);
-    float d = 0.0f;
-    if (m < M) {
-        const int64_t t = m / UM;
-        const int rr = (int)(m % UM);
-        const uint4 hv = *reinterpret_cast<const uint4 *>(H4 + (((size_t)t * 4 + c) * 16 + (rr >> 3)) * 8 * 64 +
-                                                          (size_t)kg * 64 + (rr & 7) * 8);
-        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&hv);
-        float s = 0.0f;
+    const float bias = b5[0];
+    constexpr int R = kHeadRows / 8;   // rows per warp
+    float d[R], z[R][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) s += __bfloat162float(h[e]) * __bfloat162float(w[e]);
+    for (int i = 0; i < R; ++i) {
+        const int64_t m = m0 + warp * R + i;
+        const float4 z0 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0);
+        const float4 z1 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0 + 4);
+        z[i][0] = z0.x; z[i][1] = z0.y; z[i][2] = z0.z; z[i][3] = z0.w;
+        z[i][4] = z1.x; z[i][5] = z1.y; z[i][6] = z1.z; z[i][7] = z1.w;
+        d[i] = 0.0f;
+        if (m < M) {
+            const int64_t t = m / UM;
+            const int rr = (int)(m % UM);
+            const uint4 hv = *reinterpret_cast<const uint4 *>(H4 + (((size_t)t * 4 + c) * 16 + (rr >> 3)) * 8 * 64 +
+                                                              (size_t)kg * 64 + (rr & 7) * 8);
+            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&hv);
+            float s = 0.0f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const float l = __shfl_sync(0xffffffffu, s, 0) + b5[0];
-        const float ym = y[m];
-        d = (1.0f / (1.0f + expf(-l)) - ym) / (float)M;
-        if (lane == 0) {
-            logit[m] = l;
-            dl[m] = d;
-            loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - ym * l;
+            for (int e = 0; e < 8; ++e) s += __bfloat162float(h[e]) * __bfloat162float(w[e]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const float l = __shfl_sync(0xffffffffu, s, 0) + bias;
+            const float ym = y[m];
+            d[i] = (1.0f / (1.0f + expf(-l)) - ym) / (float)M;
+            if (lane == 0) {
+                logit[m] = l;
+                dl[m] = d[i];
+                loss_terms[m] = fmaxf(l, 0.0f) + log1pf(expf(-fabsf(l))) - ym * l;
+            }
         }
     }
-    const float4 z0 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0);
-    const float4 z1 = *reinterpret_cast<const float4 *>(Z4 + m * 256 + k0 + 4);
-    const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-    float v[8];
-    uint16_t u[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        v[e] = m < M ? d * __bfloat162float(w[e]) * gelu_grad_u(z[e]) : 0.0f;
-        const __nv_bfloat16 vb = __float2bfloat16_rn(v[e]);
-        u[e] = *reinterpret_cast<const uint16_t *>(&vb);
+    for (int i = 0; i < R; ++i) {
+        const int rl = warp * R + i;   // row within the block
+        const int64_t m = m0 + rl;
+        float v[8];
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = m < M ? d[i] * __bfloat162float(w[e]) * gelu_grad_u(z[i][e]) : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pk[e] = pack_bf16(v[2 * e], v[2 * e + 1]);
+        *reinterpret_cast<float4 *>(dz + m * 256 + k0) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(dz + m * 256 + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        const uint4 p4 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(dzb) + tiled_at(m, k0, UM, 4)) = p4;
+        *reinterpret_cast<uint4 *>(S + rl * kHeadLd + k0) = p4;
     }
-    *reinterpret_cast<float4 *>(dz + m * 256 + k0) = make_float4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<float4 *>(dz + m * 256 + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-    uint4 pk;
-    pk.x = (uint32_t)u[0] | ((uint32_t)u[1] << 16);
-    pk.y = (uint32_t)u[2] | ((uint32_t)u[3] << 16);
-    pk.z = (uint32_t)u[4] | ((uint32_t)u[5] << 16);
-    pk.w = (uint32_t)u[6] | ((uint32_t)u[7] << 16);
-    *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(dzb) + tiled_at(m, k0, UM, 4)) = pk;
-    uint16_t *b = reinterpret_cast<uint16_t *>(dzbT);
+    __syncthreads();
+    // transposed-tiled: element (k, m) of the 256 x m_pad matrix in 128-row
+    // tiles over k; piece q holds rows m0 + 8 g .. + 7 of column k
+    uint16_t *bT = reinterpret_cast<uint16_t *>(dzbT);
+    const int64_t kcn = m_pad / 64;
+    constexpr int G = kHeadRows / 8;   // pieces per column
+    for (int q = threadIdx.x; q < 256 * G; q += blockDim.x) {
+        const int k = ((q / (8 * G)) << 3) | (q & 7);
+        const int g = (q >> 3) % G;
+        uint16_t u[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) b[tiled_at_pow2(k0 + e, m, 7, m_pad / 64)] = u[e];
+        for (int r = 0; r < 8; ++r) u[r] = S[(g * 8 + r) * kHeadLd + k];
+        const size_t at = (((size_t)(k >> 7) * kcn + (size_t)(m0 >> 6)) * 16 + (size_t)((k & 127) >> 3)) * 512 +
+                          (size_t)(((m0 & 63) >> 3) + g) * 64 + (size_t)(k & 7) * 8;
+        *reinterpret_cast<uint4 *>(bT + at) =
+            make_uint4((uint32_t)u[0] | ((uint32_t)u[1] << 16), (uint32_t)u[2] | ((uint32_t)u[3] << 16),
+                       (uint32_t)u[4] | ((uint32_t)u[5] << 16), (uint32_t)u[6] | ((uint32_t)u[7] << 16));
+    }
 }
 
 // BF16 weights [out][in_pad] of the four hidden layers (at w_off[l] in pb) ->
@@ -633,7 +662,7 @@ __global__ void k_retile_weights(RetileArgs r) {
 // records the step's loss and advances the step counter.
 struct AdamStepArgs {
     float *p, *m, *v;
-    const float *g;
+    float *g;
     __nv_bfloat16 *pb;
     int64_t n;
     float lr, b1, b2, eps;
@@ -644,6 +673,10 @@ struct AdamStepArgs {
     unsigned *ticket;
     RetileArgs r;
     size_t w_end[4];   // the weights of layer l are [w_off[l], w_end[l]) of the parameter array
+    // with wpart[l], layer l's weight gradient is the sum of its `splits`
+    // batch-split partials (each [256][in_pad], in split order), also stored to g
+    const float *wpart[4];
+    int splits;
 };
 __global__ void k_adam_step(AdamStepArgs a) {
     __shared__ bool last;
@@ -653,7 +686,21 @@ __global__ void k_adam_step(AdamStepArgs a) {
     const float c1 = a.c12[2 * st], c2 = a.c12[2 * st + 1];
     uint16_t *wt = reinterpret_cast<uint16_t *>(a.r.wt), *wtT = reinterpret_cast<uint16_t *>(a.r.wtT);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = a.g[i];
+        int l = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if ((size_t)i >= a.r.w_off[q] && (size_t)i < a.w_end[q]) l = q;
+        const int64_t e = l >= 0 ? (int64_t)((size_t)i - a.r.w_off[l]) : 0;
+        float gi;
+        if (l >= 0 && a.wpart[l]) {
+            const float *wp = a.wpart[l];
+            const int64_t len = (int64_t)(a.w_end[l] - a.r.w_off[l]);
+            gi = wp[e];
+            for (int z = 1; z < a.splits; ++z) gi = gi + wp[(int64_t)z * len + e];
+            a.g[i] = gi;
+        } else {
+            gi = a.g[i];
+        }
         const float mi = a.b1 * a.m[i] + (1.0f - a.b1) * gi;
         const float vi = a.b2 * a.v[i] + (1.0f - a.b2) * gi * gi;
         a.m[i] = mi;
@@ -662,15 +709,12 @@ __global__ void k_adam_step(AdamStepArgs a) {
         a.p[i] = w;
         const __nv_bfloat16 wb = __float2bfloat16_rn(w);
         a.pb[i] = wb;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            if ((size_t)i >= a.r.w_off[l] && (size_t)i < a.w_end[l]) {
-                const int K = a.r.in_pad[l];
-                const int64_t e = (int64_t)((size_t)i - a.r.w_off[l]), o = e / K, k = e % K;
-                const uint16_t u = *reinterpret_cast<const uint16_t *>(&wb);
-                wt[a.r.wt_off[l] + tiled_at(o, k, 256, K / 64)] = u;
-                if (l >= 1) wtT[a.r.wtT_off[l] + tiled_at(k, o, 256, 4)] = u;
-            }
+        if (l >= 0) {
+            const int K = a.r.in_pad[l];
+            const int64_t o = e / K, k = e % K;
+            const uint16_t u = *reinterpret_cast<const uint16_t *>(&wb);
+            wt[a.r.wt_off[l] + tiled_at(o, k, 256, K / 64)] = u;
+            if (l >= 1) wtT[a.r.wtT_off[l] + tiled_at(k, o, 256, 4)] = u;
         }
     }
     __syncthreads();
@@ -903,9 +947,8 @@ cudaError_t launch_train_input(const float *X, int64_t M, int64_t m_pad, uint16_
 cudaError_t launch_train_head(const uint16_t *H4_tiled, const uint16_t *w5, const float *b5, const float *y,
                               int64_t M, int64_t m_pad, const float *Z4, float *logit, float *dl, float *dz,
                               uint16_t *dzb, uint16_t *dzbT, float *loss_terms, cudaStream_t s) {
-    const int rows_per_block = 8;
-    return pdl_launch(k_train_head, dim3((unsigned)((m_pad + rows_per_block - 1) / rows_per_block)),
-                      dim3(32 * rows_per_block), 0, s, reinterpret_cast<const __nv_bfloat16 *>(H4_tiled),
+    if (m_pad % kHeadRows) return cudaErrorInvalidValue;
+    return pdl_launch(k_train_head, dim3((unsigned)(m_pad / kHeadRows)), dim3(256), 0, s, reinterpret_cast<const __nv_bfloat16 *>(H4_tiled),
                       reinterpret_cast<const __nv_bfloat16 *>(w5), b5, y, M, m_pad, Z4, logit, dl, dz,
                       reinterpret_cast<__nv_bfloat16 *>(dzb), reinterpret_cast<__nv_bfloat16 *>(dzbT), loss_terms);
 }
@@ -926,10 +969,11 @@ cudaError_t launch_retile_weights(const uint16_t *pb, const size_t *w_off, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint16_t *pb, int64_t n, float lr,
+cudaError_t launch_adam_step(float *p, float *m, float *v, float *g, uint16_t *pb, int64_t n, float lr,
                              const float *c12, int64_t *step, const float *loss, float *loss_hist, unsigned *ticket,
                              const size_t *w_off, const size_t *w_end, const size_t *wt_off, const size_t *wtT_off,
-                             const int *in_pad, uint16_t *wt, uint16_t *wtT, cudaStream_t s) {
+                             const int *in_pad, uint16_t *wt, uint16_t *wtT, const float *const *wpart, int splits,
+                             cudaStream_t s) {
     AdamStepArgs a;
     a.p = p;
     a.m = m;
@@ -953,7 +997,9 @@ cudaError_t launch_adam_step(float *p, float *m, float *v, const float *g, uint1
         a.r.wt_off[l] = wt_off[l];
         a.r.wtT_off[l] = wtT_off[l];
         a.r.in_pad[l] = in_pad[l];
+        a.wpart[l] = wpart ? wpart[l] : nullptr;
     }
+    a.splits = splits;
     a.r.wt = reinterpret_cast<__nv_bfloat16 *>(wt);
     a.r.wtT = reinterpret_cast<__nv_bfloat16 *>(wtT);
     return pdl_launch(k_adam_step, dim3(grid_for(n)), dim3(256), 0, s, a);
