@@ -45,21 +45,23 @@ __device__ __forceinline__ void bin_consts(double dl, int nbins, double &rdl_s, 
     m = rdl_s < INFINITY ? (long long)((nbins + 2 + 31) / 32) + 1 : (1ll << 62);
 }
 
-// Integer estimate of the bin, for windows whose l values fit a 64-bit fixed
-// point: L = trunc(l 2^F) from l's bit pattern (|L| < 2^62 for every l of the
-// window, F = 62 - e with max(|lmin|, |lmax|) < 2^e), D = L - Lmin and
-// Q = D R / 2^P with R = 2^(44 - F + P) / dl truncated to a 64-bit integer in
-// [2^62, 2^63): Q estimates (l - lmin) / dl in units of 2^-44 of a bin.  In those
-// units the two truncations of L cost below 2 r (r = 2^(44 - F) / dl), R's
-// truncation below 1/2 (Q < 2^61) and the final shift below 1; the oracle's
-// rounded difference and quotient are within 2^-52 relative of the exact
-// quotient, below 2^8 units for up to 2^16 bins.  So where Q's fraction is more
-// than m = 2 r + 2^9 + 65 units from 0 and from 1, floor(Q 2^-44) is the
-// oracle's bin.  Only integer operations per particle.
+// Integer estimate of the bin: L = trunc(l 2^F) from l's bit pattern (|L| <
+// 2^62 for every l of the window, F = 62 - e with max(|lmin|, |lmax|) < 2^e),
+// D = L - Lmin, D' = D >> s (s makes Lmax - Lmin fit 32 bits) and
+// Q = D' R with R = trunc(2^(G + s - F) / dl) normalised into [2^31, 2^32):
+// one 32 x 32 -> 64-bit product estimates (l - lmin) / dl in units of 2^-G of
+// a bin.  In those units the truncations of L, Lmin and D cost below 3 R <
+// 2^34, R's truncation below D' < 2^32, the rounding of R's quotient below
+// 2^11, and the oracle's rounded difference and quotient are within 2^-52
+// relative of the exact quotient, below 2^(G - 36) for up to 2^16 bins; so
+// where Q's fraction is more than m = 2^35 + 2^(G - 35) units from 0 and from
+// 1, floor(Q 2^-G) is the oracle's bin.  G must lie in [40, 63] (windows far
+// narrower than 2^-30 of their magnitude leave it below and take the division).
 struct BinFast {
-    int F, P;
+    int F, s, G;
+    uint32_t R;
     long long lmin_fix;
-    unsigned long long R, m;
+    unsigned long long m;
     bool on;
 };
 
@@ -84,13 +86,13 @@ __device__ __forceinline__ long long fix_of(double l, int F, bool &ok) {
     return (b >> 63) ? -v : v;
 }
 
+// The constants of one window (computed once per block).
 __device__ __forceinline__ BinFast bin_fast_consts(double lmin, double lmax, double dl, int nbins) {
     BinFast c;
     c.on = false;
-    c.F = 0;
-    c.P = 0;
-    c.lmin_fix = 0;
+    c.F = c.s = c.G = 0;
     c.R = 0;
+    c.lmin_fix = 0;
     c.m = 0;
     if (!(dl > 0.0) || nbins > 65536) return c;
     const double big = fmax(fabs(lmin), fabs(lmax));
@@ -98,16 +100,21 @@ __device__ __forceinline__ BinFast bin_fast_consts(double lmin, double lmax, dou
     int eb;
     frexp(big, &eb);                          // big < 2^eb
     c.F = 62 - eb;                            // |l| 2^F < 2^62
-    const double r = ldexp(1.0, 44 - c.F) / dl;
-    int er;
-    const double fr = frexp(r, &er);          // r = fr 2^er, fr in [0.5, 1)
-    c.P = 63 - er;                            // R = fr 2^63 in [2^62, 2^63)
-    if (c.P < 1 || c.P > 120 || !(r < 1e12)) return c;
-    c.R = (unsigned long long)ldexp(fr, 63);
-    bool ok;
-    c.lmin_fix = fix_of(lmin, c.F, ok);
-    if (!ok) return c;
-    c.m = (unsigned long long)(2.0 * r) + 512 + 64 + 1;
+    bool ok0, ok1;
+    c.lmin_fix = fix_of(lmin, c.F, ok0);
+    const long long lmax_fix = fix_of(lmax, c.F, ok1);
+    if (!ok0 || !ok1 || lmax_fix < c.lmin_fix) return c;
+    const unsigned long long dmax = (unsigned long long)(lmax_fix - c.lmin_fix);
+    const int bits = 64 - __clzll((long long)dmax);
+    c.s = bits > 32 ? bits - 32 : 0;          // D' = D >> s < 2^32
+    const double A = ldexp(1.0, c.s - c.F) / dl;
+    if (!(A > 0.0) || !isfinite(A)) return c;
+    int ea;
+    const double fa = frexp(A, &ea);          // A = fa 2^ea, fa in [0.5, 1)
+    c.G = 32 - ea;                            // R = fa 2^32 in [2^31, 2^32)
+    if (c.G < 40 || c.G > 63) return c;
+    c.R = (uint32_t)ldexp(fa, 32);
+    c.m = (1ull << 35) + (1ull << (c.G - 35));
     c.on = true;
     return c;
 }
@@ -120,14 +127,13 @@ __device__ __forceinline__ int bin_of_fast(double l, const BinFast &c, double lm
         const long long L = fix_of(l, c.F, ok);
         const long long D = L - c.lmin_fix;
         if (ok && D >= 0) {
-            const unsigned long long ud = (unsigned long long)D;
-            const unsigned long long hi = __umul64hi(ud, c.R), lo = ud * c.R;
-            const unsigned long long Q = c.P >= 64 ? (hi >> (c.P - 64)) : ((hi << (64 - c.P)) | (lo >> c.P));
-            const unsigned long long fr = Q & ((1ull << kBinFracBits) - 1);
-            const unsigned long long k = Q >> kBinFracBits;
-            if ((c.P < 64 ? (hi >> c.P) == 0 : true) && k < (unsigned long long)nbins && fr > c.m &&
-                fr < (1ull << kBinFracBits) - c.m)
-                return (int)k;
+            const unsigned long long dp = (unsigned long long)D >> c.s;
+            if ((dp >> 32) == 0) {
+                const unsigned long long Q = (unsigned long long)(uint32_t)dp * (unsigned long long)c.R;
+                const unsigned long long k = Q >> c.G;
+                const unsigned long long fr = Q & ((1ull << c.G) - 1);
+                if (k < (unsigned long long)nbins && fr > c.m && fr < (1ull << c.G) - c.m) return (int)k;
+            }
         }
     }
     return bin_of(l, lmin, dl, rdl_s, m_exact, nbins);

@@ -63,7 +63,8 @@ __device__ __forceinline__ double sel6(const double (&q)[6], int j) {
 __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict__ views, int n_var,
                                                   const int64_t *__restrict__ offsets,
                                                   const double *__restrict__ x0, const double *__restrict__ y0,
-                                                  int64_t n, int32_t n_turns, int32_t *__restrict__ survival) {
+                                                  int64_t n, int32_t n_turns, double zero,
+                                                  int32_t *__restrict__ survival) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     if (i >= n) return;   // whole 8-lane groups leave together
     const int r = threadIdx.x & 7;
@@ -82,16 +83,21 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
     for (int turn = 0; alive && turn < n_turns; ++turn) {
         for (int e = 0; e < L.n_elem; ++e) {
             const DevElem *E = L.elems + e;
-            const int type = __ldg(&E->type);
+            // the record's first 32 bytes (type, n, term0, flags; row offsets) in two independent loads
+            const int4 hd = __ldg(reinterpret_cast<const int4 *>(E));
+            const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
+            const int type = hd.x;
             if (type == TRK_MAP) {
-                const uint32_t flags = __ldg(&E->flags);
-                const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
+                const uint32_t flags = (uint32_t)hd.w;
                 const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
-                const double2 *t = reinterpret_cast<const double2 *>(L.terms + __ldg(&E->term0));
+                const double2 *t = reinterpret_cast<const double2 *>(L.terms + hd.z);
                 const int rr = r < 6 ? r : 0;
                 const int kb = rb[rr], len = (r < 6 && ((L.row_mask >> rr) & 1u)) ? rb[rr + 1] - rb[rr] : 0;
                 double acc = (r < 6 && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
-                const double z0 = __ldg(&E->p[0]) * 0.0;   // as the tracking kernel's map
+                // +0 at run time: fma(a, b, z0) rounds as a * b, as the tracking
+                // kernel's map (whose z0 = p * 0.0 may be -0: only the sign of an
+                // exact zero can differ, and no loss decision depends on it)
+                const double z0 = zero;
                 for (int k = 0; k < len; ++k) {
                     const double2 tv = __ldg(t + kb + k);
                     const int code = (int)(unsigned)(__double_as_longlong(tv.y) & 0xffffffffll);
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                 for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
             } else if (type == TRK_THINSEXT) {
                 const double k2 = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
-                const double x = q[0], y = q[2], z0 = k2 * 0.0;   // as the tracking kernel
+                const double x = q[0], y = q[2], z0 = zero;   // as the tracking kernel (see the map)
                 q[1] = fma(-hk, fma(x, x, -fma(y, y, z0)), q[1]);
                 q[3] = fma(k2, fma(x, y, z0), q[3]);
             } else if (type == TRK_EDRIFT) {
@@ -127,6 +133,8 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
     if (r == 0) survival[i] = surv;
 }
 
+constexpr int kLaneBlock = 64;   // threads per block of k_da_lanes (8 particles)
+
 int grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -146,8 +154,11 @@ cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const do
 cudaError_t launch_da_lanes(const LatticeView *views, int n_var, const int64_t *offsets, const double *x0,
                             const double *y0, int64_t n, int32_t n_turns, int32_t *survival, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    // small blocks spread few particles over many SMs: each SM's L1 then holds
+    // the records of fewer variants' lattices
     const int64_t threads = 8 * n;
-    k_da_lanes<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(views, n_var, offsets, x0, y0, n, n_turns, survival);
+    k_da_lanes<<<(unsigned)((threads + kLaneBlock - 1) / kLaneBlock), kLaneBlock, 0, s>>>(views, n_var, offsets, x0,
+                                                                                      y0, n, n_turns, 0.0, survival);
     return cudaGetLastError();
 }
 

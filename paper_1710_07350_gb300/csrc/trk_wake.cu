@@ -97,13 +97,23 @@ __global__ void __launch_bounds__(kHistThreads, 2) k_wake_hist(const double *__r
     const bool any = kmin <= kmax;
     const double lmin = any ? dkey_inv(kmin) : 0.0;
     const double lmax = any ? dkey_inv(kmax) : 0.0;
-    const double dl = (lmax - lmin) / nbins;
-    // 1/dl for the kick (0: no window or zero width, every particle takes bin 0's voltage)
-    if (blockIdx.x == 0 && threadIdx.x == 0) win->idl[2 * slot + which] = (any && dl > 0.0) ? 1.0 / dl : 0.0;
-    double rdl_s;
-    long long bin_m;
-    bin_consts(dl, nbins, rdl_s, bin_m);
-    const BinFast bf = bin_fast_consts(lmin, lmax, dl, nbins);
+    // the window's constants, once per block (a chain of divisions: computed by
+    // every thread they kept the FP64 pipe busy for a third of the pass)
+    __shared__ double s_dl, s_rdl;
+    __shared__ long long s_m;
+    __shared__ BinFast s_bf;
+    if (threadIdx.x == 0) {
+        const double d = (lmax - lmin) / nbins;
+        s_dl = d;
+        bin_consts(d, nbins, s_rdl, s_m);
+        s_bf = bin_fast_consts(lmin, lmax, d, nbins);
+        // 1/dl for the kick (0: no window or zero width, every particle takes bin 0's voltage)
+        if (blockIdx.x == 0) win->idl[2 * slot + which] = (any && d > 0.0) ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const double dl = s_dl, rdl_s = s_rdl;
+    const long long bin_m = s_m;
+    const BinFast bf = s_bf;
     // wake function samples W(m dl) = w0 / sqrt(max(m dl, s_c))
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nbins; m += gridDim.x * blockDim.x) {
         const double s = (double)m * dl;
