@@ -110,6 +110,7 @@ struct TrackArgs {
     double rf_ip[4];
     int32_t n_rf_ip;
     int32_t pad_rf;
+    double zero;            // 0.0 (a value the compiler cannot see: see track_tile)
     double *partials;       // [turn][tile][28]
     int32_t *tile_alive;    // alive count per tile at the end (may be null)
     const double *wake_V;   // voltages of the kicking wake

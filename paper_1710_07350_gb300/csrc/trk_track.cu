@@ -46,14 +46,13 @@ __device__ __forceinline__ double tget(const Tile<P> &q, int p, int j) {
 // rows (which is what bounds a lightly occupied GPU).
 template <int P>
 __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E, const DevTerm *__restrict__ terms,
-                                      uint32_t rows, bool &dirty) {
+                                      uint32_t rows, double z0, bool &dirty) {
     const uint32_t flags = __ldg(&E->flags);
     const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
     const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
     const double2 *t = reinterpret_cast<const double2 *>(terms + __ldg(&E->term0));
-    // +0 known only at run time (a map's p[] is zero): monomial products are
-    // fma(m, x_j, z0), rounded as m * x_j but issued at the DFMA rate
-    const double z0 = __ldg(&E->p[0]) * 0.0;
+    // z0: +0 known only at run time (the kernel's `zero` argument): monomial
+    // products are fma(m, x_j, z0), rounded as m * x_j but issued at the DFMA rate
     double acc[6][P];
     int len[6], n = 0;
 #pragma unroll
@@ -96,8 +95,8 @@ __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E,
 // x += L x', y += L y', l += L (sqrt(1 + v) - 1), v = x'^2 + y'^2; for v < 2^-14
 // sqrt(1+v) - 1 = v/2 - v^2/8 + v^3/16 - 5 v^4/128 to FP64 rounding.
 template <int P>
-__device__ __forceinline__ void v_edrift(Tile<P> &q, double L) {
-    const double z0 = L * 0.0;   // run-time +0: products issued as FMAs (as in v_map)
+__device__ __forceinline__ void v_edrift(Tile<P> &q, double L, double z0) {
+    // z0 = run-time +0: products issued as FMAs (as in v_map)
     double g[P];
     bool need = false;
 #pragma unroll
@@ -258,8 +257,9 @@ __device__ __forceinline__ void v_kick_drift_t(Tile<P> &q, const double (&iP)[P]
                  dmq = __ldg(&E->p[11]);
     // z0 = +0 known only at run time: products (and doublings) are written
     // fma(a, b, z0), which rounds as a * b (adding +0 to a rounded product is
-    // exact) but issues as an FMA, faster than a multiply or an add on this GPU's
-    // FP64 pipe
+    // exact but for the sign of an exact zero) and issues as an FMA, faster than
+    // a multiply or an add on this GPU's FP64 pipe.  Taken from the element (the
+    // kernel-wide zero measured 2.7 % slower on the kick-drift ring)
     const double z0 = d1 * 0.0;
     double a1[P], a0[P], hb1[P], hb0[P], b1[P], b0[P];
     if (FL & 1u) {
@@ -315,9 +315,8 @@ __device__ __forceinline__ void v_kick_drift(Tile<P> &q, double (&iP)[P], bool &
 
 // Thin sextupole (Table 1 THINSEXT): x' -= (K2L/2)(x^2 - y^2), y' += K2L x y.
 template <int P>
-__device__ __forceinline__ void v_thin_sext(Tile<P> &q, const DevElem *__restrict__ E) {
-    const double k = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
-    const double z0 = k * 0.0;   // run-time +0: products issued as FMAs (as in v_map)
+__device__ __forceinline__ void v_thin_sext(Tile<P> &q, const DevElem *__restrict__ E, double z0) {
+    const double k = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);   // z0: run-time +0 (as in v_map)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double t = fma(q.x[p], q.x[p], -fma(q.y[p], q.y[p], z0));
@@ -386,15 +385,30 @@ __device__ __forceinline__ double rf_cos(double cphi, double sphi, double phi, d
 // slopes scaled by P/P'.
 template <int P>
 __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E, double p0, double ip01,
-                                       bool &dirty) {
+                                       double z0, bool &dirty) {
     const double V = __ldg(&E->p[0]), phi = __ldg(&E->p[1]), k = __ldg(&E->p[2]);
     const double cphi = __ldg(&E->p[4]), sphi = __ldg(&E->p[5]);
-    const double z0 = V * 0.0;   // run-time +0 (see rf_cos)
+    // z0: run-time +0 (see rf_cos)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double Pp = fma(fma(q.d[p], 1.0, 1.0), p0, z0);   // (1 + delta) p0, each step rounded as written
         const double P1 = fma(V, rf_cos(cphi, sphi, phi, fma(k, q.l[p], z0), z0), Pp);
-        const double s = Pp / P1;
+        // s = Pp / P1 through Newton's iteration for the reciprocal, r <- r + r (1 - P1 r),
+        // which squares the relative error 1 - P1 r at every step, seeded with 1/p0'
+        // (P1 = (1 + delta') p0': the seed's error is -delta').  Three steps from
+        // |1 - P1 r| <= 2^-8 leave the rounding of the last step; s = Pp r is then
+        // within two units of rounding of the quotient.  A particle further off the
+        // reference momentum (or a NaN) takes the division.
+        double s;
+        const double e0 = fma(-P1, ip01, 1.0);
+        if (((unsigned long long)__double_as_longlong(e0) << 1) <= (0x3F70000000000000ull << 1)) {
+            double r = fma(ip01, e0, ip01);
+            r = fma(r, fma(-P1, r, 1.0), r);
+            r = fma(r, fma(-P1, r, 1.0), r);
+            s = fma(Pp, r, z0);
+        } else {
+            s = Pp / P1;
+        }
         q.xp[p] = fma(q.xp[p], s, z0);
         q.yp[p] = fma(q.yp[p], s, z0);
         q.d[p] = fma(P1, ip01, -1.0);
@@ -408,11 +422,14 @@ __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, b
     if (flat) return __ldg(V);
     // the differences as fma(a, +-1, b): one rounding, the same as a - b, at the DFMA rate
     const double u = fma(fma(lmin, -1.0, l), idl, -0.5);
-    const double k0 = floor(u);
-    if (!(k0 >= 0.0)) return __ldg(V);
-    if (k0 >= (double)(nb - 1)) return __ldg(V + nb - 1);
-    const int k = (int)k0;
-    const double f = fma(k0, -1.0, u);
+    // k = floor(u) by one conversion (saturating at the int range) and integer
+    // bounds tests; NaN (exponent all ones, mantissa non-zero) takes bin 0's
+    // voltage, as a negative u does
+    if (((unsigned long long)__double_as_longlong(u) << 1) > 0xFFE0000000000000ull) return __ldg(V);
+    const int k = __double2int_rd(u);
+    if (k < 0) return __ldg(V);
+    if (k >= nb - 1) return __ldg(V + nb - 1);
+    const double f = fma((double)k, -1.0, u);
     const double v0 = __ldg(V + k), v1 = __ldg(V + k + 1);
     return fma(f, fma(v0, -1.0, v1), v0);
 }
@@ -600,6 +617,10 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
     const int64_t base = (int64_t)tile * T;
     if (base >= n_alive) return;  // whole block beyond the alive range
 
+    // +0 known only at run time: the element products fma(a, b, z0) round as
+    // a * b (but for the sign of an exact zero, which no loss test or later
+    // non-zero value depends on) and issue at the DFMA rate
+    const double z0 = a.zero;
     Tile<P> q;
     bool alive[P];
     double iP[P];
@@ -656,7 +677,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                 canon = false;
             }
             switch (type) {
-            case TRK_MAP: v_map<P>(q, E, L.terms, L.row_mask, dirty); break;
+            case TRK_MAP: v_map<P>(q, E, L.terms, L.row_mask, z0, dirty); break;
             case TRK_EDRIFT:
                 // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
                 // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
@@ -664,18 +685,18 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                     v_drift<P>(q.x, q.y, q.l, q.xp, q.yp, __ldg(&E->p[0]), __ldg(&E->p[1]), __ldg(&E->p[2]),
                                __ldg(&E->p[0]) * 0.0);
                 else
-                    v_edrift<P>(q, __ldg(&E->p[0]));
+                    v_edrift<P>(q, __ldg(&E->p[0]), z0);
                 break;
             case TRK_KQUAD:
             case TRK_KSEXT: v_kick_drift<P>(q, iP, dirty, canon, E); break;
-            case TRK_THINSEXT: v_thin_sext<P>(q, E); break;
+            case TRK_THINSEXT: v_thin_sext<P>(q, E, z0); break;
             case TRK_SBEND: v_sbend<P>(q, E); break;
             case TRK_RFCA: {
                 const double p01 = p0 + __ldg(&E->p[3]);
                 // the host's reciprocal when it has one for this cavity (single-turn segments)
                 const double ip01 = n_rf < a.n_rf_ip ? a.rf_ip[n_rf] : 1.0 / p01;
                 ++n_rf;
-                v_rfca<P>(q, E, p0, ip01, dirty);
+                v_rfca<P>(q, E, p0, ip01, z0, dirty);
                 p0 = p01;
                 break;
             }
