@@ -184,13 +184,15 @@ static trk_status compile_map(const trk_element_desc &d, int idx, DevElem &E, st
 
 // Coordinates a survival scan needs: the aperture reads x and y; a map row
 // that is needed reads the coordinates of its terms (and its own, when its
-// diagonal coefficient is 1); a thin sextupole reads x and y; an exact drift
+// diagonal coefficient is 1), leaving out the terms with a factor in `zero`
+// (survival_zeros: exactly zero, and dropped from the scan's terms); a thin
+// sextupole reads x and y; an exact drift
 // moves x, y by the slopes and l by a function of both.  The set is grown over
 // the whole lattice until it stops changing (the lattice repeats every turn).
 // Rows outside it never influence an aperture test, so a survival scan may
 // skip them and still take bit-identical decisions.  Any other element type
 // keeps every row.
-static uint32_t survival_rows(const trk_lattice &L) {
+static uint32_t survival_rows(const trk_lattice &L, uint32_t zero) {
     uint32_t need = 0x5u;   // x (0) and y (2)
     for (int it = 0; it < 8; ++it) {
         const uint32_t before = need;
@@ -201,9 +203,11 @@ static uint32_t survival_rows(const trk_lattice &L) {
                     for (int k = E.rb[r]; k < E.rb[r + 1]; ++k) {
                         const int code = L.terms[E.term0 + k].code;
                         const int deg = code & 3;
-                        if (deg >= 1) need |= 1u << ((code >> 2) & 7);
-                        if (deg >= 2) need |= 1u << ((code >> 5) & 7);
-                        if (deg >= 3) need |= 1u << ((code >> 8) & 7);
+                        uint32_t f = 0;   // the term's factors
+                        if (deg >= 1) f |= 1u << ((code >> 2) & 7);
+                        if (deg >= 2) f |= 1u << ((code >> 5) & 7);
+                        if (deg >= 3) f |= 1u << ((code >> 8) & 7);
+                        if (!(f & zero)) need |= f;   // a term with a factor that stays zero is dropped
                     }
                 }
             } else if (E.type == TRK_THINSEXT) {
@@ -479,8 +483,8 @@ extern "C" trk_status trk_create_lattice(const trk_element_desc *elems, int32_t 
     v.n_elem = n;
     v.ap_type = opts->aperture;
     v.row_mask = 0x3Fu;
-    L->survival_rows = survival_rows(*L);
     L->survival_zero = survival_zeros(*L);
+    L->survival_rows = survival_rows(*L, L->survival_zero);
     v.ap_a = opts->a;
     v.ap_b = opts->b;
     // |x| <= a as integers: bit patterns of the positive bounds shifted left by one
@@ -1338,8 +1342,10 @@ extern "C" trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int3
     if (!d_x0 || !d_y0 || !d_survival) return fail(TRK_EINVAL, "trk_da_survival_lanes: NULL point or output array");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<LatticeView> hv(n_var);
+    int lanes = 4;   // 4 lanes per particle when no view evaluates rows 4 or 5
     for (int v = 0; v < n_var; ++v) {
         hv[v] = lats[v]->sview;
+        if (hv[v].row_mask & ~0xFu) lanes = 8;
     }
     LatticeView *dv = nullptr;
     int64_t *doff = nullptr;
@@ -1347,7 +1353,7 @@ extern "C" trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int3
     if (e == cudaSuccess) e = cudaMalloc(&doff, (n_var + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemcpyAsync(dv, hv.data(), n_var * sizeof(LatticeView), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offsets, (n_var + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_da_lanes(dv, n_var, doff, d_x0, d_y0, total, n_turns, d_survival, s);
+    if (e == cudaSuccess) e = launch_da_lanes(dv, n_var, doff, d_x0, d_y0, total, n_turns, lanes, d_survival, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dv);
     cudaFree(doff);

@@ -54,22 +54,29 @@ __device__ __forceinline__ double sel6(const double (&q)[6], int j) {
     return v;
 }
 
-// Particle i of the point list takes threads 8 i .. 8 i + 7; its variant is the
-// v with offsets[v] <= i < offsets[v + 1].  Every lane of the group holds all
-// six coordinates; lane r < 6 sums row r of a map, and six independent
-// shuffles hand the new coordinates to the group.  Thin sextupoles, drifts and
-// the aperture test run on every lane with the same operations (no exchange).
-// Lattices hold MAP, EDRIFT and THINSEXT elements only (checked on the host).
+// Particle i of the point list takes threads LANES i .. LANES i + LANES - 1; its
+// variant is the v with offsets[v] <= i < offsets[v + 1].  Every lane of the
+// group holds all six coordinates; lane r < min(6, LANES) sums row r of a map,
+// and as many independent shuffles hand the new coordinates to the group.  Thin
+// sextupoles, drifts and the aperture test run on every lane with the same
+// operations (no exchange).  LANES = 4 serves views whose survival rows are
+// among x, x', y, y' (rows 4 and 5 are then read by no evaluated row and keep
+// their values); it halves the replicated work, which binds passes of a few
+// thousand points.  Lattices hold MAP, EDRIFT and THINSEXT elements only
+// (checked on the host).
+template <int LANES>
 __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict__ views, int n_var,
                                                   const int64_t *__restrict__ offsets,
                                                   const double *__restrict__ x0, const double *__restrict__ y0,
                                                   int64_t n, int32_t n_turns, double zero,
                                                   int32_t *__restrict__ survival) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    if (i >= n) return;   // whole 8-lane groups leave together
-    const int r = threadIdx.x & 7;
-    const int g0 = (threadIdx.x & 31) & ~7;
-    const unsigned gm = 0xFFu << g0;
+    static_assert(LANES == 4 || LANES == 8, "lane groups of 4 or 8");
+    constexpr int kRows = LANES < 6 ? LANES : 6;   // map rows evaluated by the group
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+    if (i >= n) return;   // whole lane groups leave together
+    const int r = threadIdx.x & (LANES - 1);
+    const int g0 = (threadIdx.x & 31) & ~(LANES - 1);
+    const unsigned gm = ((1u << LANES) - 1u) << g0;
     int lo = 0, hi = n_var;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -91,9 +98,9 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                 const uint32_t flags = (uint32_t)hd.w;
                 const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
                 const double2 *t = reinterpret_cast<const double2 *>(L.terms + hd.z);
-                const int rr = r < 6 ? r : 0;
-                const int kb = rb[rr], len = (r < 6 && ((L.row_mask >> rr) & 1u)) ? rb[rr + 1] - rb[rr] : 0;
-                double acc = (r < 6 && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
+                const int rr = r < kRows ? r : 0;
+                const int kb = rb[rr], len = (r < kRows && ((L.row_mask >> rr) & 1u)) ? rb[rr + 1] - rb[rr] : 0;
+                double acc = (r < kRows && ((flags >> rr) & 1u)) ? sel6(q, rr) : 0.0;
                 // +0 at run time: fma(a, b, z0) rounds as a * b, as the tracking
                 // kernel's map (whose z0 = p * 0.0 may be -0: only the sign of an
                 // exact zero can differ, and no loss decision depends on it)
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
                     acc = fma(tv.x, m, acc);
                 }
 #pragma unroll
-                for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
+                for (int c = 0; c < kRows; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
             } else if (type == TRK_THINSEXT) {
                 const double k2 = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
                 const double x = q[0], y = q[2], z0 = zero;   // as the tracking kernel (see the map)
@@ -133,7 +140,8 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
     if (r == 0) survival[i] = surv;
 }
 
-constexpr int kLaneBlock = 64;   // threads per block of k_da_lanes (8 particles)
+// particles per block of k_da_lanes: 8 up to kLaneSmall points, 16 above
+constexpr int kLaneSmall = 4096;
 
 int grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
@@ -152,13 +160,20 @@ cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const do
 }
 
 cudaError_t launch_da_lanes(const LatticeView *views, int n_var, const int64_t *offsets, const double *x0,
-                            const double *y0, int64_t n, int32_t n_turns, int32_t *survival, cudaStream_t s) {
+                            const double *y0, int64_t n, int32_t n_turns, int lanes, int32_t *survival,
+                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    if (lanes != 4 && lanes != 8) return cudaErrorInvalidValue;
     // small blocks spread few particles over many SMs: each SM's L1 then holds
-    // the records of fewer variants' lattices
-    const int64_t threads = 8 * n;
-    k_da_lanes<<<(unsigned)((threads + kLaneBlock - 1) / kLaneBlock), kLaneBlock, 0, s>>>(views, n_var, offsets, x0,
-                                                                                      y0, n, n_turns, 0.0, survival);
+    // the records of fewer variants' lattices (measured: a 34-point pass over 34
+    // variants 45 ms at 32 particles per block, 23 ms at 8; above a few thousand
+    // points 16 per block keep more warps per SM in flight)
+    const int per = n <= kLaneSmall ? 8 : 16;
+    const unsigned grid = (unsigned)((n + per - 1) / per);
+    if (lanes == 4)
+        k_da_lanes<4><<<grid, 4 * per, 0, s>>>(views, n_var, offsets, x0, y0, n, n_turns, 0.0, survival);
+    else
+        k_da_lanes<8><<<grid, 8 * per, 0, s>>>(views, n_var, offsets, x0, y0, n, n_turns, 0.0, survival);
     return cudaGetLastError();
 }
 

@@ -245,8 +245,10 @@ cudaError_t launch_head_tiled(const uint16_t *H4, const uint16_t *w5, const floa
                               cudaStream_t s);
 cudaError_t launch_da_init(double *coords, int64_t pitch, int32_t *ids, const double *x0, const double *y0,
                            int64_t first, int64_t n, cudaStream_t s);
+// lanes: 8, or 4 when every view's row_mask lies within rows 0..3
 cudaError_t launch_da_lanes(const LatticeView *views, int n_var, const int64_t *offsets, const double *x0,
-                            const double *y0, int64_t n, int32_t n_turns, int32_t *survival, cudaStream_t s);
+                            const double *y0, int64_t n, int32_t n_turns, int lanes, int32_t *survival,
+                            cudaStream_t s);
 cudaError_t launch_da_survival(const int32_t *ids, const int32_t *lt, int64_t n, int32_t n_turns, int32_t *survival,
                                cudaStream_t s);
 

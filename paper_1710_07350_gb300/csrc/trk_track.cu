@@ -46,13 +46,15 @@ __device__ __forceinline__ double tget(const Tile<P> &q, int p, int j) {
 // rows (which is what bounds a lightly occupied GPU).
 template <int P>
 __device__ __forceinline__ void v_map(Tile<P> &q, const DevElem *__restrict__ E, const DevTerm *__restrict__ terms,
-                                      uint32_t rows, double z0, bool &dirty) {
+                                      uint32_t rows, bool &dirty) {
     const uint32_t flags = __ldg(&E->flags);
     const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
     const int16_t *rb = reinterpret_cast<const int16_t *>(&rbv);
     const double2 *t = reinterpret_cast<const double2 *>(terms + __ldg(&E->term0));
-    // z0: +0 known only at run time (the kernel's `zero` argument): monomial
-    // products are fma(m, x_j, z0), rounded as m * x_j but issued at the DFMA rate
+    // +0 known only at run time (a map's p[] is zero): monomial products are
+    // fma(m, x_j, z0), rounded as m * x_j but issued at the DFMA rate (taken per
+    // element: the kernel-wide zero measured 3-10 % slower on map rings)
+    const double z0 = __ldg(&E->p[0]) * 0.0;
     double acc[6][P];
     int len[6], n = 0;
 #pragma unroll
@@ -677,7 +679,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs &a, const int tile, T
                 canon = false;
             }
             switch (type) {
-            case TRK_MAP: v_map<P>(q, E, L.terms, L.row_mask, z0, dirty); break;
+            case TRK_MAP: v_map<P>(q, E, L.terms, L.row_mask, dirty); break;
             case TRK_EDRIFT:
                 // x += L x', y += L y', l += L (sqrt(1 + x'^2 + y'^2) - 1); in scaled canonical
                 // momenta x' = qx (1 + g) and sqrt(1 + x'^2 + y'^2) = 1 + g: the drift of the integrator
