@@ -750,12 +750,21 @@ def c4_record(args, warmup, with_cpu, clocks_index=None, plain_stride=1):
     clk = clocks.stop() if clocks is not None else None
     passes = n_tot * 60 * turns
     passes_plain = n_plain * 60 * turns
+    # the method's count of every variant (the lattices keep their moments); all particles survive
+    from paper_1710_07350_gb300 import flops
+    f_tot = sum(flops.step_work(l, v[2], turns)[1] for l, v in zip(lats, vs))
+    ach = f_tot / res["batched"] / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / PEAK_FP64_TFLOPS, "flops": f_tot,
+            "count": "flops.py element model per pass + 54 per particle-turn for the moments; wall time of the "
+                     "batched call, host launch included"}
     return {"workload": "c4: 256 variants of the FODO ring + thin sextupoles, %d particles, 1000 turns" % n_tot,
             "metric": UNIT, "value": passes / res["batched"], "batched_value": passes / res["batched"],
             "plain_value": passes_plain / res["plain"], "batched_s": res["batched"], "plain_s": res["plain"],
             "plain_sample": "every %dth variant (%d variants, %d particles), one call each" % (plain_stride, len(plain_idx),
                                                                                              n_plain),
-            "speedup": (passes / res["batched"]) / (passes_plain / res["plain"]), "autotuned_schedule": tuned,
+            "speedup": (passes / res["batched"]) / (passes_plain / res["plain"]), "roofline": roof,
+            "autotuned_schedule": tuned,
             "alive_end": alive,
             "note": "passes counted as if all survive; wall time of the calls, host launch included", "clocks": clk,
             "cpu_baseline": c4_cpu_baseline() if with_cpu else None}
