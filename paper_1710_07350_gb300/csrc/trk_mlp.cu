@@ -442,7 +442,7 @@ static cudaError_t mlp_retile(trk_mlp *N, cudaStream_t s) {
 
 // Gradients of the mean BCE over M rows into N->g and the loss into N->loss,
 // every product on tcgen05 (the tiled weights must be current: mlp_retile).
-// Rounding points as mlp_grad_rows: h0 = bf16(x), z FP32, h = bf16(gelu(z)),
+// Rounding points (the file header's): h0 = bf16(x), z FP32, h = bf16(gelu(z)),
 // dz FP32, dzb = bf16(dz), dW = dzb^T h and dh = dzb W in FP32, db = sum dz.
 struct GatherRows {
     const int32_t *perm = nullptr;
