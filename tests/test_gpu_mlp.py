@@ -113,3 +113,34 @@ def test_training_learns_a_disc():
     Xv, yv = data(20000, seed=6)
     pred = (trk.trk_mlp_forward(net, torch.from_numpy(Xv).cuda()).cpu().numpy() > 0).astype(np.float32)
     assert np.mean(pred == yv) > 0.97
+
+
+def test_gradients_and_training_are_deterministic():
+    """The backward pass runs as a fork-join over several streams with
+    programmatic dependent launch; every sum has one writer and a fixed order,
+    so two runs on the same inputs give the same bits (gradients, loss history,
+    weights), and a short last batch does too."""
+    p = params64(11)
+    X, y = data(5000, seed=12)
+    Xt, yt = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    runs = []
+    for _ in range(2):
+        net = trk.trk_mlp_create(p)
+        loss = trk.trk_mlp_grad(net, Xt, yt).item()
+        _, g = trk.trk_mlp_get(net)
+        runs.append((loss, g))
+    assert runs[0][0] == runs[1][0]
+    for l in range(5):
+        for k in range(2):
+            assert np.array_equal(runs[0][1][l][k], runs[1][1][l][k]), (l, k)
+    gen = np.random.default_rng(13)
+    perm = torch.from_numpy(np.stack([gen.permutation(len(X)) for _ in range(3)]).astype(np.int32)).cuda()
+    out = []
+    for _ in range(2):
+        net = trk.trk_mlp_create(syn.mlp_init(7))
+        hist = trk.trk_mlp_train(net, Xt, yt, batch=1024, epochs=3, perm=perm, lr=2e-3).cpu().numpy()
+        w, _ = trk.trk_mlp_get(net)
+        out.append((hist, w))
+    assert np.array_equal(out[0][0], out[1][0])
+    for l in range(5):
+        assert np.array_equal(out[0][1][l][0], out[1][1][l][0]) and np.array_equal(out[0][1][l][1], out[1][1][l][1])
