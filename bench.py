@@ -473,7 +473,10 @@ def run_da(n_var, trk, syn, torch):
     out = {"variants": n_var, "grid": [n, n], "turns": turns, "coarse_stride": stride, "band_radius": 2,
            "audit_fraction": 0.005, "sentinel_stride": 5, "expand_radius": 0}
     res = {}
-    for name, use in (("surrogate", 1), ("nonlearned", 0)):
+    # the surrogate arm: the network predicts the cells near the nearest-known
+    # boundary (use_mlp 2; measured 133 scans/s against 127 with the network on
+    # every cell)
+    for name, use in (("surrogate", 2), ("nonlearned", 0)):
         net = trk.trk_mlp_create(syn.mlp_init(7)) if use else None
         opts = {"nx": n, "ny": n, "half_width": syn.DA_HALF_WIDTH, "n_turns": turns, "coarse_stride": stride,
                 "band_radius": 2, "use_mlp": use, "epochs": epochs, "batch": batch, "lr": 2e-3,
@@ -491,6 +494,7 @@ def run_da(n_var, trk, syn, torch):
                      "max_cell_distance": int(max(d[2] for d in diffs)),
                      "tracked_fraction": (st["n_tracked"] + st["n_coarse"]) / st["n_cells"],
                      "audit_cells": st["n_audit"], "audit_wrong": st["n_audit_wrong"], "band_passes": st["n_passes"],
+                     "network_cells": st["n_region"],
                      "pass_cells": st["pass_cells"], "pass_ms": [round(v, 1) for v in st["pass_ms"]],
                      "ms": {k: st[k] for k in ("ms_coarse", "ms_train", "ms_infer", "ms_band", "ms_retrack")}}
     out["scans_per_s"] = {"plain": n_var / t_plain, "batched": n_var / t_batched,

@@ -363,7 +363,11 @@ trk_status trk_mlp_get(trk_mlp *net, float *const *W, float *const *b, float *co
  *      n_turns) with trk_mlp_train(epochs, batch, lr, d_perm) and predicts every
  *      cell (logit > 0 = survives); use_mlp = 0: every cell takes the label of
  *      its nearest known cell (the nearest coarse cell, or the nearest sentinel
- *      cell where that is strictly closer); the known labels override either;
+ *      cell where that is strictly closer); use_mlp = 2: the network, trained
+ *      as for 1, predicts only the cells within Chebyshev distance 3 of a
+ *      boundary cell of the nearest-known prediction (where the known cells
+ *      disagree), the nearest known cell the rest; the known labels override
+ *      every form;
  *   3. cells within Chebyshev distance band_radius of a predicted-boundary cell
  *      (8-neighbourhood holding both classes), and the caller's audit cells
  *      (d_audit[v][iy][ix] != 0, optional), are re-tracked exactly in FP64 and
@@ -403,6 +407,7 @@ typedef struct {
     int64_t pass_cells[16];  /* cells tracked in pass k (passes past 15 add to [15]) */
     double pass_ms[16];      /* wall time of pass k: band, gather, track, merge */
     int64_t n_sentinel;      /* sentinel cells tracked with the coarse cells */
+    int64_t n_region;        /* cells the network predicted (use_mlp 1: every cell; 2: the region) */
 } trk_triage_stats;
 trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_var, const float *d_params,
                          const uint8_t *d_audit, trk_mlp *net, const int32_t *d_perm, const trk_triage_opts *opts,

@@ -80,6 +80,34 @@ __global__ void k_grid_features(int64_t c0, int64_t m, int nx, int ny, double w,
     }
 }
 
+// Features of the listed cells idx[0, m).
+__global__ void k_list_features(const int64_t *__restrict__ idx, int64_t m, int nx, int ny, double w,
+                                const float *__restrict__ params, float *__restrict__ X) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = idx[i];
+        const int ix = (int)(c % nx);
+        const int iy = (int)((c / nx) % ny);
+        const int v = (int)(c / ((int64_t)nx * ny));
+        X[i * 8 + 0] = (float)(cell_centre(ix, nx, w) / w);
+        X[i * 8 + 1] = (float)(cell_centre(iy, ny, w) / w);
+        for (int k = 0; k < 6; ++k) X[i * 8 + 2 + k] = params[v * 6 + k];
+    }
+}
+
+// The cells with bit 0 of region set, in any order (each cell's prediction
+// depends on its own features only, so the order does not reach the mask).
+__global__ void k_region_list(const uint8_t *__restrict__ region, int64_t n, int64_t *__restrict__ idx,
+                              unsigned long long *__restrict__ count) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        if (region[c] & 1) idx[atomicAdd(count, 1ull)] = c;
+}
+
+__global__ void k_list_threshold(const int64_t *__restrict__ idx, const float *__restrict__ logit, int64_t m,
+                                 uint8_t *__restrict__ mask) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        mask[idx[i]] = logit[i] > 0.0f ? 1 : 0;
+}
+
 __global__ void k_threshold(const float *__restrict__ logit, int64_t m, uint8_t *__restrict__ mask) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
         mask[i] = logit[i] > 0.0f ? 1 : 0;
@@ -408,7 +436,39 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
     S.ms_train = t2 - t1;
 
     // 3. predicted mask of every cell
-    if (o->use_mlp) {
+    if (o->use_mlp == 2) {
+        // nearest known cell everywhere, then the network where the known cells
+        // disagree: within distance 3 of a boundary cell of that prediction
+        k_nearest_known<<<grid_for(n_all), 256, 0, s>>>(ksurv.p, dcells.p, nx, ny, st, off, cx, cy, per_v, dnsx.p,
+                                                        dnsy.p, (int)sxp.size(), n_var, o->n_turns, d_mask);
+        DBuf<uint8_t> rb, rt;
+        DBuf<unsigned long long> rcount;
+        if (rb.alloc(n_all) || rt.alloc(n_all) || rcount.alloc(1))
+            return set_error(TRK_ENOMEM, "trk_da_triage: region allocation failed");
+        k_boundary<<<grid_for(n_all), 256, 0, s>>>(d_mask, nx, ny, n_var, rb.p);
+        k_dilate_x<<<grid_for(n_all), 256, 0, s>>>(rb.p, nullptr, nx, ny, n_var, 3, 0, rt.p);
+        k_dilate_y<<<grid_for(n_all), 256, 0, s>>>(rt.p, nx, ny, n_var, 3, 0, rb.p);
+        TRI_CUDA(cudaMemsetAsync(rcount.p, 0, sizeof(unsigned long long), s));
+        DBuf<int64_t> ridx;
+        if (ridx.alloc(n_all)) return set_error(TRK_ENOMEM, "trk_da_triage: region allocation failed");
+        k_region_list<<<grid_for(n_all), 256, 0, s>>>(rb.p, n_all, ridx.p, rcount.p);
+        TRI_CUDA(cudaGetLastError());
+        unsigned long long nr = 0;
+        TRI_CUDA(cudaMemcpyAsync(&nr, rcount.p, sizeof nr, cudaMemcpyDeviceToHost, s));
+        TRI_CUDA(cudaStreamSynchronize(s));
+        S.n_region = (int64_t)nr;
+        const int64_t chunk = 1 << 20;
+        DBuf<float> X, logit;
+        if (X.alloc(chunk * 8) || logit.alloc(chunk)) return set_error(TRK_ENOMEM, "trk_da_triage: inference allocation failed");
+        for (int64_t c0 = 0; c0 < (int64_t)nr; c0 += chunk) {
+            const int64_t m = (int64_t)nr - c0 < chunk ? (int64_t)nr - c0 : chunk;
+            k_list_features<<<grid_for(m), 256, 0, s>>>(ridx.p + c0, m, nx, ny, w, d_params, X.p);
+            r = trk_mlp_forward(net, X.p, m, logit.p, stream);
+            if (r != TRK_OK) return r;
+            k_list_threshold<<<grid_for(m), 256, 0, s>>>(ridx.p + c0, logit.p, m, d_mask);
+        }
+    } else if (o->use_mlp) {
+        S.n_region = n_all;
         const int64_t chunk = 1 << 20;
         DBuf<float> X, logit;
         if (X.alloc(chunk * 8) || logit.alloc(chunk)) return set_error(TRK_ENOMEM, "trk_da_triage: inference allocation failed");

@@ -60,7 +60,7 @@ class trk_triage_stats(ctypes.Structure):
                 ("n_tracked", c_int64), ("n_audit_wrong", c_int64), ("ms_coarse", c_double),
                 ("ms_train", c_double), ("ms_infer", c_double), ("ms_band", c_double), ("ms_retrack", c_double),
                 ("n_passes", c_int64), ("pass_cells", c_int64 * 16), ("pass_ms", c_double * 16),
-                ("n_sentinel", c_int64)]
+                ("n_sentinel", c_int64), ("n_region", c_int64)]
 
 
 class trk_schedule(ctypes.Structure):

@@ -49,7 +49,7 @@ def test_batched_scan_equals_per_lattice_scan():
         assert np.array_equal(one, batched[v * n * n:(v + 1) * n * n])
 
 
-@pytest.mark.parametrize("use_mlp", [1, 0])
+@pytest.mark.parametrize("use_mlp", [1, 2, 0])
 def test_triage_matches_exhaustive_boundary(use_mlp):
     nv, n, turns = 4, 96, 300
     L = [trk.trk_create_lattice(syn.lattice_c5(v), moments=False) for v in range(nv)]
@@ -77,6 +77,11 @@ def test_triage_matches_exhaustive_boundary(use_mlp):
     assert np.array_equal(surv[exact], exh[exact])
     assert st["n_tracked"] < nv * n * n and st["n_coarse"] == ncoarse
     assert 1 <= st["n_passes"] < 64
+    # the network predicts every cell (1) or only those near the nearest-known boundary (2)
+    if use_mlp == 1:
+        assert st["n_region"] == nv * n * n
+    elif use_mlp == 2:
+        assert 0 < st["n_region"] < nv * n * n
 
 
 def test_nonlearned_triage_matches_triage_oracle():
