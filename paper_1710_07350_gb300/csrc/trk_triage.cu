@@ -303,6 +303,7 @@ __global__ void k_fill_predicted(const uint8_t *__restrict__ mask, const uint8_t
 }
 
 constexpr int64_t kLaneCells = 16384;
+constexpr int64_t kOnePerThreadCells = 1 << 20;   // band passes up to this size: one particle per thread
 
 // Sentinel positions on an axis of n cells: off, off + stride, ... up to
 // n - 1 - off, plus n - 1 - off itself (off = stride / 2), inside [0, n).
@@ -554,14 +555,16 @@ extern "C" trk_status trk_da_triage(const trk_lattice *const *lats, int32_t n_va
         const double p1 = now_ms();
         t_band += p1 - p0;
         // Few cells: the pass is bound by one particle's latency over all turns,
-        // so the lane-parallel scan (8 lanes per particle) takes it where the
-        // lattices allow; otherwise one particle per thread keeps one chain per
-        // thread and spreads the warps over the SMs.
+        // so the lane-parallel scan (4 or 8 lanes per particle) takes it where the
+        // lattices allow; otherwise one particle per thread up to about a million
+        // cells keeps one chain per thread and spreads the warps over the SMs
+        // (measured: 484 k random cells 67 ms at one particle per thread, 103 ms at
+        // two; equal near 1 M; two per thread ahead from 2 M).
         r = TRK_EUNSUPPORTED;
         if (n_todo <= kLaneCells)
             r = trk_da_survival_lanes(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, tsurv.p, stream);
         if (r == TRK_EUNSUPPORTED) {
-            trk_schedule sch = {128, n_todo <= 2 * 152 * 128 ? 1 : 2, 1, 2};
+            trk_schedule sch = {128, n_todo <= kOnePerThreadCells ? 1 : 2, 1, 2};
             r = trk_da_survival(lats, n_var, toffs.data(), tx0.p, ty0.p, o->n_turns, &sch, tsurv.p, stream);
         }
         if (r != TRK_OK) return r;
