@@ -90,9 +90,11 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
     for (int turn = 0; alive && turn < n_turns; ++turn) {
         for (int e = 0; e < L.n_elem; ++e) {
             const DevElem *E = L.elems + e;
-            // the record's first 32 bytes (type, n, term0, flags; row offsets) in two independent loads
+            // the record's first 48 bytes (type, n, term0, flags; row offsets; p[0], p[1])
+            // in three independent loads, whatever the element needs of them
             const int4 hd = __ldg(reinterpret_cast<const int4 *>(E));
             const int4 rbv = __ldg(reinterpret_cast<const int4 *>(E->rb));
+            const double2 pp = __ldg(reinterpret_cast<const double2 *>(E->p));
             const int type = hd.x;
             if (type == TRK_MAP) {
                 const uint32_t flags = (uint32_t)hd.w;
@@ -118,12 +120,12 @@ __global__ void __launch_bounds__(256) k_da_lanes(const LatticeView *__restrict_
 #pragma unroll
                 for (int c = 0; c < kRows; ++c) q[c] = __shfl_sync(gm, acc, g0 + c);
             } else if (type == TRK_THINSEXT) {
-                const double k2 = __ldg(&E->p[0]), hk = __ldg(&E->p[1]);
+                const double k2 = pp.x, hk = pp.y;
                 const double x = q[0], y = q[2], z0 = zero;   // as the tracking kernel (see the map)
                 q[1] = fma(-hk, fma(x, x, -fma(y, y, z0)), q[1]);
                 q[3] = fma(k2, fma(x, y, z0), q[3]);
             } else if (type == TRK_EDRIFT) {
-                const double Ld = __ldg(&E->p[0]);
+                const double Ld = pp.x;
                 const double xp = q[1], yp = q[3];
                 const double g = edrift_g(fma(xp, xp, yp * yp));
                 q[0] = fma(Ld, xp, q[0]);
