@@ -419,11 +419,13 @@ __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E
 }
 
 // Wake voltage at l: linear interpolation between bin centres, clamped.
-__device__ __forceinline__ double wake_volt(double l, double lmin, double idl, bool flat,
+// c0 = -(lmin idl + 1/2), once per thread: u = l idl + c0 = (l - lmin) / dl - 1/2
+// in one FMA (a rounding of c0 and one of u, against the oracle's difference,
+// quotient and subtraction).
+__device__ __forceinline__ double wake_volt(double l, double c0, double idl, bool flat,
                                             const double *__restrict__ V, int nb) {
     if (flat) return __ldg(V);
-    // the differences as fma(a, +-1, b): one rounding, the same as a - b, at the DFMA rate
-    const double u = fma(fma(lmin, -1.0, l), idl, -0.5);
+    const double u = fma(l, idl, c0);
     // k = floor(u) by one conversion (saturating at the int range) and integer
     // bounds tests; NaN (exponent all ones, mantissa non-zero) takes bin 0's
     // voltage, as a negative u does
@@ -431,6 +433,7 @@ __device__ __forceinline__ double wake_volt(double l, double lmin, double idl, b
     const int k = __double2int_rd(u);
     if (k < 0) return __ldg(V);
     if (k >= nb - 1) return __ldg(V + nb - 1);
+    // the differences as fma(a, -1, b): one rounding, the same as b - a
     const double f = fma((double)k, -1.0, u);
     const double v0 = __ldg(V + k), v1 = __ldg(V + k + 1);
     return fma(f, fma(v0, -1.0, v1), v0);
@@ -556,19 +559,20 @@ __device__ __forceinline__ void wake_kick(const TrackArgs &a, Tile<P> &q, const 
     const double lmin = dkey_inv(kmin);
     const double idl = a.win->idl[2 * a.kick_slot + which];   // 1/dl from the histogram pass, 0 when flat
     const bool flat = !(idl > 0.0);
+    const double c0 = -fma(lmin, idl, 0.5);
     const double ip0 = a.ip0c;
     if (Vx) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (!alive[p]) continue;
             const double iP = ip0 / (1.0 + q.d[p]);
-            q.xp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, Vx, nbins), iP, q.xp[p]);
-            q.yp[p] = fma(wake_volt(q.l[p], lmin, idl, flat, Vx + nbins, nbins), iP, q.yp[p]);
+            q.xp[p] = fma(wake_volt(q.l[p], c0, idl, flat, Vx, nbins), iP, q.xp[p]);
+            q.yp[p] = fma(wake_volt(q.l[p], c0, idl, flat, Vx + nbins, nbins), iP, q.yp[p]);
         }
     }
 #pragma unroll
     for (int p = 0; p < P; ++p)
-        if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], lmin, idl, flat, V, nbins), ip0, q.d[p]);
+        if (alive[p]) q.d[p] = fma(wake_volt(q.l[p], c0, idl, flat, V, nbins), ip0, q.d[p]);
 }
 
 // Check the aperture of every alive particle after element e; a particle that
