@@ -300,9 +300,10 @@ trk_status trk_da_survival(const trk_lattice *const *lats, int32_t n_var, const 
                            int32_t *d_survival, void *stream);
 
 /* The same survival turns (bit-identical) for few points: each particle gets 8
- * GPU lanes, lane r holding coordinate r, so the rows of a map are evaluated in
- * parallel and one particle's chain of dependent operations per turn is
- * shorter; one launch covers all n_turns turns, lost particles stop at once.
+ * GPU lanes (4 when no lattice's survival rows go beyond x, x', y, y'), lane r
+ * evaluating map row r, so the rows of a map are evaluated in parallel and one
+ * particle's chain of dependent operations per turn is shorter; one launch
+ * covers all n_turns turns, lost particles stop at once.
  * Lattices may hold MAP, EDRIFT and THINSEXT elements only (TRK_EUNSUPPORTED
  * otherwise); at most 2^28 points.  Arguments as trk_da_survival.
  * Synchronises the stream before returning. */
@@ -320,7 +321,8 @@ trk_status trk_da_survival_lanes(const trk_lattice *const *lats, int32_t n_var, 
  * (trk_mlp_forward) runs its hidden layers as persistent 128 x 256 tiles;
  * training (trk_mlp_grad, trk_mlp_train) runs every product -- forward, input
  * gradient, weight gradient split over the batch and summed in split order --
- * as 128 x 64 tiles; the rounding points are the same.
+ * as 128 x 32 (forward, input gradient) and 128 x 64 (weight gradient) tiles;
+ * the rounding points are the same.
  *   W[l], b[l]   HOST FP32 arrays, W[l] row-major [out][in]: l = 0: 256 x 8,
  *                l = 1..3: 256 x 256, l = 4: 1 x 256; b[l] [out]
  *   d_X          device FP32 [M][8] inputs; d_y device FP32 [M] labels (0/1)

@@ -400,7 +400,7 @@ def trk_da_survival(lattices, x0, y0, offsets, n_turns, schedule=None, stream=No
 
 
 def trk_da_survival_lanes(lattices, x0, y0, offsets, n_turns, stream=None):
-    """As trk_da_survival, 8 lanes per particle (few points; MAP, EDRIFT and
+    """As trk_da_survival, 4 or 8 lanes per particle (few points; MAP, EDRIFT and
     THINSEXT lattices)."""
     import torch
     offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
