@@ -81,7 +81,13 @@ def test_triage_matches_exhaustive_boundary(use_mlp):
     if use_mlp == 1:
         assert st["n_region"] == nv * n * n
     elif use_mlp == 2:
-        assert 0 < st["n_region"] < nv * n * n
+        # the network's cells: within distance 3 of a boundary cell of the
+        # nearest-known prediction from the exact coarse and sentinel labels
+        want = 0
+        for v in range(nv):
+            nk = otri.nearest_known_prediction(exh[v] == turns + 1, n, 4, 5)
+            want += int(otri.dilate(otri.boundary(nk), 3).sum())
+        assert st["n_region"] == want and 0 < want < nv * n * n
 
 
 def test_nonlearned_triage_matches_triage_oracle():
