@@ -393,7 +393,7 @@ __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E
     // z0: run-time +0 (see rf_cos)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const double Pp = fma(fma(q.d[p], 1.0, 1.0), p0, z0);   // (1 + delta) p0, each step rounded as written
+        const double Pp = fma(q.d[p], p0, p0);   // (1 + delta) p0 in one rounding
         const double P1 = fma(V, rf_cos(cphi, sphi, phi, fma(k, q.l[p], z0), z0), Pp);
         // s = Pp / P1 through Newton's iteration for the reciprocal, r <- r + r (1 - P1 r),
         // which squares the relative error 1 - P1 r at every step, seeded with 1/p0'
@@ -413,7 +413,7 @@ __device__ __forceinline__ void v_rfca(Tile<P> &q, const DevElem *__restrict__ E
         }
         q.xp[p] = fma(q.xp[p], s, z0);
         q.yp[p] = fma(q.yp[p], s, z0);
-        q.d[p] = fma(P1, ip01, -1.0);
+        q.d[p] = -e0;   // P1 / p0' - 1: the rounding of P1 ip01 - 1 is minus that of 1 - P1 ip01
     }
     dirty = true;
 }
