@@ -95,11 +95,23 @@ __global__ void k_list_features(const int64_t *__restrict__ idx, int64_t m, int 
 }
 
 // The cells with bit 0 of region set, in any order (each cell's prediction
-// depends on its own features only, so the order does not reach the mask).
+// depends on its own features only, so the order does not reach the mask); one
+// atomic per warp and step (the warp's set lanes take consecutive slots).
 __global__ void k_region_list(const uint8_t *__restrict__ region, int64_t n, int64_t *__restrict__ idx,
                               unsigned long long *__restrict__ count) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        if (region[c] & 1) idx[atomicAdd(count, 1ull)] = c;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of steps (the bound is rounded up to whole warps)
+    const int64_t n_up = (n + 31) / 32 * 32;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_up; c += stride) {
+        const bool set = c < n && (region[c] & 1);
+        const unsigned m = __ballot_sync(0xffffffffu, set);
+        if (!m) continue;
+        unsigned long long base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (set) idx[base + __popc(m & ((1u << lane) - 1u))] = c;
+    }
 }
 
 __global__ void k_list_threshold(const int64_t *__restrict__ idx, const float *__restrict__ logit, int64_t m,
